@@ -1,0 +1,192 @@
+/*
+ * sdmd.h -- C ABI of libsdmd, a streaming method-of-snapshots DMD engine for
+ * one NVIDIA GB300 (sm_103a). Implements the streaming SVD and exact DMD of
+ * Pendergrass, Kutz & Brunton, "Streaming GPU Singular Value and Dynamic Mode
+ * Decompositions" (arXiv 1612.07875).
+ *
+ * Model. A handle holds a window of the m most recent snapshots x_t (each a
+ * vector of n values) in a device-resident ring buffer, and the window's
+ * inner-product matrix G = X^H X (m x m) indexed by ring slot. Each push
+ * computes the one new row/column of G (m dot products over n) and drops the
+ * oldest snapshot by advancing the ring head instead of moving data
+ * (Sec. 3.1, Eq. 12a-b; Algorithm 1). sdmd_modes then reads X^H X and X^H X'
+ * as two blocks of the same G, solves the small eigenproblems in FP64 on the
+ * device and forms the exact DMD modes Phi = X' V Sigma^-1 W (Sec. 2.2,
+ * Eqs. 7-9; Algorithm 2).
+ *
+ * Conventions for every entry point:
+ *  - Return value is an sdmd_status; nothing throws across the ABI. On error
+ *    sdmd_last_error() gives a message (thread-local, valid until the next
+ *    call on the same thread).
+ *  - `stream` is a cudaStream_t (CUstream) passed as void*; NULL means the
+ *    legacy default stream. All device work is enqueued on it and the call
+ *    returns without waiting, except where stated.
+ *  - Buffer arguments may be device pointers (cudaMalloc / managed) or host
+ *    pointers (pinned or pageable); the kind is detected per call. Host
+ *    inputs are copied with cudaMemcpyAsync on `stream` (a pageable source is
+ *    copied before the call returns). Outputs to device or pinned host memory
+ *    are written in stream order; outputs to pageable host memory make the
+ *    call wait for `stream` to finish. Buffers must stay valid until the
+ *    stream reaches the work that uses them.
+ *  - The library owns the ring buffer, G and its workspaces (device memory
+ *    allocated in sdmd_create, freed in sdmd_destroy). The caller owns every
+ *    pointer it passes.
+ *  - Calls on one handle must be issued in one stream order (one stream, or
+ *    streams the caller orders with events); a handle is not thread-safe.
+ *  - The handle is bound to the CUDA device that was current at create time;
+ *    each call makes that device current and restores the caller's device.
+ */
+#ifndef SDMD_H
+#define SDMD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SDMD_API __attribute__((visibility("default")))
+#else
+#define SDMD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sdmd_s *sdmd_t;
+
+/* Snapshot element types. */
+enum {
+    SDMD_F32 = 0, /* dense float32 snapshots; G accumulated in FP64          */
+    SDMD_U8 = 1   /* dense uint8 (e.g. video pixels); G exact in int64       */
+};
+
+/* Status codes. */
+enum {
+    SDMD_OK = 0,
+    SDMD_ERR_ARG = -1,        /* invalid argument (size, pointer, dtype, r)    */
+    SDMD_ERR_OOM = -2,        /* device allocation failed                      */
+    SDMD_ERR_NOT_READY = -3,  /* window too short for the request              */
+    SDMD_ERR_CUDA = -4,       /* a CUDA runtime call or kernel launch failed   */
+    SDMD_ERR_TIMEOUT = -5,    /* a bounded device wait gave up                 */
+    SDMD_ERR_RANK = -6,       /* numerically singular system                   */
+    SDMD_ERR_UNSUPPORTED = -7 /* operation not available for this handle type  */
+};
+
+/* Largest window (number of resident snapshots) a handle may hold. */
+#define SDMD_MAX_M 256
+
+/*
+ * sdmd_create -- allocate a streaming window.
+ *   n      number of values per snapshot (the paper's n, Eq. 1), 1 <= n <= 2^34.
+ *   m      window length: number of resident snapshots, 2 <= m <= SDMD_MAX_M.
+ *          G is m x m; DMD uses the c-1 snapshot pairs of the c <= m resident
+ *          snapshots (X = oldest c-1, X' = newest c-1; Algorithm 2).
+ *   dtype  SDMD_F32 or SDMD_U8.
+ *   out    receives the handle (host pointer).
+ * Device memory: m * round_up(n * sizeof(elem), 4096) bytes of ring plus
+ * O(m^2) of G and workspaces. Ring padding is zero and never written, so
+ * vector kernels may read whole 4 KiB units. Returns SDMD_ERR_OOM if any
+ * allocation fails (nothing is leaked). Synchronous.
+ */
+SDMD_API int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t *out);
+
+/* sdmd_destroy -- wait for the handle's device work and free it. NULL is OK. */
+SDMD_API int sdmd_destroy(sdmd_t h);
+
+/*
+ * sdmd_push -- append one snapshot (streaming Gram update, Sec. 3.1, Eq. 12b;
+ * Algorithm 1's else branch).
+ *   x   n elements of the handle's dtype, contiguous; host or device pointer.
+ * Copies x into ring slot `head`, computes g_j = <x_j, x> for every resident
+ * slot j (including x itself) and writes g into row and column `head` of G
+ * (the symmetric insert), then advances head. The oldest snapshot is
+ * overwritten, not moved. Before the window is full nothing is evicted
+ * (ramp-up, Sec. 5). FP32: products in FP32 over short runs, sums in FP64,
+ * fixed reduction order (deterministic for a given n and GPU). U8: exact.
+ */
+SDMD_API int sdmd_push(sdmd_t h, const void *x, void *stream);
+
+/* sdmd_count -- number of snapshots pushed so far (host pointer). Host-side
+ * bookkeeping only; does not touch the device. */
+SDMD_API int sdmd_count(sdmd_t h, int64_t *count);
+
+/*
+ * sdmd_gram -- copy the window's Gram in time order (test and inspection
+ * hook). G receives c x c row-major values, c = min(count, m), oldest
+ * snapshot first: double for SDMD_F32, int64_t for SDMD_U8.
+ */
+SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
+
+/*
+ * sdmd_modes -- exact DMD of the current window (Sec. 2.2, Eqs. 7-9;
+ * Algorithm 2), all small algebra in FP64 on the device:
+ *   G_X = G[0:c-1, 0:c-1], G_XY = G[0:c-1, 1:c]  (X^H X and X^H X', read as
+ *        blocks of the one time-ordered G; no second set of dot products)
+ *   G_X V = V Lambda_G, sorted descending, sigma = sqrt(Lambda_G), truncated
+ *        to r and to the numerical rank (Gram eigenvalues above
+ *        lambda_1 * 64 * (c-1) * 2^-52)
+ *   vsi = V Sigma^-1; A~ = vsi^T G_XY vsi; A~ W = W Lambda (unit-norm columns)
+ *   Phi = X' vsi W   (X' read in place from the ring)
+ *   r       requested number of modes, 1 <= r <= c-1.
+ *   phi     n x r complex64, column-major (mode k at phi + 2*k*n floats,
+ *           interleaved re, im), or NULL to skip forming Phi. Columns at or
+ *           beyond the kept rank are zero.
+ *   lambda  r complex128 (interleaved re, im doubles) ordered by descending
+ *           |lambda| then by angle; entries beyond the kept rank are zero.
+ *   r_out   receives the kept rank (int32), or NULL.
+ * phi must be device memory (SDMD_ERR_ARG otherwise); lambda and r_out may
+ * be device or host memory. Needs c >= 3 snapshots (else
+ * SDMD_ERR_NOT_READY). The eigensolvers have iteration caps; if one is
+ * reached the call still completes and sdmd_status reports SDMD_ERR_RANK.
+ */
+SDMD_API int sdmd_modes(sdmd_t h, int32_t r, void *phi, void *lambda, int32_t *r_out, void *stream);
+
+/*
+ * sdmd_svd -- singular values and right singular vectors of X from the last
+ * sdmd_modes call (Sec. 2.1, Eqs. 3-4; Algorithm 1). sigma receives r doubles
+ * (descending; zero beyond the kept rank), V receives (c-1) x r doubles,
+ * column-major (vector k at V + k*(c-1)); either may be NULL. r must equal the
+ * r of that sdmd_modes call.
+ */
+SDMD_API int sdmd_svd(sdmd_t h, int32_t r, double *sigma, double *V, void *stream);
+
+/*
+ * sdmd_status -- waits for `stream`, then reports the device-side status
+ * word of the handle (SDMD_OK, or SDMD_ERR_RANK / SDMD_ERR_TIMEOUT raised by
+ * a kernel since the last sdmd_status call) and clears it.
+ */
+SDMD_API int sdmd_status(sdmd_t h, void *stream);
+
+/* Kernel classes for tracing. */
+enum {
+    SDMD_K_INGEST = 0,    /* snapshot copy into its ring slot (a memcpy)       */
+    SDMD_K_GRAM_ROW = 1,  /* Gram-row multi-dot + symmetric insert            */
+    SDMD_K_MODES = 2,     /* FP64 eigensolvers / small products (one CTA)     */
+    SDMD_K_PHI = 3,       /* Phi = X' (V Sigma^-1 W)                          */
+    SDMD_K_COUNT = 4
+};
+
+/*
+ * sdmd_trace -- enable (1) or disable (0) per-launch timing on a handle. While
+ * enabled, every device operation of the handle is bracketed by a pair of
+ * CUDA events recorded on the stream it is enqueued on. Host-side only; adds
+ * no device work besides the event records.
+ */
+SDMD_API int sdmd_trace(sdmd_t h, int32_t enable);
+
+/*
+ * sdmd_trace_read -- for kernel class `kernel` (SDMD_K_*), waits for the
+ * recorded events and returns the number of traced launches and their total
+ * device time in milliseconds since the previous read (or since tracing was
+ * enabled), then resets that class's counters.
+ */
+SDMD_API int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t *launches, double *total_ms);
+
+/* sdmd_last_error -- message for the last failed call on this thread. */
+SDMD_API const char *sdmd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDMD_H */

@@ -81,7 +81,7 @@ class DMDResult:
     lam: np.ndarray        # (r,) DMD eigenvalues, Eq. 8
     W: np.ndarray          # (r, r) eigenvectors of Atilde (unit 2-norm columns)
     M: np.ndarray          # (p, r) V Sigma^-1 W
-    Phi: np.ndarray        # (n, r) exact DMD modes, Eq. 9
+    Phi: object            # (n, r) exact DMD modes, Eq. 9 (None from dmd_from_gram)
     lam_all: np.ndarray    # (p,) all eigenvalues of X^H X, descending
 
 
@@ -100,24 +100,20 @@ def _window_blocks(W, exact_u8):
     return X, Xp, GX, GXY
 
 
-def exact_dmd(W, r):
-    """Exact DMD of the window W (n x c, columns oldest to newest), rank <= r.
+def dmd_from_gram(GX, GXY, r):
+    """The small-matrix part of exact DMD from the two Gram blocks.
 
+    GX = X^H X and GXY = X^H X' (both p x p). Returns a DMDResult without
+    Phi (Phi = None): sigma, V, vsi, A~, lambda, W, M = vsi W.
     Steps, in the order of Algorithms 1-2:
-      GX = X^H X, GXY = X^H X'                       (Eqs. 3, 7)
       GX V = V Lambda_G, sort desc, sigma = sqrt      (Eq. 3, Algorithm 1)
       vsi = V_r Sigma_r^-1
       A~ = vsi^H GXY vsi  (= U^H X' V Sigma^-1)       (Eq. 7)
       A~ W = W Lambda                                (Eq. 8)
-      Phi = X' vsi W                                 (Eq. 9)
     Eigenpairs of A~ are ordered by descending |lambda|, then by angle.
     """
-    W = np.asarray(W)
-    if W.ndim != 2 or W.shape[1] < 2:
-        raise ValueError("window needs at least 2 snapshots")
-    exact_u8 = W.dtype == np.uint8
-    X, Xp, GX, GXY = _window_blocks(W, exact_u8)
-    p = GX.shape[0]
+    GX = np.asarray(GX)
+    GXY = np.asarray(GXY)
     lam_all, sigma_all, V_all, rank = mos_svd(GX)
     rr = int(min(max(r, 0), rank))
     V = V_all[:, :rr]
@@ -133,12 +129,26 @@ def exact_dmd(W, r):
         lam = np.zeros(0, dtype=np.complex128)
         Wd = np.zeros((0, 0), dtype=np.complex128)
     M = vsi @ Wd
-    Xp_f = Xp.astype(np.complex128) if np.iscomplexobj(Xp) else Xp.astype(np.float64)
-    Phi = Xp_f @ M
     return DMDResult(r=rr, rank=rank, sigma=s, V=V, vsi=vsi, Atilde=At,
                      lam=lam.astype(np.complex128), W=Wd.astype(np.complex128),
-                     M=M.astype(np.complex128), Phi=Phi.astype(np.complex128),
-                     lam_all=lam_all)
+                     M=M.astype(np.complex128), Phi=None, lam_all=lam_all)
+
+
+def exact_dmd(W, r):
+    """Exact DMD of the window W (n x c, columns oldest to newest), rank <= r.
+
+    GX = X^H X and GXY = X^H X' are computed directly from the window
+    (Eqs. 3, 7), then dmd_from_gram, then Phi = X' vsi W (Eq. 9).
+    """
+    W = np.asarray(W)
+    if W.ndim != 2 or W.shape[1] < 2:
+        raise ValueError("window needs at least 2 snapshots")
+    exact_u8 = W.dtype == np.uint8
+    X, Xp, GX, GXY = _window_blocks(W, exact_u8)
+    res = dmd_from_gram(GX, GXY, r)
+    Xp_f = Xp.astype(np.complex128) if np.iscomplexobj(Xp) else Xp.astype(np.float64)
+    res.Phi = (Xp_f @ res.M).astype(np.complex128)
+    return res
 
 
 def pod_amplitudes(res):

@@ -1,0 +1,384 @@
+// C ABI of libsdmd: handle lifetime, argument checks, pointer-kind handling,
+// and the launch sequences of sdmd_push / sdmd_modes (see include/sdmd.h).
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sdmd.h"
+#include "sdmd_internal.cuh"
+
+using namespace sdmd;
+
+struct sdmd_s {
+  int device = 0;
+  int num_sms = 0;
+  int64_t n = 0;
+  int32_t m = 0;
+  int32_t dtype = 0;
+  int64_t elem = 0;
+  int64_t slot_bytes = 0;
+  uint8_t* ring = nullptr;
+  void* G = nullptr;          // m x m physical, 8-byte entries
+  void* gtmp = nullptr;       // m x m gather scratch for sdmd_gram
+  void* partials = nullptr;   // [m][nblk] 8-byte entries
+  unsigned int* ticket = nullptr;
+  int64_t chunk = 0;
+  int32_t nblk = 0;
+  double* ws = nullptr;       // modes workspace
+  int* status = nullptr;      // device status word
+  int* r_dev = nullptr;       // device int: kept rank of the last modes call
+  int64_t count = 0;
+  int32_t head = 0;
+  int32_t last_r = 0;         // r of the last sdmd_modes call (0 = none)
+  int32_t last_p = 0;
+  // tracing: per kernel class, event pairs recorded since the last read
+  bool trace = false;
+  std::vector<cudaEvent_t> tr_ev[SDMD_K_COUNT];
+  size_t tr_used[SDMD_K_COUNT] = {0, 0, 0, 0};
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(SDMD_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t _e = (call);                       \
+    if (_e != cudaSuccess) return cuda_fail(_e, #call); \
+  } while (0)
+
+// Makes the handle's device current for the scope of a call.
+struct DeviceScope {
+  int prev = -1;
+  bool changed = false;
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) {
+      if (cudaSetDevice(dev) == cudaSuccess) changed = true;
+    }
+  }
+  ~DeviceScope() {
+    if (changed) cudaSetDevice(prev);
+  }
+};
+
+enum PtrKind { kPageable = 0, kPinned = 1, kDevice = 2 };
+
+PtrKind ptr_kind(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kPageable;
+  }
+  switch (at.type) {
+    case cudaMemoryTypeDevice:
+    case cudaMemoryTypeManaged:
+      return kDevice;
+    case cudaMemoryTypeHost:
+      return kPinned;
+    default:
+      return kPageable;
+  }
+}
+
+// Copy `bytes` from device memory to a caller buffer of any kind; pageable
+// destinations make the call wait for the stream.
+int copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t st) {
+  if (bytes == 0) return SDMD_OK;
+  const PtrKind k = ptr_kind(dst);
+  CK(cudaMemcpyAsync(dst, src_dev, bytes, cudaMemcpyDefault, st));
+  if (k == kPageable) CK(cudaStreamSynchronize(st));
+  return SDMD_OK;
+}
+
+__global__ void gather_gram_kernel(const uint64_t* G, int m, int c, int start, uint64_t* out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= c * c) return;
+  const int i = idx / c, j = idx - i * c;
+  out[idx] = G[(int64_t)((start + i) % m) * m + (start + j) % m];
+}
+
+// Brackets one enqueued operation with a pair of events when tracing is on.
+struct TraceScope {
+  sdmd_s* h;
+  int k;
+  cudaStream_t st;
+  bool on;
+  TraceScope(sdmd_s* h_, int k_, cudaStream_t st_) : h(h_), k(k_), st(st_), on(h_->trace) {
+    if (!on) return;
+    auto& v = h->tr_ev[k];
+    while (v.size() < 2 * (h->tr_used[k] + 1)) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on = false;
+        return;
+      }
+      v.push_back(e);
+    }
+    cudaEventRecord(v[2 * h->tr_used[k]], st);
+  }
+  ~TraceScope() {
+    if (!on) return;
+    cudaEventRecord(h->tr_ev[k][2 * h->tr_used[k] + 1], st);
+    h->tr_used[k] += 1;
+  }
+};
+
+void free_all(sdmd_s* h) {
+  for (int k = 0; k < SDMD_K_COUNT; ++k)
+    for (cudaEvent_t e : h->tr_ev[k]) cudaEventDestroy(e);
+  cudaFree(h->ring);
+  cudaFree(h->G);
+  cudaFree(h->gtmp);
+  cudaFree(h->partials);
+  cudaFree(h->ticket);
+  cudaFree(h->ws);
+  cudaFree(h->status);
+  cudaFree(h->r_dev);
+}
+
+inline int32_t resident(const sdmd_s* h) { return (int32_t)(h->count < h->m ? h->count : h->m); }
+inline int32_t oldest_slot(const sdmd_s* h) { return h->count >= h->m ? h->head : 0; }
+
+}  // namespace
+
+extern "C" {
+
+const char* sdmd_last_error(void) { return g_err.c_str(); }
+
+int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) {
+  if (!out) return fail(SDMD_ERR_ARG, "sdmd_create: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > (int64_t(1) << 34)) return fail(SDMD_ERR_ARG, "sdmd_create: n=%lld out of range", (long long)n);
+  if (m < 2 || m > SDMD_MAX_M) return fail(SDMD_ERR_ARG, "sdmd_create: m=%d not in [2, %d]", m, SDMD_MAX_M);
+  if (dtype != SDMD_F32 && dtype != SDMD_U8) return fail(SDMD_ERR_ARG, "sdmd_create: dtype %d unknown", dtype);
+  sdmd_s* h = new (std::nothrow) sdmd_s();
+  if (!h) return fail(SDMD_ERR_OOM, "sdmd_create: host allocation failed");
+  CK(cudaGetDevice(&h->device));
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->n = n;
+  h->m = m;
+  h->dtype = dtype;
+  h->elem = (dtype == SDMD_U8) ? 1 : 4;
+  h->slot_bytes = ((n * h->elem + kSlotAlign - 1) / kSlotAlign) * kSlotAlign;
+  gram_row_schedule(h->slot_bytes, h->num_sms, &h->chunk, &h->nblk);
+  const size_t ring_bytes = (size_t)m * (size_t)h->slot_bytes;
+  const size_t ws_bytes = (size_t)modes_ws_doubles(m) * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&h->ring, ring_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->ring, 0, ring_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * 8);
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->ws, 0, ws_bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->r_dev, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? SDMD_ERR_OOM : SDMD_ERR_CUDA;
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return fail(code, "sdmd_create(n=%lld, m=%d): %s", (long long)n, m, cudaGetErrorString(e));
+  }
+  *out = h;
+  return SDMD_OK;
+}
+
+int sdmd_destroy(sdmd_t h) {
+  if (!h) return SDMD_OK;
+  DeviceScope ds(h->device);
+  cudaDeviceSynchronize();
+  free_all(h);
+  delete h;
+  return SDMD_OK;
+}
+
+int sdmd_push(sdmd_t h, const void* x, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_push: NULL handle");
+  if (!x) return fail(SDMD_ERR_ARG, "sdmd_push: NULL snapshot");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int32_t s = h->head;
+  {
+    TraceScope ts(h, SDMD_K_INGEST, st);
+    CK(cudaMemcpyAsync(h->ring + (int64_t)s * h->slot_bytes, x, (size_t)(h->n * h->elem),
+                       cudaMemcpyDefault, st));
+  }
+  GramRowArgs a;
+  a.ring = h->ring;
+  a.slot_bytes = h->slot_bytes;
+  a.chunk = h->chunk;
+  a.nblk = h->nblk;
+  a.c = (int32_t)(h->count + 1 < h->m ? h->count + 1 : h->m);
+  a.s_new = s;
+  a.m = h->m;
+  a.partials = h->partials;
+  a.ticket = h->ticket;
+  a.G = h->G;
+  {
+    TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+    CK(launch_gram_row(h->dtype, a, st));
+  }
+  h->head = (s + 1) % h->m;
+  h->count += 1;
+  return SDMD_OK;
+}
+
+int sdmd_count(sdmd_t h, int64_t* count) {
+  if (!h || !count) return fail(SDMD_ERR_ARG, "sdmd_count: NULL argument");
+  *count = h->count;
+  return SDMD_OK;
+}
+
+int sdmd_gram(sdmd_t h, void* G, void* stream) {
+  if (!h || !G) return fail(SDMD_ERR_ARG, "sdmd_gram: NULL argument");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int c = resident(h);
+  if (c == 0) return SDMD_OK;
+  const bool direct = ptr_kind(G) == kDevice;
+  uint64_t* dst = direct ? static_cast<uint64_t*>(G) : static_cast<uint64_t*>(h->gtmp);
+  gather_gram_kernel<<<(c * c + 255) / 256, 256, 0, st>>>(static_cast<const uint64_t*>(h->G), h->m, c,
+                                                           oldest_slot(h), dst);
+  CK(cudaGetLastError());
+  if (!direct) return copy_out(G, h->gtmp, (size_t)c * c * 8, st);
+  return SDMD_OK;
+}
+
+int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_modes: NULL handle");
+  const int c = resident(h);
+  if (c < 3) return fail(SDMD_ERR_NOT_READY, "sdmd_modes: %d snapshots resident, need >= 3", c);
+  if (r < 1 || r > c - 1) return fail(SDMD_ERR_ARG, "sdmd_modes: r=%d not in [1, %d]", r, c - 1);
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (phi && ptr_kind(phi) != kDevice)
+    return fail(SDMD_ERR_ARG, "sdmd_modes: phi must be device memory (n x r complex64)");
+  ModesArgs a;
+  a.G = h->G;
+  a.g_is_int = (h->dtype == SDMD_U8) ? 1 : 0;
+  a.m = h->m;
+  a.c = c;
+  a.start = oldest_slot(h);
+  a.r_req = r;
+  a.ws = h->ws;
+  a.status = h->status;
+  a.r_dev = h->r_dev;
+  {
+    TraceScope ts(h, SDMD_K_MODES, st);
+    CK(launch_modes_small(a, st));
+  }
+  const ModesLayout L = modes_layout(h->m);
+  if (phi) {
+    PhiArgs pa;
+    pa.ring = h->ring;
+    pa.slot_bytes = h->slot_bytes;
+    pa.n = h->n;
+    pa.dtype = h->dtype;
+    pa.m = h->m;
+    pa.start = a.start;
+    pa.p = c - 1;
+    pa.r = r;
+    pa.Mf = reinterpret_cast<const float*>(h->ws + L.Mf);
+    pa.r_dev = h->r_dev;
+    pa.phi = static_cast<float*>(phi);
+    TraceScope ts(h, SDMD_K_PHI, st);
+    CK(launch_phi(pa, st));
+  }
+  h->last_r = r;
+  h->last_p = c - 1;
+  if (lambda) {
+    const int rc = copy_out(lambda, h->ws + L.lamout, (size_t)r * 16, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  if (r_out) {
+    const int rc = copy_out(r_out, h->r_dev, sizeof(int32_t), st);
+    if (rc != SDMD_OK) return rc;
+  }
+  return SDMD_OK;
+}
+
+int sdmd_svd(sdmd_t h, int32_t r, double* sigma, double* V, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_svd: NULL handle");
+  if (h->last_r == 0) return fail(SDMD_ERR_NOT_READY, "sdmd_svd: no sdmd_modes call yet");
+  if (r != h->last_r) return fail(SDMD_ERR_ARG, "sdmd_svd: r=%d differs from the last sdmd_modes r=%d", r, h->last_r);
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ModesLayout L = modes_layout(h->m);
+  if (sigma) {
+    const int rc = copy_out(sigma, h->ws + L.sig, (size_t)r * sizeof(double), st);
+    if (rc != SDMD_OK) return rc;
+  }
+  if (V) {
+    const int rc = copy_out(V, h->ws + L.V, (size_t)r * h->last_p * sizeof(double), st);
+    if (rc != SDMD_OK) return rc;
+  }
+  return SDMD_OK;
+}
+
+int sdmd_trace(sdmd_t h, int32_t enable) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_trace: NULL handle");
+  h->trace = enable != 0;
+  for (int k = 0; k < SDMD_K_COUNT; ++k) h->tr_used[k] = 0;
+  return SDMD_OK;
+}
+
+int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t* launches, double* total_ms) {
+  if (!h || !launches || !total_ms) return fail(SDMD_ERR_ARG, "sdmd_trace_read: NULL argument");
+  if (kernel < 0 || kernel >= SDMD_K_COUNT) return fail(SDMD_ERR_ARG, "sdmd_trace_read: kernel %d", kernel);
+  DeviceScope ds(h->device);
+  double tot = 0.0;
+  const size_t used = h->tr_used[kernel];
+  for (size_t i = 0; i < used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventSynchronize(h->tr_ev[kernel][2 * i + 1]));
+    CK(cudaEventElapsedTime(&ms, h->tr_ev[kernel][2 * i], h->tr_ev[kernel][2 * i + 1]));
+    tot += ms;
+  }
+  *launches = (int64_t)used;
+  *total_ms = tot;
+  h->tr_used[kernel] = 0;
+  return SDMD_OK;
+}
+
+int sdmd_status(sdmd_t h, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_status: NULL handle");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int v = 0;
+  CK(cudaMemcpyAsync(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+  CK(cudaStreamSynchronize(st));
+  if (v & kDevTimeout) return fail(SDMD_ERR_TIMEOUT, "device wait timed out");
+  if (v & kDevRank) return fail(SDMD_ERR_RANK, "eigensolver iteration cap reached");
+  return SDMD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Internal declarations shared by the libsdmd translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sdmd.h"
+
+namespace sdmd {
+
+// Ring slots are padded to a multiple of this many bytes; the padding is zero
+// and is never written, so kernels may process whole units.
+constexpr int64_t kSlotAlign = 4096;
+
+// Gram-row kernel geometry (gram_row.cu).
+constexpr int kGrThreads = 256;
+constexpr int kGrWarps = kGrThreads / 32;
+constexpr int kGrUnroll = 8;                       // 16-byte loads per lane per step
+constexpr int kGrStep = 32 * 16 * kGrUnroll;       // bytes one warp reads per step
+constexpr int kGrSub = 16384;                      // x_new bytes staged in smem
+
+// Device-side status word values (mirrors the public codes).
+constexpr int kDevOk = 0;
+constexpr int kDevRank = 1;      // an eigensolver reached its iteration cap
+constexpr int kDevTimeout = 2;   // a bounded wait gave up
+
+struct GramRowArgs {
+  const uint8_t* ring;   // slot j starts at ring + j * slot_bytes
+  int64_t slot_bytes;    // multiple of kSlotAlign
+  int64_t chunk;         // bytes per CTA, multiple of kGrStep
+  int32_t nblk;          // CTAs; nblk * chunk >= slot_bytes
+  int32_t c;             // resident slots 0..c-1 (after this push)
+  int32_t s_new;         // slot holding the new snapshot
+  int32_t m;             // G is m x m
+  void* partials;        // [nblk][m] per-CTA partial sums (FP64 or int64)
+  unsigned int* ticket;  // CTA completion counter, zero between launches
+  void* G;               // m x m, double (f32) or int64 (u8), physical slots
+};
+
+// Gram row for one pushed snapshot; launches one kernel on `st`.
+cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st);
+
+// Schedule of the Gram-row kernel: a function of slot size and SM count only,
+// so that every entry of G sees the same summation order.
+void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t* nblk);
+
+struct ModesArgs {
+  const void* G;        // m x m physical (double or int64)
+  int32_t g_is_int;     // 1: int64 entries
+  int32_t m;
+  int32_t c;            // resident snapshots (>= 3)
+  int32_t start;        // physical slot of the oldest resident snapshot
+  int32_t r_req;        // requested modes (1 <= r_req <= c-1)
+  double* ws;           // workspace (modes_ws_doubles(m) doubles)
+  int* status;          // device status word (sticky error bits)
+  int* r_dev;           // kept rank (device int)
+};
+
+// Doubles of workspace needed by the modes kernel for window length m.
+int64_t modes_ws_doubles(int m);
+
+// Offsets (in doubles) of the named arrays inside the modes workspace.
+struct ModesLayout {
+  int64_t A, GXY, HV, d, e, lam, Z, V, Y, At, Hc, Qc, Wc, M, Mf, sig, lamout, tmp, lu;
+  int64_t total;
+};
+ModesLayout modes_layout(int m);
+
+cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st);
+
+struct PhiArgs {
+  const uint8_t* ring;
+  int64_t slot_bytes;
+  int64_t n;
+  int32_t dtype;
+  int32_t m;
+  int32_t start;        // physical slot of the oldest resident snapshot
+  int32_t p;            // c-1 columns of X'
+  int32_t r;            // requested modes (output columns)
+  const float* Mf;      // p x 2r  (re, im) of V Sigma^-1 W, FP32
+  const int* r_dev;     // kept rank; columns >= *r_dev are written as zero
+  float* phi;           // n x r complex64, column-major
+};
+
+cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
+
+}  // namespace sdmd

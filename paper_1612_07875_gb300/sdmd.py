@@ -1,0 +1,166 @@
+"""Thin ctypes binding of libsdmd (include/sdmd.h): same names, argument
+marshalling only. Every step of the computation runs in the library's CUDA
+kernels; there is no Python or CPU fallback. If libsdmd.so is missing or
+cannot be loaded, the first call raises.
+
+Pointer arguments accept a torch tensor, a numpy array, or a raw address
+(int). Streams accept a torch.cuda.Stream, a raw cudaStream_t (int) or
+None / 0 for the legacy default stream.
+"""
+import ctypes
+import os
+import threading
+
+SDMD_F32 = 0
+SDMD_U8 = 1
+
+SDMD_OK = 0
+SDMD_ERR_ARG = -1
+SDMD_ERR_OOM = -2
+SDMD_ERR_NOT_READY = -3
+SDMD_ERR_CUDA = -4
+SDMD_ERR_TIMEOUT = -5
+SDMD_ERR_RANK = -6
+SDMD_ERR_UNSUPPORTED = -7
+SDMD_MAX_M = 256
+
+SDMD_K_INGEST = 0
+SDMD_K_GRAM_ROW = 1
+SDMD_K_MODES = 2
+SDMD_K_PHI = 3
+SDMD_K_COUNT = 4
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsdmd.so")
+
+_lock = threading.Lock()
+_lib = None
+
+_VP = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+
+# name -> argtypes (every entry point returns int except sdmd_last_error)
+_SIGNATURES = {
+    "sdmd_create": [_I64, _I32, _I32, ctypes.POINTER(_VP)],
+    "sdmd_destroy": [_VP],
+    "sdmd_push": [_VP, _VP, _VP],
+    "sdmd_count": [_VP, ctypes.POINTER(_I64)],
+    "sdmd_gram": [_VP, _VP, _VP],
+    "sdmd_modes": [_VP, _I32, _VP, _VP, _VP, _VP],
+    "sdmd_svd": [_VP, _I32, _VP, _VP, _VP],
+    "sdmd_status": [_VP, _VP],
+    "sdmd_trace": [_VP, _I32],
+    "sdmd_trace_read": [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
+}
+
+
+class SdmdError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+def lib():
+    """Load libsdmd.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libsdmd.so is not built (%s); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, argt in _SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = argt
+                fn.restype = ctypes.c_int
+            L.sdmd_last_error.argtypes = []
+            L.sdmd_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def ptr(x):
+    """Address of a torch tensor / numpy array / int (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def stream_handle(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    if hasattr(s, "cuda_stream"):
+        return s.cuda_stream
+    raise TypeError("not a stream: %r" % type(s))
+
+
+def _check(rc, fn):
+    if rc != SDMD_OK:
+        raise SdmdError(rc, "%s: %s" % (fn, sdmd_last_error()))
+    return rc
+
+
+def sdmd_last_error():
+    return lib().sdmd_last_error().decode(errors="replace")
+
+
+def sdmd_create(n, m, dtype):
+    h = _VP()
+    _check(lib().sdmd_create(int(n), int(m), int(dtype), ctypes.byref(h)), "sdmd_create")
+    return h.value
+
+
+def sdmd_destroy(h):
+    _check(lib().sdmd_destroy(h), "sdmd_destroy")
+
+
+def sdmd_push(h, x, stream=None):
+    _check(lib().sdmd_push(h, ptr(x), stream_handle(stream)), "sdmd_push")
+
+
+def sdmd_count(h):
+    c = _I64()
+    _check(lib().sdmd_count(h, ctypes.byref(c)), "sdmd_count")
+    return c.value
+
+
+def sdmd_gram(h, G, stream=None):
+    _check(lib().sdmd_gram(h, ptr(G), stream_handle(stream)), "sdmd_gram")
+
+
+def sdmd_modes(h, r, phi, lam, r_out=None, stream=None):
+    _check(lib().sdmd_modes(h, int(r), ptr(phi), ptr(lam), ptr(r_out), stream_handle(stream)),
+           "sdmd_modes")
+
+
+def sdmd_svd(h, r, sigma, V, stream=None):
+    _check(lib().sdmd_svd(h, int(r), ptr(sigma), ptr(V), stream_handle(stream)), "sdmd_svd")
+
+
+def sdmd_status(h, stream=None):
+    return lib().sdmd_status(h, stream_handle(stream))
+
+
+def sdmd_trace(h, enable):
+    _check(lib().sdmd_trace(h, 1 if enable else 0), "sdmd_trace")
+
+
+def sdmd_trace_read(h, kernel):
+    """(launches, total_ms) for kernel class `kernel` since the last read."""
+    n = _I64()
+    ms = ctypes.c_double()
+    _check(lib().sdmd_trace_read(h, int(kernel), ctypes.byref(n), ctypes.byref(ms)), "sdmd_trace_read")
+    return n.value, ms.value
+
+
+def exported_symbols():
+    """Names the binding expects the library to export."""
+    return sorted(list(_SIGNATURES) + ["sdmd_last_error"])

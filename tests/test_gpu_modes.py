@@ -1,0 +1,199 @@
+"""GPU parity of the exact-DMD step (sdmd_modes / sdmd_svd) against the oracle.
+
+Two kinds of check:
+* same-input parity: the oracle's FP64 dense DMD (numpy/LAPACK) run on the
+  GPU's own G, so only the eigensolvers and small products are compared;
+* end-to-end parity: the oracle recomputes G from the window (exact for
+  uint8) and everything after; eigenvalues within 1e-6 absolute.
+Phi is compared column by column after fixing each column's scale and phase.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1612_07875_gb300 import sdmd as S
+from paper_1612_07875_gb300 import synth
+
+from helpers import col_cos, match_eigs, normalize_cols, rel_fro
+
+pytestmark = pytest.mark.gpu
+
+EIG_TOL = 1e-6
+
+
+def _stream(h, so, frames, dev):
+    for x in frames:
+        S.sdmd_push(h, torch.from_numpy(x).to(dev))
+        so.push(x)
+
+
+def _modes(h, n, r, dev, c):
+    phi = torch.zeros(r, n, 2, dtype=torch.float32, device=dev)
+    lam = np.zeros(2 * r)
+    rout = np.zeros(1, np.int32)
+    S.sdmd_modes(h, r, phi, lam, rout)
+    sig = np.zeros(r)
+    V = np.zeros(r * (c - 1))
+    S.sdmd_svd(h, r, sig, V)
+    torch.cuda.synchronize()
+    assert S.sdmd_status(h) == S.SDMD_OK
+    P = phi.cpu().numpy()
+    P = (P[..., 0] + 1j * P[..., 1]).T          # n x r
+    return int(rout[0]), lam[0::2] + 1j * lam[1::2], sig, V.reshape(r, c - 1).T, P
+
+
+def _gram(h, c, dev, is_u8):
+    G = torch.empty(c, c, dtype=torch.int64 if is_u8 else torch.float64, device=dev)
+    S.sdmd_gram(h, G)
+    torch.cuda.synchronize()
+    return G.cpu().numpy().astype(np.float64)
+
+
+def _compare_same_input(G, rk, lam, sig, V, r):
+    ref = oracle.dmd_from_gram(G[:-1, :-1], G[:-1, 1:], r)
+    assert rk == ref.r
+    assert np.allclose(sig[:rk], ref.sigma, rtol=1e-10, atol=0)
+    err, _ = match_eigs(lam[:rk], ref.lam)
+    assert err <= 1e-9, err
+    assert (col_cos(V[:, :rk], ref.V) > 1 - 1e-9).all()
+    assert np.all(lam[rk:] == 0)
+    return ref
+
+
+def test_planted_fp32_config1_shape(cuda_device):
+    # Synthetic configuration 1: 64x64 field, window 32, r = 10, noise var 1e-3.
+    ps = synth.PlantedStream(seed=synth.config_seed(1))
+    n, m, r, T = ps.n, 32, 10, 60
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    so = oracle.StreamOracle(n, m, "f32")
+    try:
+        _stream(h, so, [ps.snapshot(t) for t in range(T)], cuda_device)
+        rk, lam, sig, V, P = _modes(h, n, r, cuda_device, m)
+        G = _gram(h, m, cuda_device, False)
+        ref = _compare_same_input(G, rk, lam, sig, V, r)
+        # Phi = X' M: oracle product with the oracle's M on the same window
+        W = so.window()
+        Pref = W[:, 1:].astype(np.float64) @ ref.M
+        _, perm = match_eigs(lam[:rk], ref.lam)
+        Pn = normalize_cols(P[:, :rk])
+        Rn = normalize_cols(Pref[:, perm])
+        assert rel_fro(Pn, Rn) <= 1e-4
+        assert np.all(P[:, rk:] == 0)
+        # end-to-end: the 5 planted (signal) eigenvalues agree with the oracle
+        # that recomputes G from the window
+        full = so.modes(5)
+        rk5, lam5, *_ = _modes(h, n, 5, cuda_device, m)
+        err, _ = match_eigs(lam5[:rk5], full.lam)
+        assert rk5 == 5 and err <= EIG_TOL, err
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_u8_video_end_to_end_exact_gram(cuda_device):
+    vs = synth.VideoStream(H=72, W=128, C=3, seed=synth.config_seed(2))
+    n, m, r, T = vs.n, 20, 8, 27
+    h = S.sdmd_create(n, m, S.SDMD_U8)
+    so = oracle.StreamOracle(n, m, "u8")
+    try:
+        _stream(h, so, [vs.frame(t) for t in range(T)], cuda_device)
+        rk, lam, sig, V, P = _modes(h, n, r, cuda_device, m)
+        ref = so.modes(r)
+        assert rk == ref.r
+        err, perm = match_eigs(lam[:rk], ref.lam)
+        assert err <= EIG_TOL, err
+        assert np.allclose(sig[:rk], ref.sigma, rtol=1e-10)
+        Pn = normalize_cols(P[:, :rk])
+        Rn = normalize_cols(ref.Phi[:, perm])
+        assert rel_fro(Pn, Rn) <= 1e-4
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_ramp_up_window_not_full(cuda_device):
+    ps = synth.PlantedStream(side=24, noise_var=1e-4, seed=77)
+    n, m = ps.n, 32
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    so = oracle.StreamOracle(n, m, "f32")
+    try:
+        _stream(h, so, [ps.snapshot(t) for t in range(9)], cuda_device)
+        rk, lam, sig, V, P = _modes(h, n, 5, cuda_device, 9)
+        G = _gram(h, 9, cuda_device, False)
+        _compare_same_input(G, rk, lam, sig, V, 5)
+        ref = so.modes(5)
+        err, _ = match_eigs(lam[:rk], ref.lam)
+        assert err <= EIG_TOL
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_rank_clamped_to_numerical_rank(cuda_device):
+    # snapshots drawn from a 3-dimensional subspace: at most 3 modes survive
+    rng = np.random.default_rng(3)
+    n, m = 2000, 12
+    B = rng.standard_normal((n, 3))
+    frames = [(B @ rng.standard_normal(3)).astype(np.float32) for _ in range(m)]
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    so = oracle.StreamOracle(n, m, "f32")
+    try:
+        _stream(h, so, frames, cuda_device)
+        rk, lam, sig, V, P = _modes(h, n, 8, cuda_device, m)
+        assert rk == 3
+        assert np.all(lam[3:] == 0) and np.all(sig[3:] == 0) and np.all(P[:, 3:] == 0)
+        G = _gram(h, m, cuda_device, False)
+        _compare_same_input(G, rk, lam, sig, V, 8)
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_max_window_256(cuda_device):
+    rng = np.random.default_rng(4)
+    n, m, r = 3000, 256, 12
+    h = S.sdmd_create(n, m, S.SDMD_U8)
+    so = oracle.StreamOracle(n, m, "u8")
+    try:
+        base = rng.integers(0, 200, n)
+        frames = [np.clip(base + rng.integers(-30, 31, n), 0, 255).astype(np.uint8) for _ in range(m + 3)]
+        _stream(h, so, frames, cuda_device)
+        rk, lam, sig, V, P = _modes(h, n, r, cuda_device, m)
+        ref = so.modes(r)
+        assert rk == ref.r
+        err, _ = match_eigs(lam[:rk], ref.lam)
+        assert err <= EIG_TOL, err
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_full_size_hd_video_modes(cuda_device):
+    # Benchmark launch configuration: n = 1920*1080*3 uint8, m = 100, r = 10.
+    vs = synth.VideoStream(seed=synth.config_seed(2))
+    n, m, r, T = vs.n, 100, 10, 103
+    h = S.sdmd_create(n, m, S.SDMD_U8)
+    frames = []
+    try:
+        for t in range(T):
+            f = vs.frame(t)
+            frames.append(f)
+            S.sdmd_push(h, torch.from_numpy(f).to(cuda_device))
+        frames = frames[-m:]
+        rk, lam, sig, V, P = _modes(h, n, r, cuda_device, m)
+        Gref = oracle.gram_u8_cols(frames).astype(np.float64)     # exact
+        G = _gram(h, m, cuda_device, True)
+        assert np.array_equal(G, Gref)
+        ref = oracle.dmd_from_gram(Gref[:-1, :-1], Gref[:-1, 1:], r)
+        assert rk == ref.r
+        err, perm = match_eigs(lam[:rk], ref.lam)
+        assert err <= EIG_TOL, err
+        # sampled rows of Phi, computed one by one by the oracle
+        rows = np.random.default_rng(1).integers(0, n, 64)
+        Xp_rows = np.stack([f[rows] for f in frames[1:]], axis=1).astype(np.float64)
+        Pref = Xp_rows @ ref.M[:, perm]
+        got = P[rows, :rk]
+        scale = np.abs(Pref).max(axis=0)
+        # fix each column's phase on the sampled rows (columns match up to a unit factor)
+        for k in range(rk):
+            i = int(np.argmax(np.abs(Pref[:, k])))
+            got[:, k] *= (Pref[i, k] / got[i, k]) / abs(Pref[i, k] / got[i, k])
+        assert (np.abs(got - Pref).max(axis=0) <= 1e-4 * scale).all()
+    finally:
+        S.sdmd_destroy(h)
