@@ -182,6 +182,37 @@ SDMD_API int sdmd_trace(sdmd_t h, int32_t enable);
  */
 SDMD_API int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t *launches, double *total_ms);
 
+/*
+ * sdmd_gram_row_static -- one Gram row, g[j] = <x_j, y> for j < c, computed
+ * without allocating any device memory. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code whose
+ * device memory is owned by another allocator (a framework's caching pool or
+ * a serving runtime that hands out only pre-registered buffers), real-time
+ * loops that must not take cudaMalloc's device-wide synchronisation or its
+ * unbounded latency, and plugins whose host application forbids device
+ * allocations. It needs no handle: the caller passes every input and output.
+ *   dtype  SDMD_F32 (g: c doubles) or SDMD_U8 (g: c int64, exact).
+ *   X      device pointer to c snapshots of n elements; snapshot j starts at
+ *          element j * ld. X and y 16-byte aligned, ld * sizeof(elem) a
+ *          multiple of 16, ld >= n.
+ *   c      1 <= c <= SDMD_GRAM_ROW_STATIC_MAX_C; larger c is rejected with
+ *          SDMD_ERR_ARG.
+ *   y      device pointer to n elements (may alias one of the x_j).
+ *   g      device pointer to the c outputs.
+ * Scratch: a fixed 1 MiB + 256 B array in device global memory, compiled
+ * into the library (every GPU that loads the library holds it until process
+ * exit). The first call on each device looks up that array's address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * All calls share the one array and the ticket in it is reset to zero at the
+ * start of each call: calls that overlap on the GPU (on different streams,
+ * or from several threads) race and must be serialised by the caller.
+ * FP32 results use a different summation order than sdmd_push (equal to
+ * rounding); U8 results are exact.
+ */
+#define SDMD_GRAM_ROW_STATIC_MAX_C 256
+SDMD_API int sdmd_gram_row_static(int32_t dtype, const void *X, int64_t ld, int32_t c, const void *y,
+                                  int64_t n, void *g, void *stream);
+
 /* sdmd_last_error -- message for the last failed call on this thread. */
 SDMD_API const char *sdmd_last_error(void);
 

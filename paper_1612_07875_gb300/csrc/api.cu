@@ -162,6 +162,11 @@ inline int32_t oldest_slot(const sdmd_s* h) { return h->count >= h->m ? h->head 
 
 }  // namespace
 
+int sdmd::set_last_error(int code, const char* msg) {
+  g_err = msg;
+  return code;
+}
+
 extern "C" {
 
 const char* sdmd_last_error(void) { return g_err.c_str(); }

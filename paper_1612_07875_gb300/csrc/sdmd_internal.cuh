@@ -84,4 +84,7 @@ struct PhiArgs {
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
 
+// Records `msg` as this thread's sdmd_last_error() text; returns `code`.
+int set_last_error(int code, const char* msg);
+
 }  // namespace sdmd

@@ -51,6 +51,7 @@ _SIGNATURES = {
     "sdmd_status": [_VP, _VP],
     "sdmd_trace": [_VP, _I32],
     "sdmd_trace_read": [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
+    "sdmd_gram_row_static": [_I32, _VP, _I64, _I32, _VP, _I64, _VP, _VP],
 }
 
 
@@ -159,6 +160,15 @@ def sdmd_trace_read(h, kernel):
     ms = ctypes.c_double()
     _check(lib().sdmd_trace_read(h, int(kernel), ctypes.byref(n), ctypes.byref(ms)), "sdmd_trace_read")
     return n.value, ms.value
+
+
+SDMD_GRAM_ROW_STATIC_MAX_C = 256
+
+
+def sdmd_gram_row_static(dtype, X, ld, c, y, n, g, stream=None):
+    """g[j] = <x_j, y> for j < c with no device allocation (see sdmd.h)."""
+    _check(lib().sdmd_gram_row_static(int(dtype), ptr(X), int(ld), int(c), ptr(y), int(n), ptr(g),
+                                      stream_handle(stream)), "sdmd_gram_row_static")
 
 
 def exported_symbols():
