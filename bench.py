@@ -278,6 +278,7 @@ def run_ours(args):
     total_ms = ev[0].elapsed_time(ev[K])
     per_step = np.array([ev[i].elapsed_time(ev[i + 1]) for i in range(K)])
     traces = {k: S.sdmd_trace_read(h, k) for k in range(S.SDMD_K_COUNT)}
+    phase_cycles = S.sdmd_modes_phase_cycles(h, sh)
     S.sdmd_trace(h, False)
     if S.sdmd_status(h, sh) != S.SDMD_OK:
         raise RuntimeError("device status after timed region: " + S.sdmd_last_error())
@@ -301,7 +302,8 @@ def run_ours(args):
     il, ims = traces[S.SDMD_K_INGEST]
     kernels = {"gram_row": {"launches": gl, "us": gram_us, "GB/s": gram_gbs},
                "phi": {"launches": pl, "us": phi_us, "GB/s": phi_bytes / (phi_us * 1e-6) / 1e9},
-               "modes_small_f64": {"launches": ml, "us": 1e3 * mms / max(ml, 1)},
+               "modes_small_f64": {"launches": ml, "us": 1e3 * mms / max(ml, 1),
+                                   "phase_kcycles": {k: v / 1e3 for k, v in phase_cycles.items()}},
                "ingest_copy": {"launches": il, "us": 1e3 * ims / max(il, 1)}}
     traffic = None
     tfile = os.path.join(ROOT, "profiles", "traffic.json")

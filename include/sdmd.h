@@ -183,6 +183,15 @@ SDMD_API int sdmd_trace(sdmd_t h, int32_t enable);
 SDMD_API int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t *launches, double *total_ms);
 
 /*
+ * sdmd_modes_phase_cycles -- SM clock counter (clock64) at the phase
+ * boundaries of the last FP64 modes kernel, for profiling: [0] start,
+ * [1] gather, [2] tridiagonalisation, [3] bisection, [4] inverse iteration,
+ * [5] back-transform, [6] A~, [7] eig(A~), [8] end. Copies `count` (<= 16)
+ * values to host memory and waits for `stream`.
+ */
+SDMD_API int sdmd_modes_phase_cycles(sdmd_t h, int64_t *cycles, int32_t count, void *stream);
+
+/*
  * sdmd_gram_row_static -- one Gram row, g[j] = <x_j, y> for j < c, computed
  * without allocating any device memory. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code whose

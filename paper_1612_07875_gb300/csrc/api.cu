@@ -242,11 +242,13 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   a.chunk = h->chunk;
   a.nblk = h->nblk;
   a.c = (int32_t)(h->count + 1 < h->m ? h->count + 1 : h->m);
+  a.s_first = (h->count + 1 <= h->m) ? 0 : (s + 1) % h->m;
   a.s_new = s;
   a.m = h->m;
   a.partials = h->partials;
   a.ticket = h->ticket;
   a.G = h->G;
+  a.status = h->status;
   {
     TraceScope ts(h, SDMD_K_GRAM_ROW, st);
     CK(launch_gram_row(h->dtype, a, st));
@@ -370,6 +372,16 @@ int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t* launches, double* total_m
   *launches = (int64_t)used;
   *total_ms = tot;
   h->tr_used[kernel] = 0;
+  return SDMD_OK;
+}
+
+int sdmd_modes_phase_cycles(sdmd_t h, int64_t* cycles, int32_t count, void* stream) {
+  if (!h || !cycles || count < 1 || count > 16) return fail(SDMD_ERR_ARG, "sdmd_modes_phase_cycles: bad argument");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ModesLayout L = modes_layout(h->m);
+  CK(cudaMemcpyAsync(cycles, h->ws + L.clk, (size_t)count * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return SDMD_OK;
 }
 

@@ -3,21 +3,30 @@
 // snapshot x_j is dotted with the new snapshot x_new; O(n m) work that reads
 // each window byte exactly once, so the kernel is HBM-bound.
 //
-// Decomposition: the n dimension (in bytes, padded to whole 4 KiB units) is
-// split into `nblk` contiguous chunks, one per CTA, about two CTAs per SM.
-// A CTA stages its chunk of x_new in shared memory 16 KiB at a time; each of
-// its 8 warps streams whole slots (warp w takes slots w, w+8, ...) with
-// 16-byte loads, 8 in flight per lane, and reduces each slot's sub-chunk with
-// warp shuffles into a per-CTA accumulator. The per-CTA partials go to a
-// small [slot][CTA] array; the last CTA to finish (atomic ticket, no waiting)
-// sums them in a fixed order and writes row and column `s_new` of G.
+// Decomposition: the n dimension (bytes, padded to whole 4 KiB units) is cut
+// into `nblk` contiguous chunks, one CTA per SM. A CTA walks its chunk in
+// sub-chunks of up to 32 KiB: thread 0 brings the sub-chunk of x_new into
+// shared memory with one bulk copy (TMA, cp.async.bulk), then each of the 8
+// warps streams its slots (warp w takes slots w, w+8, ...) in 4 KiB pieces
+// through its own 4-stage shared-memory ring: lane 0 issues cp.async.bulk
+// copies that complete on one mbarrier per stage, the lanes wait on the
+// barrier, consume the piece (16 bytes per lane per step) and hand the stage
+// back. That keeps 128 KiB of loads in flight per SM without register
+// pressure. Each slot's sub-chunk sum is reduced with warp shuffles into a
+// per-CTA accumulator; the per-CTA partials go to a [slot][CTA] array and the
+// last CTA to finish (atomic ticket, no waiting) sums them in a fixed order
+// and writes row and column `s_new` of G.
 //
-//  - uint8: __dp4a (4 u8 x u8 products summed into u32). A lane sums at most
-//    16 KiB / 32 = 512 products (< 255^2 * 512 < 2^32) before the value goes
-//    to int64, so the result is exact and independent of order.
-//  - float32: four FP32 FMA chains of 8 products per step per lane, then the
-//    step's sum is added in FP64; the cross-lane / cross-CTA sums are FP64 in
-//    a fixed order, so results are deterministic for a given schedule.
+//  - uint8: __dp4a (4 u8 x u8 products into u32). A lane sums at most
+//    32 KiB / 32 = 1024 products (< 2^32 / 255^2) before the value goes to
+//    int64, so the result is exact and independent of order.
+//  - float32: four FP32 FMA chains of 8 products per piece per lane, then the
+//    piece's sum is added in FP64; cross-lane and cross-CTA sums are FP64 in a
+//    fixed order, so results are deterministic for a given schedule.
+//
+// Every mbarrier wait is bounded (about one second of SM clock); on expiry
+// the kernel raises kDevTimeout in the handle's status word, stops issuing
+// copies, waits (bounded) for the copies it has in flight, and finishes.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -26,6 +35,11 @@
 namespace sdmd {
 
 namespace {
+
+constexpr int kStages = 4;
+constexpr int kPiece = 4096;                       // bytes per bulk copy
+constexpr int kXSub = 32768;                       // x_new bytes staged per sub-chunk
+constexpr long long kWaitCycles = 2000000000LL;    // ~1 s at 2 GHz
 
 __device__ __forceinline__ long long warp_sum(long long v) {
 #pragma unroll
@@ -39,33 +53,75 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Stage `len` bytes (multiple of 16) of x_new into shared memory.
-__device__ __forceinline__ void stage_xnew(uint8_t* xs, const uint8_t* src, int len) {
-  for (int o = threadIdx.x * 16; o < len; o += blockDim.x * 16)
-    *reinterpret_cast<uint4*>(xs + o) = __ldcg(reinterpret_cast<const uint4*>(src + o));
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Last CTA: fixed-order sums of the per-CTA partials, symmetric insert into G.
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity` of barrier `bar`; false on expiry.
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  if (mbar_try(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+struct Smem {
+  uint8_t stage[kGrWarps][kStages][kPiece];   // per-warp piece rings
+  uint8_t xs[kXSub];                          // x_new sub-chunk
+  unsigned long long bar[kGrWarps][kStages];  // one mbarrier per stage
+  unsigned long long xbar;                    // x_new barrier
+  long long acc_i[SDMD_MAX_M];
+  double acc_d[SDMD_MAX_M];
+  int last;
+};
+
 template <typename Acc>
-__device__ void finish_row(const GramRowArgs& a) {
-  __shared__ bool last;
+__device__ void finish_row(const GramRowArgs& a, Smem& sm) {
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int t = atomicAdd(a.ticket, 1u);
-    last = (t == (unsigned int)a.nblk - 1u);
+    sm.last = (t == (unsigned int)a.nblk - 1u);
   }
   __syncthreads();
-  if (!last) return;
+  if (!sm.last) return;
   __threadfence();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const Acc* P = static_cast<const Acc*>(a.partials);
   Acc* G = static_cast<Acc*>(a.G);
-  for (int j = warp; j < a.c; j += kGrWarps) {
+  for (int jj = warp; jj < a.c; jj += kGrWarps) {
     Acc s = 0;
-    for (int b = lane; b < a.nblk; b += 32) s += __ldcg(P + (int64_t)j * a.nblk + b);
+    for (int b = lane; b < a.nblk; b += 32) s += __ldcg(P + (int64_t)jj * a.nblk + b);
     s = warp_sum(s);
     if (lane == 0) {
+      const int j = (a.s_first + jj) % a.m;
       G[(int64_t)a.s_new * a.m + j] = s;
       G[(int64_t)j * a.m + a.s_new] = s;
     }
@@ -73,106 +129,163 @@ __device__ void finish_row(const GramRowArgs& a) {
   if (threadIdx.x == 0) *a.ticket = 0u;  // ready for the next launch
 }
 
-__global__ void __launch_bounds__(kGrThreads)
-gram_row_u8_kernel(GramRowArgs a) {
-  __shared__ __align__(16) uint8_t xs[kGrSub];
-  __shared__ long long acc[SDMD_MAX_M];
+template <bool kU8>
+__global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t beg = (int64_t)blockIdx.x * a.chunk;
   const int64_t end = min(beg + a.chunk, a.slot_bytes);
-  for (int j = threadIdx.x; j < a.c; j += blockDim.x) acc[j] = 0;
-  const uint8_t* xnew = a.ring + (int64_t)a.s_new * a.slot_bytes;
-  for (int64_t sub = beg; sub < end; sub += kGrSub) {
-    const int len = (int)min((int64_t)kGrSub, end - sub);   // multiple of kGrStep
-    __syncthreads();
-    stage_xnew(xs, xnew + sub, len);
-    __syncthreads();
-    for (int j = warp; j < a.c; j += kGrWarps) {
-      const uint8_t* xj = a.ring + (int64_t)j * a.slot_bytes + sub;
-      unsigned int s = 0;
-      for (int o = lane * 16; o < len; o += kGrStep) {
-        uint4 v[kGrUnroll];
-#pragma unroll
-        for (int u = 0; u < kGrUnroll; ++u)
-          v[u] = __ldcs(reinterpret_cast<const uint4*>(xj + o + u * 512));
-#pragma unroll
-        for (int u = 0; u < kGrUnroll; ++u) {
-          const uint4 w = *reinterpret_cast<const uint4*>(xs + o + u * 512);
-          s = __dp4a(v[u].x, w.x, s);
-          s = __dp4a(v[u].y, w.y, s);
-          s = __dp4a(v[u].z, w.z, s);
-          s = __dp4a(v[u].w, w.w, s);
-        }
-      }
-      const long long t = warp_sum((long long)s);
-      if (lane == 0) acc[j] += t;
-    }
+  for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
+    sm.acc_i[j] = 0;
+    sm.acc_d[j] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < kGrWarps; ++w)
+      for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&sm.bar[w][s]), 1);
+    mbar_init(smem_u32(&sm.xbar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
-  long long* P = static_cast<long long*>(a.partials);
-  for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = acc[j];
-  finish_row<long long>(a);
-}
-
-__global__ void __launch_bounds__(kGrThreads)
-gram_row_f32_kernel(GramRowArgs a) {
-  __shared__ __align__(16) uint8_t xs[kGrSub];
-  __shared__ double acc[SDMD_MAX_M];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t beg = (int64_t)blockIdx.x * a.chunk;
-  const int64_t end = min(beg + a.chunk, a.slot_bytes);
-  for (int j = threadIdx.x; j < a.c; j += blockDim.x) acc[j] = 0.0;
   const uint8_t* xnew = a.ring + (int64_t)a.s_new * a.slot_bytes;
-  for (int64_t sub = beg; sub < end; sub += kGrSub) {
-    const int len = (int)min((int64_t)kGrSub, end - sub);
-    __syncthreads();
-    stage_xnew(xs, xnew + sub, len);
-    __syncthreads();
-    for (int j = warp; j < a.c; j += kGrWarps) {
-      const uint8_t* xj = a.ring + (int64_t)j * a.slot_bytes + sub;
-      double s = 0.0;
-      for (int o = lane * 16; o < len; o += kGrStep) {
-        float4 v[kGrUnroll];
-#pragma unroll
-        for (int u = 0; u < kGrUnroll; ++u)
-          v[u] = __ldcs(reinterpret_cast<const float4*>(xj + o + u * 512));
-        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-#pragma unroll
-        for (int u = 0; u < kGrUnroll; ++u) {
-          const float4 w = *reinterpret_cast<const float4*>(xs + o + u * 512);
-          f0 = fmaf(v[u].x, w.x, f0);
-          f1 = fmaf(v[u].y, w.y, f1);
-          f2 = fmaf(v[u].z, w.z, f2);
-          f3 = fmaf(v[u].w, w.w, f3);
-        }
-        s += (double)((f0 + f1) + (f2 + f3));
-      }
-      s = warp_sum(s);
-      if (lane == 0) acc[j] += s;
+  const int nmine = (a.c > warp) ? (a.c - warp + kGrWarps - 1) / kGrWarps : 0;  // slots of this warp
+  unsigned g = 0;                  // pieces this warp has consumed so far (all sub-chunks)
+  bool failed = false;             // a bounded wait expired: stop issuing, drain, finish
+  int sub_i = 0;
+  for (int64_t sub = beg; sub < end; sub += kXSub, ++sub_i) {
+    const int len = (int)min((int64_t)kXSub, end - sub);          // multiple of kPiece
+    const int npieces = len / kPiece;
+    const int nitems = nmine * npieces;
+    const bool live = !failed;     // copies are issued in this sub-chunk only if live
+    __syncthreads();               // xs is free again
+    if (threadIdx.x == 0 && live) {
+      const unsigned xb = smem_u32(&sm.xbar);
+      mbar_expect_tx(xb, (unsigned)len);
+      bulk_g2s(smem_u32(sm.xs), xnew + sub, (unsigned)len, xb);
     }
+    if (lane == 0 && live) {       // prologue: this warp's first kStages pieces
+      for (int it = 0; it < kStages && it < nitems; ++it) {
+        const unsigned s = (g + it) % kStages;
+        const int j = (a.s_first + warp + kGrWarps * (it / npieces)) % a.m;
+        const unsigned b = smem_u32(&sm.bar[warp][s]);
+        mbar_expect_tx(b, kPiece);
+        bulk_g2s(smem_u32(sm.stage[warp][s]),
+                 a.ring + (int64_t)j * a.slot_bytes + sub + (int64_t)kPiece * (it % npieces), kPiece, b);
+      }
+    }
+    int fail_it = -1;              // first item not consumed after a failure
+    if (live && !mbar_wait(smem_u32(&sm.xbar), (unsigned)(sub_i & 1))) failed = true;
+    failed = __any_sync(0xffffffffu, failed);
+    if (live && failed) fail_it = 0;
+    unsigned int su = 0;
+    double sd = 0.0;
+    for (int it = 0; it < nitems; ++it) {
+      const unsigned gi = g + it, s = gi % kStages, par = (gi / kStages) & 1;
+      const int q = it % npieces;
+      bool bad = false;
+      if (!failed && !mbar_wait(smem_u32(&sm.bar[warp][s]), par)) bad = true;
+      if (__any_sync(0xffffffffu, bad) && !failed) {
+        failed = true;
+        fail_it = it;
+      }
+      if (!failed) {
+        const uint8_t* piece = sm.stage[warp][s];
+        const uint8_t* xq = sm.xs + kPiece * q;
+        if constexpr (kU8) {
+#pragma unroll
+          for (int u = 0; u < kPiece / 512; ++u) {
+            const uint4 v = *reinterpret_cast<const uint4*>(piece + 16 * lane + 512 * u);
+            const uint4 w = *reinterpret_cast<const uint4*>(xq + 16 * lane + 512 * u);
+            su = __dp4a(v.x, w.x, su);
+            su = __dp4a(v.y, w.y, su);
+            su = __dp4a(v.z, w.z, su);
+            su = __dp4a(v.w, w.w, su);
+          }
+        } else {
+          float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+#pragma unroll
+          for (int u = 0; u < kPiece / 512; ++u) {
+            const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+            const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+            f0 = fmaf(v.x, w.x, f0);
+            f1 = fmaf(v.y, w.y, f1);
+            f2 = fmaf(v.z, w.z, f2);
+            f3 = fmaf(v.w, w.w, f3);
+          }
+          sd += (double)((f0 + f1) + (f2 + f3));
+        }
+      }
+      __syncwarp();                // all lanes are done reading stage s
+      if (lane == 0 && !failed && it + kStages < nitems) {
+        const int nx = it + kStages;
+        const int j = (a.s_first + warp + kGrWarps * (nx / npieces)) % a.m;
+        const unsigned b = smem_u32(&sm.bar[warp][s]);
+        mbar_expect_tx(b, kPiece);
+        bulk_g2s(smem_u32(sm.stage[warp][s]),
+                 a.ring + (int64_t)j * a.slot_bytes + sub + (int64_t)kPiece * (nx % npieces), kPiece, b);
+      }
+      if (q == npieces - 1) {      // this slot is finished for the sub-chunk
+        const int jj = warp + kGrWarps * (it / npieces);
+        if constexpr (kU8) {
+          const long long t = warp_sum((long long)su);
+          if (lane == 0) sm.acc_i[jj] += t;
+          su = 0;
+        } else {
+          const double t = warp_sum(sd);
+          if (lane == 0) sm.acc_d[jj] += t;
+          sd = 0.0;
+        }
+      }
+    }
+    if (fail_it >= 0) {
+      // copies issued but not consumed are items [fail_it, fail_it + kStages):
+      // wait for each (bounded) before the shared memory is released
+      for (int k = fail_it; k < nitems && k < fail_it + kStages; ++k) {
+        const unsigned gk = g + k;
+        mbar_wait(smem_u32(&sm.bar[warp][gk % kStages]), (gk / kStages) & 1);
+      }
+      mbar_wait(smem_u32(&sm.xbar), (unsigned)(sub_i & 1));
+      if (lane == 0) atomicOr(a.status, kDevTimeout);
+    }
+    g += nitems;
   }
   __syncthreads();
-  double* P = static_cast<double*>(a.partials);
-  for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = acc[j];
-  finish_row<double>(a);
+  if constexpr (kU8) {
+    long long* P = static_cast<long long*>(a.partials);
+    for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = sm.acc_i[j];
+    finish_row<long long>(a, sm);
+  } else {
+    double* P = static_cast<double*>(a.partials);
+    for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = sm.acc_d[j];
+    finish_row<double>(a, sm);
+  }
 }
 
 }  // namespace
 
 void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t* nblk) {
-  const int64_t units = (slot_bytes + kGrStep - 1) / kGrStep;
-  int64_t want = 2LL * (num_sms > 0 ? num_sms : 1);
+  const int64_t units = (slot_bytes + kPiece - 1) / kPiece;
+  int64_t want = (num_sms > 0 ? num_sms : 1);
   if (want > units) want = units;
   const int64_t per = (units + want - 1) / want;     // units per CTA
-  *chunk = per * kGrStep;
+  *chunk = per * kPiece;
   *nblk = (int32_t)((units + per - 1) / per);
 }
 
 cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
+  static bool attr = false;
+  const size_t smem = sizeof(Smem);
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gram_row_bulk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gram_row_bulk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   if (dtype == SDMD_U8)
-    gram_row_u8_kernel<<<a.nblk, kGrThreads, 0, st>>>(a);
+    gram_row_bulk_kernel<true><<<a.nblk, kGrThreads, smem, st>>>(a);
   else
-    gram_row_f32_kernel<<<a.nblk, kGrThreads, 0, st>>>(a);
+    gram_row_bulk_kernel<false><<<a.nblk, kGrThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

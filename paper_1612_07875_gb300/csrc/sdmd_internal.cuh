@@ -15,9 +15,6 @@ constexpr int64_t kSlotAlign = 4096;
 // Gram-row kernel geometry (gram_row.cu).
 constexpr int kGrThreads = 256;
 constexpr int kGrWarps = kGrThreads / 32;
-constexpr int kGrUnroll = 8;                       // 16-byte loads per lane per step
-constexpr int kGrStep = 32 * 16 * kGrUnroll;       // bytes one warp reads per step
-constexpr int kGrSub = 16384;                      // x_new bytes staged in smem
 
 // Device-side status word values (mirrors the public codes).
 constexpr int kDevOk = 0;
@@ -27,14 +24,17 @@ constexpr int kDevTimeout = 2;   // a bounded wait gave up
 struct GramRowArgs {
   const uint8_t* ring;   // slot j starts at ring + j * slot_bytes
   int64_t slot_bytes;    // multiple of kSlotAlign
-  int64_t chunk;         // bytes per CTA, multiple of kGrStep
+  int64_t chunk;         // bytes per CTA, multiple of 4096
   int32_t nblk;          // CTAs; nblk * chunk >= slot_bytes
-  int32_t c;             // resident slots 0..c-1 (after this push)
+  int32_t c;             // resident snapshots (after this push)
+  int32_t s_first;       // physical slot of the oldest resident snapshot;
+                         // the window is slots s_first, s_first+1, ... (mod m)
   int32_t s_new;         // slot holding the new snapshot
   int32_t m;             // G is m x m
   void* partials;        // [nblk][m] per-CTA partial sums (FP64 or int64)
   unsigned int* ticket;  // CTA completion counter, zero between launches
   void* G;               // m x m, double (f32) or int64 (u8), physical slots
+  int* status;           // device status word (kDevTimeout on an expired wait)
 };
 
 // Gram row for one pushed snapshot; launches one kernel on `st`.
@@ -61,7 +61,7 @@ int64_t modes_ws_doubles(int m);
 
 // Offsets (in doubles) of the named arrays inside the modes workspace.
 struct ModesLayout {
-  int64_t A, GXY, HV, d, e, lam, Z, V, Y, At, Hc, Qc, Wc, M, Mf, sig, lamout, tmp, lu;
+  int64_t A, GXY, HV, d, e, lam, Z, V, Y, At, Hc, Qc, Wc, M, Mf, sig, lamout, tmp, lu, clk;
   int64_t total;
 };
 ModesLayout modes_layout(int m);

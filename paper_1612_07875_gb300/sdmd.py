@@ -52,6 +52,7 @@ _SIGNATURES = {
     "sdmd_trace": [_VP, _I32],
     "sdmd_trace_read": [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
     "sdmd_gram_row_static": [_I32, _VP, _I64, _I32, _VP, _I64, _VP, _VP],
+    "sdmd_modes_phase_cycles": [_VP, ctypes.POINTER(_I64), _I32, _VP],
 }
 
 
@@ -160,6 +161,17 @@ def sdmd_trace_read(h, kernel):
     ms = ctypes.c_double()
     _check(lib().sdmd_trace_read(h, int(kernel), ctypes.byref(n), ctypes.byref(ms)), "sdmd_trace_read")
     return n.value, ms.value
+
+
+MODES_PHASES = ["gather", "tridiagonalise", "bisection", "inverse_iteration", "back_transform",
+                "atilde", "eig_atilde", "outputs"]
+
+
+def sdmd_modes_phase_cycles(h, stream=None):
+    """Per-phase SM cycles of the last FP64 modes kernel (dict)."""
+    buf = (_I64 * 9)()
+    _check(lib().sdmd_modes_phase_cycles(h, buf, 9, stream_handle(stream)), "sdmd_modes_phase_cycles")
+    return {name: int(buf[i + 1] - buf[i]) for i, name in enumerate(MODES_PHASES)}
 
 
 SDMD_GRAM_ROW_STATIC_MAX_C = 256
