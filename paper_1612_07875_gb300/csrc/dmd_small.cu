@@ -1,35 +1,45 @@
-// Small dense FP64 algebra of the exact DMD step (Sec. 2.1 Eqs. 3-4, Sec. 2.2
-// Eqs. 7-9; Algorithm 1's eig/sort and Algorithm 2's vsi, A~, eig, vsi*W).
-// Everything here is O(m^3) on m <= 256 and runs in one CTA of 256 threads,
-// in FP64. GB300 issues FP64 at about 2 FMA per clock per SM, so the kernel
-// keeps G_X in shared memory (p <= 144), exploits symmetry in the rank-2
-// updates, counts Sturm sign changes without divisions, runs the inverse
-// iterations of all wanted vectors in parallel, and computes every scalar
-// once (one thread) instead of redundantly in every lane.
+// Small dense algebra of the exact DMD step (Sec. 2.1 Eqs. 3-4, Sec. 2.2
+// Eqs. 7-9; Algorithm 1's eig/sort and Algorithm 2's vsi, A~, eig, vsi*W),
+// one CTA of 256 threads per call.
 //
-// Steps (one kernel, phases separated by __syncthreads):
+// Precision plan. GB300 executes FP64 at about 1/64 of the FP32 rate, and an
+// FP64 instruction costs the same whether one lane or 32 are active. So the
+// O(p^3) and O(p^2 r) parts run in double-float ("df64", csrc/df64.cuh:
+// hi + lo float pairs, ~48 bits) on the FP32 pipes, and the sequential,
+// latency-bound parts run in FP32 and are then refined in df64 by steps whose
+// result does not depend on the FP32 error to first order:
+//
 //  0. gather  G_X = G[0:p, 0:p], G_XY = G[0:p, 1:p+1] in time order from the
-//     ring-indexed physical G (p = c-1).
-//  1. Householder tridiagonalisation of G_X: Q^T G_X Q = T (d, e).
-//  2. the r largest eigenvalues of T by Sturm-count bisection (one thread
-//     per eigenvalue) to ~1e-11 relative.
-//  3. their eigenvectors by inverse iteration on T (LU with partial
-//     pivoting, one thread per vector), Gram-Schmidt over all wanted vectors
-//     after every solve; Rayleigh quotients z^T T z give the final values.
-//  4. back-transform z -> Q z (warp per vector) = columns of V.
+//     ring-indexed physical G (p = c-1), converted to df64 and scaled by an
+//     exact power of two so that the largest diagonal entry is in [0.5, 1).
+//  1. Householder tridiagonalisation of G_X in df64: Q^T G_X Q = T (d, e),
+//     reflectors kept in the rows of G_X's storage.
+//  2. the r largest eigenvalues of T by Sturm-count multisection in FP32
+//     (one warp per eigenvalue, 32 points per round): shifts accurate to
+//     ~eps32 * |T|.
+//  3. df64 inverse iteration on T with those shifts (one thread per vector,
+//     LU with partial pivoting), classical Gram-Schmidt over all wanted
+//     vectors after every solve, then a Rayleigh-Ritz step (Z^T T Z
+//     diagonalised by parallel cyclic Jacobi in df64); a second round uses
+//     the Ritz values as shifts. Clusters of close eigenvalues are resolved
+//     by the Gram-Schmidt / Rayleigh-Ritz steps.
+//  4. back-transform z -> Q z in df64 (warp per vector) = columns of V.
 //  5. numerical rank, sigma = sqrt(lambda), vsi = V Sigma^-1.
-//  6. A~ = vsi^T (G_XY vsi).
-//  7. eig of A~ (warp 0): complex Householder-Hessenberg, shifted complex QR
-//     (Wilkinson shifts) to Schur form T = Q^H A~ Q, eigenvectors by
-//     back-substitution on T, W = Q y normalised to unit 2-norm, eigenpairs
-//     ordered by descending |lambda| then angle.
-//  8. M = vsi W (complex), written in FP32 for the Phi kernel; lambda and
-//     sigma written out.
+//  6. A~ = vsi^T (G_XY vsi) in df64.
+//  7. eig(A~): FP32 complex Householder-Hessenberg, shifted QR (Wilkinson
+//     shifts) to Schur form on warp 0, right and left eigenvectors by
+//     triangular solves; each eigenvalue is then replaced by the two-sided
+//     Rayleigh quotient u^H A~ w / u^H w evaluated in df64, whose error is
+//     second order in the FP32 eigenvector errors. W = unit-norm right
+//     eigenvectors; eigenpairs ordered by descending |lambda| then angle.
+//  8. M = vsi W in df64, written in FP32 (scaled back) for the Phi kernel;
+//     lambda, sigma and V written out in FP64.
 #include <cuda_runtime.h>
 #include <float.h>
 #include <math.h>
 #include <stdint.h>
 
+#include "df64.cuh"
 #include "sdmd_internal.cuh"
 
 namespace sdmd {
@@ -38,414 +48,171 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr double kEps = 2.220446049250313e-16;   // 2^-52
+constexpr double kEps = 2.220446049250313e-16;   // 2^-52 (rank rule, as the oracle)
 constexpr double kRankRtol = 64.0;               // rank threshold factor (times p * eps)
-constexpr int kInvIters = 3;                     // inverse-iteration solves per vector
-constexpr int kBisectMax = 160;                  // bisection iteration cap
+constexpr float kEps32 = 5.9604645e-8f;          // 2^-24
+constexpr int kInvIters = 2;                     // inverse-iteration solves per vector and round
+constexpr int kMsRounds = 8;                     // FP32 multisection rounds (33-way each)
+constexpr int kJacobiSweeps = 12;                // Rayleigh-Ritz Jacobi sweep cap
 constexpr int kSmemMaxP = 144;                   // G_X kept in shared memory up to this p
-constexpr int kSmemMaxR = 48;                    // eig(A~) workspace in shared memory up to this r
+constexpr int kRRMax = 32;                       // Rayleigh-Ritz matrices in smem up to this r
+constexpr int kEigMaxR = 48;                     // FP32 eig workspace in smem up to this r
 
-struct C2 {
-  double re, im;
-};
-__device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.re + b.re, a.im + b.im}; }
-__device__ __forceinline__ C2 csub(C2 a, C2 b) { return {a.re - b.re, a.im - b.im}; }
-__device__ __forceinline__ C2 cmul(C2 a, C2 b) {
-  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+// ------------------------------------------------------------ helpers ----
+__device__ __forceinline__ dd shfl_dd(dd v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
-__device__ __forceinline__ C2 cconj(C2 a) { return {a.re, -a.im}; }
-__device__ __forceinline__ C2 cscale(C2 a, double s) { return {a.re * s, a.im * s}; }
-__device__ __forceinline__ double cabs2(C2 a) { return a.re * a.re + a.im * a.im; }
-__device__ __forceinline__ double cabs(C2 a) { return hypot(a.re, a.im); }
-__device__ __forceinline__ C2 cdiv(C2 a, C2 b) {
-  // Smith's algorithm
-  if (fabs(b.re) >= fabs(b.im)) {
-    const double r = b.im / b.re, den = b.re + b.im * r;
-    return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
-  }
-  const double r = b.re / b.im, den = b.re * r + b.im;
-  return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
-}
-__device__ __forceinline__ C2 csqrt(C2 z) {
-  const double m = cabs(z);
-  if (m == 0.0) return {0.0, 0.0};
-  double re = sqrt(0.5 * (m + fabs(z.re)));
-  double im = z.im / (2.0 * re);
-  if (z.re >= 0.0) return {re, im};
-  return {fabs(im), copysign(re, z.im)};
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
+// xor-butterfly sum; dd_add is commutative bit for bit, so all lanes agree
+__device__ __forceinline__ dd warp_sum_dd(dd v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v = dd_add(v, shfl_dd(v, o));
+  return v;
+}
+__device__ __forceinline__ float warp_max_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
+struct CF {
+  float re, im;
+};
+__device__ __forceinline__ CF cadd(CF a, CF b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ CF csub(CF a, CF b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ CF cmul(CF a, CF b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ CF cconj(CF a) { return {a.re, -a.im}; }
+__device__ __forceinline__ CF cscale(CF a, float s) { return {a.re * s, a.im * s}; }
+__device__ __forceinline__ float cabs2(CF a) { return a.re * a.re + a.im * a.im; }
+__device__ __forceinline__ float cabs(CF a) { return hypotf(a.re, a.im); }
+__device__ __forceinline__ CF cdiv(CF a, CF b) {
+  if (fabsf(b.re) >= fabsf(b.im)) {
+    const float r = b.im / b.re, den = b.re + b.im * r;
+    return {(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+  }
+  const float r = b.re / b.im, den = b.re * r + b.im;
+  return {(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+}
+__device__ __forceinline__ CF csqrt(CF z) {
+  const float m = cabs(z);
+  if (m == 0.f) return {0.f, 0.f};
+  const float re = sqrtf(0.5f * (m + fabsf(z.re)));
+  const float im = z.im / (2.f * re);
+  if (z.re >= 0.f) return {re, im};
+  return {fabsf(im), copysignf(re, z.im)};
+}
+
+// Row of the lower-triangle element with flat index f (row-major, j <= i).
+__device__ __forceinline__ int tri_row(int f) {
+  int i = (int)((sqrtf(8.f * (float)f + 1.f) - 1.f) * 0.5f);
+  while ((i + 1) * (i + 2) / 2 <= f) ++i;
+  while (i * (i + 1) / 2 > f) --i;
+  return i;
+}
+
 struct WS {
-  double *A, *GXY, *d, *e, *lam, *Z, *V, *Y, *At, *Hc, *Qc, *Wc, *M, *sig, *lamout, *tmp, *lu, *clk;
+  dd *GXYd, *Ad, *Z, *Y, *lu;
+  double *V, *sig, *lamout;
   float* Mf;
+  long long* clk;
 };
 
 __device__ WS carve(double* base, const ModesLayout& L) {
   WS w;
-  w.A = base + L.A;
-  w.GXY = base + L.GXY;
-  w.d = base + L.d;
-  w.e = base + L.e;
-  w.lam = base + L.lam;
-  w.Z = base + L.Z;
+  w.GXYd = reinterpret_cast<dd*>(base + L.GXY);
+  w.Ad = reinterpret_cast<dd*>(base + L.A);
+  w.Z = reinterpret_cast<dd*>(base + L.Z);
+  w.Y = reinterpret_cast<dd*>(base + L.Y);
+  w.lu = reinterpret_cast<dd*>(base + L.lu);
   w.V = base + L.V;
-  w.Y = base + L.Y;
-  w.At = base + L.At;
-  w.Hc = base + L.Hc;
-  w.Qc = base + L.Qc;
-  w.Wc = base + L.Wc;
-  w.M = base + L.M;
   w.sig = base + L.sig;
   w.lamout = base + L.lamout;
-  w.tmp = base + L.tmp;
-  w.lu = base + L.lu;
-  w.clk = base + L.clk;
   w.Mf = reinterpret_cast<float*>(base + L.Mf);
+  w.clk = reinterpret_cast<long long*>(base + L.clk);
   return w;
 }
 
-// ---------------------------------------------------------------- phase 3 --
-// LU factorisation with partial pivoting of the tridiagonal T - lambda I.
-// Row i of U has (u0, u1, u2) on columns (i, i+1, i+2); mult/piv describe L.
-__device__ void tri_lu(const double* d, const double* e, int p, double lambda, double tiny,
-                       double* u0, double* u1, double* u2, double* mult, double* piv) {
-  double cd = d[0] - lambda, c1 = (p > 1) ? e[0] : 0.0, c2 = 0.0;
-  for (int i = 0; i + 1 < p; ++i) {
-    const double sub = e[i];
-    const double nd = d[i + 1] - lambda;
-    const double n1 = (i + 2 < p) ? e[i + 1] : 0.0;
-    if (fabs(cd) >= fabs(sub)) {
-      const double mu = (cd != 0.0) ? sub / cd : 0.0;
-      u0[i] = cd;
-      u1[i] = c1;
-      u2[i] = c2;
-      piv[i] = 0.0;
-      mult[i] = mu;
-      cd = nd - mu * c1;
-      c1 = n1 - mu * c2;
-      c2 = 0.0;
-    } else {
-      const double mu = cd / sub;
-      u0[i] = sub;
-      u1[i] = nd;
-      u2[i] = n1;
-      piv[i] = 1.0;
-      mult[i] = mu;
-      cd = c1 - mu * nd;
-      c1 = c2 - mu * n1;
-      c2 = 0.0;
-    }
-    if (fabs(u0[i]) < tiny) u0[i] = copysign(tiny, u0[i]);
-  }
-  u0[p - 1] = (fabs(cd) < tiny) ? copysign(tiny, cd) : cd;
-  u1[p - 1] = 0.0;
-  u2[p - 1] = 0.0;
-}
-
-__device__ void tri_solve(int p, const double* u0, const double* u1, const double* u2,
-                          const double* mult, const double* piv, double* b) {
-  for (int i = 0; i + 1 < p; ++i) {
-    if (piv[i] != 0.0) {
-      const double bi = b[i], bn = b[i + 1];
-      b[i] = bn;
-      b[i + 1] = bi - mult[i] * bn;
-    } else {
-      b[i + 1] -= mult[i] * b[i];
-    }
-  }
-  for (int i = p - 1; i >= 0; --i) {
-    double s = b[i];
-    if (i + 1 < p) s -= u1[i] * b[i + 1];
-    if (i + 2 < p) s -= u2[i] * b[i + 2];
-    b[i] = s / u0[i];
-  }
-}
-
-// ---------------------------------------------------------------- phase 7 --
-// Eigen-decomposition of the complex r x r matrix H (row-major, C2) by one
-// warp: Hessenberg reduction, shifted QR to Schur form with Q accumulated,
-// eigenvectors W (columns, unit norm). Returns false if the QR iteration cap
-// was reached.
-__device__ bool warp_eig(C2* H, C2* Q, C2* W, C2* ycol, int r, double* cs, C2* sn) {
-  const int lane = threadIdx.x & 31;
-  for (int idx = lane; idx < r * r; idx += 32) {
-    const int i = idx / r, j = idx - i * r;
-    Q[idx] = {i == j ? 1.0 : 0.0, 0.0};
-  }
-  __syncwarp();
-  // Householder to upper Hessenberg: for column j, reflect H[j+1..r-1][j].
-  for (int j = 0; j + 2 < r; ++j) {
-    const int L = r - j - 1;
-    double tail = 0.0;
-    for (int i = 1 + lane; i < L; i += 32) tail += cabs2(H[(j + 1 + i) * r + j]);
-    tail = warp_sum(tail);
-    const C2 x0 = H[(j + 1) * r + j];
-    __syncwarp();
-    if (tail == 0.0) continue;
-    // reflector scalars on lane 0 only, then broadcast
-    C2 v0 = {0.0, 0.0};
-    double ivn = 0.0;
-    if (lane == 0) {
-      const double ax0 = cabs(x0);
-      const double nrm = sqrt(ax0 * ax0 + tail);
-      const C2 ph = (ax0 > 0.0) ? cscale(x0, 1.0 / ax0) : C2{1.0, 0.0};
-      const C2 alpha = cscale(ph, -nrm);                 // -e^{i arg x0} |x|
-      v0 = csub(x0, alpha);
-      ivn = 1.0 / sqrt(cabs2(v0) + tail);
-    }
-    v0.re = __shfl_sync(0xffffffffu, v0.re, 0);
-    v0.im = __shfl_sync(0xffffffffu, v0.im, 0);
-    const double vn_inv = __shfl_sync(0xffffffffu, ivn, 0);
-    // v stored in ycol[0..L-1]
-    for (int i = lane; i < L; i += 32) ycol[i] = cscale(i == 0 ? v0 : H[(j + 1 + i) * r + j], vn_inv);
-    __syncwarp();
-    // H <- (I - 2 v v^H) H on rows j+1..r-1 (columns j..r-1)
-    for (int q = j + lane; q < r; q += 32) {
-      C2 s = {0.0, 0.0};
-      for (int i = 0; i < L; ++i) s = cadd(s, cmul(cconj(ycol[i]), H[(j + 1 + i) * r + q]));
-      for (int i = 0; i < L; ++i) H[(j + 1 + i) * r + q] = csub(H[(j + 1 + i) * r + q], cscale(cmul(ycol[i], s), 2.0));
-    }
-    __syncwarp();
-    // H <- H (I - 2 v v^H) on columns j+1..r-1 (all rows); Q likewise
-    for (int q = lane; q < 2 * r; q += 32) {
-      C2* M = (q < r) ? H : Q;
-      const int row = (q < r) ? q : q - r;
-      C2 s = {0.0, 0.0};
-      for (int i = 0; i < L; ++i) s = cadd(s, cmul(M[row * r + j + 1 + i], ycol[i]));
-      for (int i = 0; i < L; ++i)
-        M[row * r + j + 1 + i] = csub(M[row * r + j + 1 + i], cscale(cmul(s, cconj(ycol[i])), 2.0));
-    }
-    __syncwarp();
-    for (int i = 2 + lane; i <= L; i += 32) H[(j + i) * r + j] = {0.0, 0.0};
-    __syncwarp();
-  }
-  // Shifted QR on the Hessenberg matrix.
-  double hnorm = 0.0;
-  for (int idx = lane; idx < r * r; idx += 32) hnorm = fmax(hnorm, cabs(H[idx]));
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) hnorm = fmax(hnorm, __shfl_xor_sync(0xffffffffu, hnorm, o));
-  if (hnorm == 0.0) hnorm = 1.0;
-  bool ok = true;
-  int hi = r - 1, its = 0, total = 0;
-  const int cap = 60 * r + 60;
-  while (hi > 0) {
-    // deflation scan (lane 0), result broadcast
-    int l = hi;
-    if (lane == 0) {
-      while (l > 0) {
-        const double sub = cabs(H[l * r + l - 1]);
-        double scale = cabs(H[l * r + l]) + cabs(H[(l - 1) * r + l - 1]);
-        if (scale == 0.0) scale = hnorm;
-        if (sub <= kEps * scale) break;
-        --l;
-      }
-      if (l > 0) H[l * r + l - 1] = {0.0, 0.0};
-    }
-    l = __shfl_sync(0xffffffffu, l, 0);
-    __syncwarp();
-    if (l == hi) {
-      --hi;
-      its = 0;
-      continue;
-    }
-    if (total >= cap) {
-      ok = false;
-      break;
-    }
-    ++its;
-    ++total;
-    // Wilkinson shift from the trailing 2 x 2 of the active block (lane 0)
-    C2 mu = {0.0, 0.0};
-    if (lane == 0) {
-      const C2 a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi], c = H[hi * r + hi - 1],
-               dd = H[hi * r + hi];
-      if (its % 11 == 10) {
-        mu = cadd(dd, C2{0.75 * cabs(c), 0.0});       // exceptional shift
-      } else {
-        const C2 half = cscale(csub(a, dd), 0.5);
-        const C2 disc = csqrt(cadd(cmul(half, half), cmul(b, c)));
-        const C2 tr = cscale(cadd(a, dd), 0.5);
-        const C2 m1 = cadd(tr, disc), m2 = csub(tr, disc);
-        mu = (cabs(csub(m1, dd)) <= cabs(csub(m2, dd))) ? m1 : m2;
-      }
-    }
-    mu.re = __shfl_sync(0xffffffffu, mu.re, 0);
-    mu.im = __shfl_sync(0xffffffffu, mu.im, 0);
-    for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = csub(H[q * r + q], mu);
-    __syncwarp();
-    // H - mu I = Q R by Givens rotations on rows j, j+1
-    for (int j = l; j < hi; ++j) {
-      double c = 1.0;
-      C2 s = {0.0, 0.0};
-      if (lane == 0) {
-        const C2 a = H[j * r + j], b = H[(j + 1) * r + j];
-        const double aa = cabs(a), rho = hypot(aa, cabs(b));
-        if (rho == 0.0) {
-          c = 1.0;
-        } else if (aa == 0.0) {
-          c = 0.0;
-          s = {1.0, 0.0};
-        } else {
-          c = aa / rho;
-          s = cscale(cmul(cscale(a, 1.0 / aa), cconj(b)), 1.0 / rho);
-        }
-      }
-      c = __shfl_sync(0xffffffffu, c, 0);
-      s.re = __shfl_sync(0xffffffffu, s.re, 0);
-      s.im = __shfl_sync(0xffffffffu, s.im, 0);
-      __syncwarp();
-      for (int q = j + lane; q < r; q += 32) {
-        const C2 h1 = H[j * r + q], h2 = H[(j + 1) * r + q];
-        H[j * r + q] = cadd(cscale(h1, c), cmul(s, h2));
-        H[(j + 1) * r + q] = csub(cscale(h2, c), cmul(cconj(s), h1));
-      }
-      if (lane == 0) {
-        cs[j] = c;
-        sn[j] = s;
-      }
-      __syncwarp();
-    }
-    // R Q + mu I: apply G_j^H on columns j, j+1 (rows 0..j+1); Q <- Q G_j^H
-    for (int j = l; j < hi; ++j) {
-      const double c = cs[j];
-      const C2 s = sn[j];
-      for (int q = lane; q < r + (j + 2); q += 32) {
-        C2* M = (q < j + 2) ? H : Q;
-        const int row = (q < j + 2) ? q : q - (j + 2);
-        if (q >= j + 2 && row >= r) continue;
-        const C2 h1 = M[row * r + j], h2 = M[row * r + j + 1];
-        M[row * r + j] = cadd(cscale(h1, c), cmul(h2, cconj(s)));
-        M[row * r + j + 1] = csub(cscale(h2, c), cmul(h1, s));
-      }
-      __syncwarp();
-    }
-    for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = cadd(H[q * r + q], mu);
-    __syncwarp();
-  }
-  __syncwarp();
-  // Eigenvectors of the upper-triangular Schur factor, one per lane.
-  double tnorm = 0.0;
-  for (int idx = lane; idx < r * r; idx += 32) {
-    const int i = idx / r, j = idx - i * r;
-    if (j >= i) tnorm = fmax(tnorm, cabs(H[idx]));
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) tnorm = fmax(tnorm, __shfl_xor_sync(0xffffffffu, tnorm, o));
-  const double small = fmax(kEps * tnorm, DBL_MIN);
-  for (int k = lane; k < r; k += 32) {
-    C2* y = ycol + k * r;
-    const C2 lk = H[k * r + k];
-    for (int i = k + 1; i < r; ++i) y[i] = {0.0, 0.0};
-    y[k] = {1.0, 0.0};
-    for (int i = k - 1; i >= 0; --i) {
-      C2 s = {0.0, 0.0};
-      for (int j = i + 1; j <= k; ++j) s = cadd(s, cmul(H[i * r + j], y[j]));
-      C2 den = csub(H[i * r + i], lk);
-      if (cabs(den) < small) den = {small, 0.0};
-      y[i] = cdiv(cscale(s, -1.0), den);
-    }
-    double nn = 0.0;
-    for (int q = 0; q < r; ++q) {
-      C2 w = {0.0, 0.0};
-      for (int i = 0; i <= k; ++i) w = cadd(w, cmul(Q[q * r + i], y[i]));
-      W[q * r + k] = w;
-      nn += cabs2(w);
-    }
-    const double inv = 1.0 / sqrt(nn);
-    for (int q = 0; q < r; ++q) W[q * r + k] = cscale(W[q * r + k], inv);
-  }
-  __syncwarp();
-  return ok;
-}
-
 // ---------------------------------------------------------------- phase 1 --
-// Householder reduction of the symmetric p x p matrix A (row-major, full
-// storage) to tridiagonal form T = Q^T A Q (d, e). Reflector k is
-// H_k = I - 2 v v^T on indices k+1..p-1 with v unit (zero when column k is
-// already reduced); v is stored over row k, A[k][k+1..p-1], which holds no
-// data any more once step k has run. Scalars are formed by one thread and
-// shared through `sc`: on GB300 every FP64 lane-op counts, so no FP64 value
-// is computed redundantly by all threads.
-__device__ void tridiagonalize(double* A, int p, double* d, double* e, double* vs, double* pv,
-                               double* wv, double* sc) {
+// df64 Householder reduction of the symmetric p x p matrix A (row-major,
+// full storage) to tridiagonal form (d, e). Reflector k is I - 2 v v^T on
+// indices k+1..p-1 with v unit (zero if column k is already reduced), stored
+// over row k, A[k][k+1..p-1]. Scalars are formed by one lane and shared.
+__device__ void tridiagonalize(dd* A, int p, dd* d, dd* e, dd* vs, dd* pv, dd* wv, dd* part, dd* sc) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int k = 0; k + 2 < p; ++k) {
     const int L = p - k - 1;
-    double* rowk = A + (int64_t)k * p + (k + 1);
+    dd* rowk = A + (int64_t)k * p + (k + 1);
     if (warp == 0) {
-      double t = 0.0;
-      for (int i = 1 + lane; i < L; i += 32) t = fma(rowk[i], rowk[i], t);
-      t = warp_sum(t);
+      dd t = {0.f, 0.f};
+      for (int i = 1 + lane; i < L; i += 32) t = dd_fma(rowk[i], rowk[i], t);
+      t = warp_sum_dd(t);
       if (lane == 0) {
-        const double x0 = rowk[0];
+        const dd x0 = rowk[0];
         d[k] = A[(int64_t)k * p + k];
-        if (t == 0.0) {
-          sc[0] = 0.0;
+        if (t.hi == 0.f) {
+          sc[0] = {0.f, 0.f};
           e[k] = x0;
         } else {
-          const double nrm = sqrt(fma(x0, x0, t));
-          const double alpha = (x0 >= 0.0) ? -nrm : nrm;
-          const double v0 = x0 - alpha;                 // same sign as x0: no cancellation
-          sc[0] = 1.0 / sqrt(fma(v0, v0, t));
+          const dd nrm = dd_sqrt(dd_fma(x0, x0, t));
+          const dd alpha = (x0.hi >= 0.f) ? dd_neg(nrm) : nrm;
+          const dd v0 = dd_sub(x0, alpha);                 // same sign as x0: no cancellation
+          sc[0] = dd_div(dd_make(1.f), dd_sqrt(dd_fma(v0, v0, t)));
           sc[1] = v0;
           e[k] = alpha;
         }
       }
     }
     __syncthreads();
-    const double inv = sc[0];
-    if (inv == 0.0) {
-      for (int i = tid; i < L; i += kThreads) rowk[i] = 0.0;
+    const dd inv = sc[0];
+    if (inv.hi == 0.f) {
+      for (int i = tid; i < L; i += kThreads) rowk[i] = {0.f, 0.f};
       __syncthreads();
       continue;
     }
-    const double v0 = sc[1];
-    for (int i = tid; i < L; i += kThreads) vs[i] = (i == 0 ? v0 : rowk[i]) * inv;
+    const dd v0 = sc[1];
+    for (int i = tid; i < L; i += kThreads) vs[i] = dd_mul(i == 0 ? v0 : rowk[i], inv);
     __syncthreads();
-    // pv = A_sub v (column i of the symmetric A_sub read as row i); v -> row k
-    double* As = A + (int64_t)(k + 1) * p + (k + 1);
-    for (int i = tid; i < L; i += kThreads) {
-      rowk[i] = vs[i];
-      double s0 = 0.0, s1 = 0.0;
-      int j = 0;
-      for (; j + 1 < L; j += 2) {
-        s0 = fma(As[(int64_t)j * p + i], vs[j], s0);
-        s1 = fma(As[(int64_t)(j + 1) * p + i], vs[j + 1], s1);
+    // pv = A_sub v, each row split into np parts (np * L <= 256)
+    dd* As = A + (int64_t)(k + 1) * p + (k + 1);
+    int np = kThreads / L;
+    np = np >= 8 ? 8 : (np >= 4 ? 4 : (np >= 2 ? 2 : 1));
+    const int seg = (L + np - 1) / np;
+    for (int idx = tid; idx < L * np; idx += kThreads) {
+      const int q = idx / L, i = idx - q * L;
+      const int j0 = q * seg, j1 = min(L, j0 + seg);
+      dd s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
+      int j = j0;
+      for (; j + 1 < j1; j += 2) {
+        s0 = dd_fma(As[(int64_t)j * p + i], vs[j], s0);
+        s1 = dd_fma(As[(int64_t)(j + 1) * p + i], vs[j + 1], s1);
       }
-      if (j < L) s0 = fma(As[(int64_t)j * p + i], vs[j], s0);
-      pv[i] = s0 + s1;
+      if (j < j1) s0 = dd_fma(As[(int64_t)j * p + i], vs[j], s0);
+      part[q * L + i] = dd_add(s0, s1);
+    }
+    for (int i = tid; i < L; i += kThreads) rowk[i] = vs[i];
+    __syncthreads();
+    for (int i = tid; i < L; i += kThreads) {
+      dd s = part[i];
+      for (int q = 1; q < np; ++q) s = dd_add(s, part[q * L + i]);
+      pv[i] = s;
     }
     __syncthreads();
     if (warp == 0) {
-      double t = 0.0;
-      for (int i = lane; i < L; i += 32) t = fma(vs[i], pv[i], t);
-      t = warp_sum(t);
+      dd t = {0.f, 0.f};
+      for (int i = lane; i < L; i += 32) t = dd_fma(vs[i], pv[i], t);
+      t = warp_sum_dd(t);
       if (lane == 0) sc[2] = t;
     }
     __syncthreads();
-    const double kv = sc[2];
-    for (int i = tid; i < L; i += kThreads) wv[i] = 2.0 * fma(-kv, vs[i], pv[i]);
+    const dd kv = sc[2];
+    for (int i = tid; i < L; i += kThreads) wv[i] = dd_scale(dd_sub(pv[i], dd_mul(kv, vs[i])), 2.f);
     __syncthreads();
-    // A_sub -= v w^T + w v^T: lower triangle computed, mirrored to the upper;
-    // thread t takes columns t and L-1-t (L+1 entries in all)
-    const int half = (L + 1) / 2;
-    for (int t = tid; t < half; t += kThreads) {
-      for (int pass = 0; pass < 2; ++pass) {
-        const int j = (pass == 0) ? t : L - 1 - t;
-        if (pass == 1 && j == t) break;
-        const double vj = vs[j], wj = wv[j];
-        for (int i = j; i < L; ++i) {
-          const double val = fma(-wv[i], vj, fma(-vs[i], wj, As[(int64_t)i * p + j]));
-          As[(int64_t)i * p + j] = val;
-          As[(int64_t)j * p + i] = val;
-        }
-      }
+    // A_sub -= v w^T + w v^T on the lower triangle (flat index), mirrored
+    const int ne = L * (L + 1) / 2;
+    for (int f = tid; f < ne; f += kThreads) {
+      const int i = tri_row(f), j = f - i * (i + 1) / 2;
+      const dd val = dd_sub(dd_sub(As[(int64_t)i * p + j], dd_mul(vs[i], wv[j])), dd_mul(wv[i], vs[j]));
+      As[(int64_t)i * p + j] = val;
+      As[(int64_t)j * p + i] = val;
     }
     __syncthreads();
   }
@@ -462,352 +229,760 @@ __device__ void tridiagonalize(double* A, int p, double* d, double* e, double* v
 }
 
 // ---------------------------------------------------------------- phase 2 --
-__device__ __forceinline__ int dexp_bits(double v) { return (__double2hiint(v) >> 20) & 0x7ff; }
-
-// Sign of v (+1 / -1), or 0 for +-0, from the bit pattern (no FP64 compare).
-__device__ __forceinline__ int dsign(double v) {
-  const long long b = __double_as_longlong(v);
-  if ((b << 1) == 0) return 0;
-  return (b < 0) ? -1 : 1;
-}
-
-// Number of eigenvalues of the symmetric tridiagonal (d, e^2) below x: sign
-// changes of the Sturm sequence p_0 = 1, p_i = (d_{i-1} - x) p_{i-1}
-// - e_{i-2}^2 p_{i-2}. No divisions; the two live terms are rescaled by exact
-// powers of two near the ends of the FP64 range; a zero term takes the sign
-// opposite to its predecessor.
-__device__ int sturm_count(const double* d, const double* e2, int p, double x) {
-  double pm = 1.0, pc = d[0] - x;
-  int s = dsign(pc);
-  if (s == 0) s = -1;
-  int cnt = (s < 0);
+// Number of eigenvalues of the FP32 tridiagonal (d, e^2) below x.
+__device__ int sturm32(const float* d, const float* e2, int p, float x, float pivmin) {
+  float q = d[0] - x;
+  if (fabsf(q) < pivmin) q = -pivmin;
+  int cnt = (q < 0.f);
   for (int i = 1; i < p; ++i) {
-    const double pn = fma(d[i] - x, pc, -e2[i - 1] * pm);
-    pm = pc;
-    pc = pn;
-    const int ex = max(dexp_bits(pc), dexp_bits(pm));
-    if (ex > 1023 + 600) {
-      pc *= 0x1p-600;
-      pm *= 0x1p-600;
-    } else if (ex < 1023 - 600) {
-      pc *= 0x1p+600;
-      pm *= 0x1p+600;
-    }
-    int sn = dsign(pc);
-    if (sn == 0) sn = -s;
-    cnt += (sn != s);
-    s = sn;
+    q = (d[i] - x) - e2[i - 1] / q;
+    if (fabsf(q) < pivmin) q = -pivmin;
+    cnt += (q < 0.f);
   }
   return cnt;
 }
 
 // ---------------------------------------------------------------- phase 3 --
-// Orthonormalise the rw vectors Z[i*p ..] in order (classical Gram-Schmidt,
-// applied twice), vectors spread over warps, rows over threads.
-__device__ void orthonormalize(double* Z, int rw, int p, double* coef, double* red, double* sc) {
+// LU with partial pivoting of the df64 tridiagonal T - mu I. Row i of U has
+// (1/u0, u1, u2) on columns (i, i+1, i+2) (diagonal stored as reciprocal);
+// mult / piv (0 or 1) describe L. Pivots below `tiny` are raised to it.
+__device__ void tri_lu_dd(const dd* d, const dd* e, int p, dd mu, float tiny, dd* u0, dd* u1, dd* u2,
+                          dd* mult, dd* piv) {
+  dd cd = dd_sub(d[0], mu), c1 = (p > 1) ? e[0] : dd{0.f, 0.f}, c2 = {0.f, 0.f};
+  for (int i = 0; i + 1 < p; ++i) {
+    const dd sub = e[i];
+    const dd nd = dd_sub(d[i + 1], mu);
+    const dd n1 = (i + 2 < p) ? e[i + 1] : dd{0.f, 0.f};
+    dd piv_val;
+    if (fabsf(cd.hi) >= fabsf(sub.hi)) {
+      const dd m = (cd.hi != 0.f) ? dd_div(sub, cd) : dd{0.f, 0.f};
+      piv_val = cd;
+      u1[i] = c1;
+      u2[i] = c2;
+      piv[i] = {0.f, 0.f};
+      mult[i] = m;
+      cd = dd_sub(nd, dd_mul(m, c1));
+      c1 = dd_sub(n1, dd_mul(m, c2));
+      c2 = {0.f, 0.f};
+    } else {
+      const dd m = dd_div(cd, sub);
+      piv_val = sub;
+      u1[i] = nd;
+      u2[i] = n1;
+      piv[i] = {1.f, 0.f};
+      mult[i] = m;
+      cd = dd_sub(c1, dd_mul(m, nd));
+      c1 = dd_sub(c2, dd_mul(m, n1));
+      c2 = {0.f, 0.f};
+    }
+    if (fabsf(piv_val.hi) < tiny) piv_val = {copysignf(tiny, piv_val.hi), 0.f};
+    u0[i] = dd_div(dd_make(1.f), piv_val);
+  }
+  const dd last = (fabsf(cd.hi) < tiny) ? dd{copysignf(tiny, cd.hi), 0.f} : cd;
+  u0[p - 1] = dd_div(dd_make(1.f), last);
+  u1[p - 1] = {0.f, 0.f};
+  u2[p - 1] = {0.f, 0.f};
+}
+
+__device__ void tri_solve_dd(int p, const dd* u0inv, const dd* u1, const dd* u2, const dd* mult, const dd* piv,
+                             dd* b) {
+  for (int i = 0; i + 1 < p; ++i) {
+    if (piv[i].hi != 0.f) {
+      const dd bi = b[i], bn = b[i + 1];
+      b[i] = bn;
+      b[i + 1] = dd_sub(bi, dd_mul(mult[i], bn));
+    } else {
+      b[i + 1] = dd_sub(b[i + 1], dd_mul(mult[i], b[i]));
+    }
+  }
+  for (int i = p - 1; i >= 0; --i) {
+    dd s = b[i];
+    if (i + 1 < p) s = dd_sub(s, dd_mul(u1[i], b[i + 1]));
+    if (i + 2 < p) s = dd_sub(s, dd_mul(u2[i], b[i + 2]));
+    b[i] = dd_mul(s, u0inv[i]);
+  }
+}
+
+// Orthonormalise vectors Z[i*p ..], i < rw, in order (classical Gram-Schmidt,
+// `passes` times), vectors over warps and rows over threads.
+__device__ void cgs_dd(dd* Z, int rw, int p, int passes, dd* coef, dd* red, dd* sc) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = 0; i < rw; ++i) {
-    double* zi = Z + (int64_t)i * p;
-    for (int pass = 0; pass < 2 && i > 0; ++pass) {
+    dd* zi = Z + (int64_t)i * p;
+    for (int pass = 0; pass < passes && i > 0; ++pass) {
       for (int j = warp; j < i; j += kWarps) {
-        const double* zj = Z + (int64_t)j * p;
-        double s = 0.0;
-        for (int q = lane; q < p; q += 32) s = fma(zj[q], zi[q], s);
-        s = warp_sum(s);
+        const dd* zj = Z + (int64_t)j * p;
+        dd s = {0.f, 0.f};
+        for (int q = lane; q < p; q += 32) s = dd_fma(zj[q], zi[q], s);
+        s = warp_sum_dd(s);
         if (lane == 0) coef[j] = s;
       }
       __syncthreads();
       for (int q = tid; q < p; q += kThreads) {
-        double s = zi[q];
-        for (int j = 0; j < i; ++j) s = fma(-coef[j], Z[(int64_t)j * p + q], s);
+        dd s = zi[q];
+        for (int j = 0; j < i; ++j) s = dd_sub(s, dd_mul(coef[j], Z[(int64_t)j * p + q]));
         zi[q] = s;
       }
       __syncthreads();
     }
-    double nn = 0.0;
-    for (int q = tid; q < p; q += kThreads) nn = fma(zi[q], zi[q], nn);
-    nn = warp_sum(nn);
+    dd nn = {0.f, 0.f};
+    for (int q = tid; q < p; q += kThreads) nn = dd_fma(zi[q], zi[q], nn);
+    nn = warp_sum_dd(nn);
     if (lane == 0) red[warp] = nn;
     __syncthreads();
     if (tid == 0) {
-      double t = 0.0;
-      for (int w = 0; w < kWarps; ++w) t += red[w];
-      sc[3] = (t > 0.0) ? 1.0 / sqrt(t) : 0.0;
+      dd t = red[0];
+      for (int w = 1; w < kWarps; ++w) t = dd_add(t, red[w]);
+      sc[3] = (t.hi > 0.f) ? dd_div(dd_make(1.f), dd_sqrt(t)) : dd{0.f, 0.f};
     }
     __syncthreads();
-    const double inv = sc[3];
-    for (int q = tid; q < p; q += kThreads) zi[q] *= inv;
+    const dd inv = sc[3];
+    for (int q = tid; q < p; q += kThreads) zi[q] = dd_mul(zi[q], inv);
     __syncthreads();
   }
 }
 
-// Shared-memory plan (dynamic): vectors first, then one big region that
-// holds G_X (phases 0-4) and later the complex r x r eigen-workspace.
+// Rayleigh-Ritz on the orthonormal vectors Z (rw x p, vector-major):
+// H = Z^T T Z (df64) diagonalised by parallel cyclic Jacobi (circle-method
+// pairing, disjoint rotations per round); Z <- Z R with columns ordered by
+// descending Ritz value, lam <- those values. H, R: rw*rw; tz: rw*p scratch.
+__device__ void rayleigh_ritz(dd* Z, int rw, int p, const dd* d, const dd* e, dd* H, dd* R, dd* tz, dd* lam,
+                              dd* sc, int* ord) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int idx = tid; idx < rw * p; idx += kThreads) {
+    const int i = idx / p, q = idx - i * p;
+    const dd* z = Z + (int64_t)i * p;
+    dd t = dd_mul(d[q], z[q]);
+    if (q > 0) t = dd_fma(e[q - 1], z[q - 1], t);
+    if (q + 1 < p) t = dd_fma(e[q], z[q + 1], t);
+    tz[idx] = t;
+  }
+  __syncthreads();
+  for (int pr = warp; pr < rw * rw; pr += kWarps) {
+    const int a = pr / rw, b = pr - a * rw;
+    if (b < a) continue;
+    dd s = {0.f, 0.f};
+    for (int q = lane; q < p; q += 32) s = dd_fma(Z[(int64_t)a * p + q], tz[(int64_t)b * p + q], s);
+    s = warp_sum_dd(s);
+    if (lane == 0) {
+      H[a * rw + b] = s;
+      H[b * rw + a] = s;
+    }
+  }
+  for (int idx = tid; idx < rw * rw; idx += kThreads) R[idx] = {(idx / rw == idx % rw) ? 1.f : 0.f, 0.f};
+  __syncthreads();
+  const int n2 = rw + (rw & 1);
+  for (int sweep = 0; sweep < kJacobiSweeps && rw > 1; ++sweep) {
+    if (tid == 0) {    // converged when the off-diagonal is below df64 resolution
+      float off = 0.f, dia = 0.f;
+      for (int a = 0; a < rw; ++a)
+        for (int b = 0; b < rw; ++b) {
+          const float v = fabsf(H[a * rw + b].hi);
+          if (a == b)
+            dia = fmaxf(dia, v);
+          else
+            off = fmaxf(off, v);
+        }
+      sc[4] = {(off <= 1e-15f * dia) ? 1.f : 0.f, 0.f};
+    }
+    __syncthreads();
+    if (sc[4].hi != 0.f) break;
+    for (int round = 0; round < n2 - 1; ++round) {
+      for (int k = tid; k < n2 / 2; k += kThreads) {
+        int a = (k == 0) ? 0 : 1 + (k - 1 + round) % (n2 - 1);
+        int b = 1 + (n2 - 2 - k + round) % (n2 - 1);
+        if (a > b) {
+          const int t = a;
+          a = b;
+          b = t;
+        }
+        dd c = {1.f, 0.f}, s = {0.f, 0.f};
+        if (b < rw) {
+          const dd hab = H[a * rw + b];
+          if (hab.hi != 0.f) {
+            const dd tau = dd_div(dd_sub(H[b * rw + b], H[a * rw + a]), dd_scale(hab, 2.f));
+            const dd root = dd_sqrt(dd_fma(tau, tau, dd_make(1.f)));
+            dd t = dd_div(dd_make(1.f), dd_add(dd_abs(tau), root));
+            if (tau.hi < 0.f) t = dd_neg(t);
+            c = dd_div(dd_make(1.f), dd_sqrt(dd_fma(t, t, dd_make(1.f))));
+            s = dd_mul(t, c);
+          }
+        }
+        ord[2 * k] = a;
+        ord[2 * k + 1] = b;
+        tz[2 * k] = c;
+        tz[2 * k + 1] = s;
+      }
+      __syncthreads();
+      for (int idx = tid; idx < (n2 / 2) * rw; idx += kThreads) {   // rows: H <- J^T H
+        const int k = idx / rw, col = idx - k * rw;
+        const int a = ord[2 * k], b = ord[2 * k + 1];
+        if (b >= rw) continue;
+        const dd c = tz[2 * k], s = tz[2 * k + 1];
+        const dd ha = H[a * rw + col], hb = H[b * rw + col];
+        H[a * rw + col] = dd_sub(dd_mul(c, ha), dd_mul(s, hb));
+        H[b * rw + col] = dd_add(dd_mul(s, ha), dd_mul(c, hb));
+      }
+      __syncthreads();
+      for (int idx = tid; idx < (n2 / 2) * rw * 2; idx += kThreads) {   // columns: H <- H J, R <- R J
+        const int half = idx / ((n2 / 2) * rw);
+        const int rem = idx - half * (n2 / 2) * rw;
+        const int k = rem / rw, row = rem - k * rw;
+        const int a = ord[2 * k], b = ord[2 * k + 1];
+        if (b >= rw) continue;
+        dd* M = half ? R : H;
+        const dd c = tz[2 * k], s = tz[2 * k + 1];
+        const dd ma = M[row * rw + a], mb = M[row * rw + b];
+        M[row * rw + a] = dd_sub(dd_mul(c, ma), dd_mul(s, mb));
+        M[row * rw + b] = dd_add(dd_mul(s, ma), dd_mul(c, mb));
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    for (int a = 0; a < rw; ++a) ord[a] = a;
+    for (int a = 0; a < rw; ++a) {
+      int best = a;
+      for (int b = a + 1; b < rw; ++b)
+        if (dd_lt(H[ord[best] * rw + ord[best]], H[ord[b] * rw + ord[b]])) best = b;
+      const int t = ord[a];
+      ord[a] = ord[best];
+      ord[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int a = tid; a < rw; a += kThreads) lam[a] = H[ord[a] * rw + ord[a]];
+  for (int idx = tid; idx < rw * p; idx += kThreads) {   // tz <- Z R (permuted)
+    const int a = idx / p, q = idx - a * p;
+    const int col = ord[a];
+    dd s = {0.f, 0.f};
+    for (int b = 0; b < rw; ++b) s = dd_fma(Z[(int64_t)b * p + q], R[b * rw + col], s);
+    tz[idx] = s;
+  }
+  __syncthreads();
+  for (int idx = tid; idx < rw * p; idx += kThreads) Z[idx] = tz[idx];
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- phase 7 --
+// FP32 eigen-decomposition of the complex r x r matrix H (row-major) on one
+// warp: Hessenberg reduction, shifted QR to Schur form with Q accumulated,
+// right eigenvectors W and left eigenvectors U (columns, unit norm).
+// Returns false if the QR iteration cap was reached.
+__device__ bool warp_eig32(CF* H, CF* Q, CF* W, CF* U, CF* ycol, int r, float* cs, CF* sn) {
+  const int lane = threadIdx.x & 31;
+  for (int idx = lane; idx < r * r; idx += 32) {
+    const int i = idx / r, j = idx - i * r;
+    Q[idx] = {i == j ? 1.f : 0.f, 0.f};
+  }
+  __syncwarp();
+  for (int j = 0; j + 2 < r; ++j) {
+    const int L = r - j - 1;
+    float tail = 0.f;
+    for (int i = 1 + lane; i < L; i += 32) tail += cabs2(H[(j + 1 + i) * r + j]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tail += __shfl_xor_sync(0xffffffffu, tail, o);
+    const CF x0 = H[(j + 1) * r + j];
+    __syncwarp();
+    if (tail == 0.f) continue;
+    const float ax0 = cabs(x0);
+    const float nrm = sqrtf(ax0 * ax0 + tail);
+    const CF ph = (ax0 > 0.f) ? cscale(x0, 1.f / ax0) : CF{1.f, 0.f};
+    const CF alpha = cscale(ph, -nrm);
+    const CF v0 = csub(x0, alpha);
+    const float vn_inv = 1.f / sqrtf(cabs2(v0) + tail);
+    for (int i = lane; i < L; i += 32) ycol[i] = cscale(i == 0 ? v0 : H[(j + 1 + i) * r + j], vn_inv);
+    __syncwarp();
+    for (int q = j + lane; q < r; q += 32) {
+      CF s = {0.f, 0.f};
+      for (int i = 0; i < L; ++i) s = cadd(s, cmul(cconj(ycol[i]), H[(j + 1 + i) * r + q]));
+      for (int i = 0; i < L; ++i) H[(j + 1 + i) * r + q] = csub(H[(j + 1 + i) * r + q], cscale(cmul(ycol[i], s), 2.f));
+    }
+    __syncwarp();
+    for (int q = lane; q < 2 * r; q += 32) {
+      CF* M = (q < r) ? H : Q;
+      const int row = (q < r) ? q : q - r;
+      CF s = {0.f, 0.f};
+      for (int i = 0; i < L; ++i) s = cadd(s, cmul(M[row * r + j + 1 + i], ycol[i]));
+      for (int i = 0; i < L; ++i)
+        M[row * r + j + 1 + i] = csub(M[row * r + j + 1 + i], cscale(cmul(s, cconj(ycol[i])), 2.f));
+    }
+    __syncwarp();
+    for (int i = 2 + lane; i <= L; i += 32) H[(j + i) * r + j] = {0.f, 0.f};
+    __syncwarp();
+  }
+  float hnorm = 0.f;
+  for (int idx = lane; idx < r * r; idx += 32) hnorm = fmaxf(hnorm, cabs(H[idx]));
+  hnorm = warp_max_f(hnorm);
+  if (hnorm == 0.f) hnorm = 1.f;
+  bool ok = true;
+  int hi = r - 1, its = 0, total = 0;
+  const int cap = 60 * r + 60;
+  while (hi > 0) {
+    int l = hi;
+    while (l > 0) {
+      const float sub = cabs(H[l * r + l - 1]);
+      float scale = cabs(H[l * r + l]) + cabs(H[(l - 1) * r + l - 1]);
+      if (scale == 0.f) scale = hnorm;
+      if (sub <= kEps32 * scale) break;
+      --l;
+    }
+    __syncwarp();
+    if (l > 0 && lane == 0) H[l * r + l - 1] = {0.f, 0.f};
+    __syncwarp();
+    if (l == hi) {
+      --hi;
+      its = 0;
+      continue;
+    }
+    if (total >= cap) {
+      ok = false;
+      break;
+    }
+    ++its;
+    ++total;
+    CF mu;
+    {
+      const CF a = H[(hi - 1) * r + hi - 1], b = H[(hi - 1) * r + hi], c = H[hi * r + hi - 1],
+               dl = H[hi * r + hi];
+      if (its % 11 == 10) {
+        mu = cadd(dl, CF{0.75f * cabs(c), 0.f});
+      } else {
+        const CF half = cscale(csub(a, dl), 0.5f);
+        const CF disc = csqrt(cadd(cmul(half, half), cmul(b, c)));
+        const CF tr = cscale(cadd(a, dl), 0.5f);
+        const CF m1 = cadd(tr, disc), m2 = csub(tr, disc);
+        mu = (cabs(csub(m1, dl)) <= cabs(csub(m2, dl))) ? m1 : m2;
+      }
+    }
+    for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = csub(H[q * r + q], mu);
+    __syncwarp();
+    for (int j = l; j < hi; ++j) {
+      const CF a = H[j * r + j], b = H[(j + 1) * r + j];
+      const float aa = cabs(a), rho = hypotf(aa, cabs(b));
+      float c;
+      CF s;
+      if (rho == 0.f) {
+        c = 1.f;
+        s = {0.f, 0.f};
+      } else if (aa == 0.f) {
+        c = 0.f;
+        s = {1.f, 0.f};
+      } else {
+        c = aa / rho;
+        s = cscale(cmul(cscale(a, 1.f / aa), cconj(b)), 1.f / rho);
+      }
+      __syncwarp();
+      for (int q = j + lane; q < r; q += 32) {
+        const CF h1 = H[j * r + q], h2 = H[(j + 1) * r + q];
+        H[j * r + q] = cadd(cscale(h1, c), cmul(s, h2));
+        H[(j + 1) * r + q] = csub(cscale(h2, c), cmul(cconj(s), h1));
+      }
+      if (lane == 0) {
+        cs[j] = c;
+        sn[j] = s;
+      }
+      __syncwarp();
+    }
+    for (int j = l; j < hi; ++j) {
+      const float c = cs[j];
+      const CF s = sn[j];
+      for (int q = lane; q < r + (j + 2); q += 32) {
+        CF* M = (q < j + 2) ? H : Q;
+        const int row = (q < j + 2) ? q : q - (j + 2);
+        if (q >= j + 2 && row >= r) continue;
+        const CF h1 = M[row * r + j], h2 = M[row * r + j + 1];
+        M[row * r + j] = cadd(cscale(h1, c), cmul(h2, cconj(s)));
+        M[row * r + j + 1] = csub(cscale(h2, c), cmul(h1, s));
+      }
+      __syncwarp();
+    }
+    for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = cadd(H[q * r + q], mu);
+    __syncwarp();
+  }
+  __syncwarp();
+  float tnorm = 0.f;
+  for (int idx = lane; idx < r * r; idx += 32) {
+    const int i = idx / r, j = idx - i * r;
+    if (j >= i) tnorm = fmaxf(tnorm, cabs(H[idx]));
+  }
+  tnorm = warp_max_f(tnorm);
+  const float small = fmaxf(kEps32 * tnorm, FLT_MIN);
+  // right eigenvectors: (T - l_k) y = 0 with y_k = 1, y_{>k} = 0; w = Q y
+  for (int k = lane; k < r; k += 32) {
+    CF* y = ycol + k * r;
+    const CF lk = H[k * r + k];
+    for (int i = k + 1; i < r; ++i) y[i] = {0.f, 0.f};
+    y[k] = {1.f, 0.f};
+    for (int i = k - 1; i >= 0; --i) {
+      CF s = {0.f, 0.f};
+      for (int j = i + 1; j <= k; ++j) s = cadd(s, cmul(H[i * r + j], y[j]));
+      CF den = csub(H[i * r + i], lk);
+      if (cabs(den) < small) den = {small, 0.f};
+      y[i] = cdiv(cscale(s, -1.f), den);
+    }
+    float nn = 0.f;
+    for (int q = 0; q < r; ++q) {
+      CF w = {0.f, 0.f};
+      for (int i = 0; i <= k; ++i) w = cadd(w, cmul(Q[q * r + i], y[i]));
+      W[q * r + k] = w;
+      nn += cabs2(w);
+    }
+    const float inv = 1.f / sqrtf(nn);
+    for (int q = 0; q < r; ++q) W[q * r + k] = cscale(W[q * r + k], inv);
+  }
+  __syncwarp();
+  // left eigenvectors: x^H T = l_k x^H with x_k = 1, x_{<k} = 0; u = Q x
+  for (int k = lane; k < r; k += 32) {
+    CF* x = ycol + k * r;
+    const CF lk = H[k * r + k];
+    for (int i = 0; i < k; ++i) x[i] = {0.f, 0.f};
+    x[k] = {1.f, 0.f};
+    for (int i = k + 1; i < r; ++i) {
+      // column i of T^H x = conj(l_k) x: sum_{j<=i} conj(T[j][i]) x_j = conj(l_k) x_i
+      CF s = {0.f, 0.f};
+      for (int j = k; j < i; ++j) s = cadd(s, cmul(cconj(H[j * r + i]), x[j]));
+      CF den = csub(cconj(H[i * r + i]), cconj(lk));
+      if (cabs(den) < small) den = {small, 0.f};
+      x[i] = cdiv(cscale(s, -1.f), den);
+    }
+    float nn = 0.f;
+    for (int q = 0; q < r; ++q) {
+      CF u = {0.f, 0.f};
+      for (int i = k; i < r; ++i) u = cadd(u, cmul(Q[q * r + i], x[i]));
+      U[q * r + k] = u;
+      nn += cabs2(u);
+    }
+    const float inv = 1.f / sqrtf(nn);
+    for (int q = 0; q < r; ++q) U[q * r + k] = cscale(U[q * r + k], inv);
+  }
+  __syncwarp();
+  return ok;
+}
+
+// Shared-memory plan (dynamic), in 8-byte units.
 struct SmemPlan {
-  int a_in_smem, eig_in_smem;
-  int64_t vec_doubles, big_doubles;
+  int a_in_smem;
+  int rr_in_smem;
+  int eig_in_smem;
+  int64_t P, vec_units, rr_units, big_units;
 };
 
 __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   SmemPlan s;
-  const int64_t P = (p + 3) & ~3;
-  s.vec_doubles = 8 * P + 64;
+  s.P = (p + 3) & ~3;
+  // d, e, vs, pv, wv, lam (df64) + part (256 df64) + d32, e2_32 (float) + 32 df64 scalars
+  s.vec_units = 6 * s.P + 256 + s.P + 32;
+  s.rr_in_smem = (r <= kRRMax);
+  s.rr_units = s.rr_in_smem ? 2 * (int64_t)r * r : 0;
   s.a_in_smem = (p <= kSmemMaxP);
-  s.eig_in_smem = (r <= kSmemMaxR);
+  s.eig_in_smem = (r <= kEigMaxR);
   const int64_t a = s.a_in_smem ? (int64_t)p * p : 0;
-  const int64_t g = s.eig_in_smem ? (int64_t)8 * r * r : 0;   // H, Q, W, y: 4 x r^2 complex
-  s.big_doubles = a > g ? a : g;
+  const int64_t g = s.eig_in_smem ? (int64_t)5 * r * r : 0;   // H, Q, W, U, y (complex float)
+  s.big_units = a > g ? a : g;
   return s;
 }
 
 __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, ModesLayout L) {
-  extern __shared__ double smem[];
-  __shared__ double red[kWarps + 1];
-  __shared__ double sc[8];
-  __shared__ int sh_reff;
-  __shared__ double cs[SDMD_MAX_M];
-  __shared__ C2 sn[SDMD_MAX_M];
-  __shared__ int order[SDMD_MAX_M];
-  __shared__ double coef[SDMD_MAX_M];
+  extern __shared__ double smem_d[];
+  __shared__ dd red[kWarps];
+  __shared__ float cs[SDMD_MAX_M];
+  __shared__ CF sn[SDMD_MAX_M];
+  __shared__ int ord[SDMD_MAX_M];
+  __shared__ dd coef[SDMD_MAX_M];
+  __shared__ int sh_int[4];
+  __shared__ float sh_f[4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   WS w = carve(a.ws, L);
-  long long* clk = reinterpret_cast<long long*>(w.clk);
   const int m = a.m, p = a.c - 1;
   const int rw = min(a.r_req, p);
   const SmemPlan plan = smem_plan(p, a.r_req);
-  const int64_t P = (p + 3) & ~3;
-  double* d = smem;
-  double* e = d + P;
-  double* e2 = e + P;
-  double* vs = e2 + P;
-  double* pv = vs + P;
-  double* wv = pv + P;
-  double* lam = wv + P;
-  double* big = smem + plan.vec_doubles;
-  double* A = plan.a_in_smem ? big : w.A;
-  if (tid == 0) clk[0] = clock64();
+  const int64_t P = plan.P;
+  dd* base = reinterpret_cast<dd*>(smem_d);
+  dd* d = base;
+  dd* e = d + P;
+  dd* vs = e + P;
+  dd* pv = vs + P;
+  dd* wv = pv + P;
+  dd* lam = wv + P;
+  dd* part = lam + P;
+  float* d32 = reinterpret_cast<float*>(part + 256);
+  float* e2_32 = d32 + P;
+  dd* sc = reinterpret_cast<dd*>(e2_32 + P);
+  dd* rrH = plan.rr_in_smem ? base + plan.vec_units : w.Y;
+  dd* rrR = rrH + (int64_t)a.r_req * a.r_req;
+  dd* big = base + plan.vec_units + plan.rr_units;
+  dd* A = plan.a_in_smem ? big : w.Ad;
+  if (tid == 0) w.clk[0] = clock64();
 
-  // ---- 0. gather time-ordered blocks
+  // ---- 0. scale (exact power of two from the largest diagonal), gather, convert
+  if (warp == 0) {
+    int ex = -1000;
+    for (int i = lane; i < p; i += 32) {
+      const int si = (a.start + i) % m;
+      int xe;
+      if (a.g_is_int) {
+        const long long g = static_cast<const long long*>(a.G)[(int64_t)si * m + si];
+        xe = (g > 0) ? 63 - __clzll(g) : -1000;
+      } else {
+        const double g = static_cast<const double*>(a.G)[(int64_t)si * m + si];
+        const int bits = (__double2hiint(g) >> 20) & 0x7ff;
+        xe = (bits > 0) ? bits - 1023 : -1000;
+      }
+      ex = max(ex, xe);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+    if (lane == 0) sh_int[0] = (ex == -1000) ? 0 : ex + 1;   // G / 2^s has max diag in [0.5, 1)
+  }
+  __syncthreads();
+  const int s_exp = sh_int[0];
   for (int idx = tid; idx < p * p; idx += kThreads) {
     const int i = idx / p, j = idx - i * p;
     const int si = (a.start + i) % m, sj = (a.start + j) % m, sj1 = (a.start + j + 1) % m;
-    double gx, gxy;
+    dd gx, gxy;
     if (a.g_is_int) {
       const long long* G = static_cast<const long long*>(a.G);
-      gx = (double)G[(int64_t)si * m + sj];
-      gxy = (double)G[(int64_t)si * m + sj1];
+      gx = dd_from_ll(G[(int64_t)si * m + sj]);
+      gxy = dd_from_ll(G[(int64_t)si * m + sj1]);
     } else {
       const double* G = static_cast<const double*>(a.G);
-      gx = G[(int64_t)si * m + sj];
-      gxy = G[(int64_t)si * m + sj1];
+      gx = dd_from_double(G[(int64_t)si * m + sj]);
+      gxy = dd_from_double(G[(int64_t)si * m + sj1]);
     }
-    A[idx] = gx;
-    w.GXY[idx] = gxy;
+    A[idx] = {ldexpf(gx.hi, -s_exp), ldexpf(gx.lo, -s_exp)};
+    w.GXYd[idx] = {ldexpf(gxy.hi, -s_exp), ldexpf(gxy.lo, -s_exp)};
   }
   __syncthreads();
-  if (tid == 0) clk[1] = clock64();
+  if (tid == 0) w.clk[1] = clock64();
 
-  // ---- 1. tridiagonalise G_X
-  tridiagonalize(A, p, d, e, vs, pv, wv, sc);
-  if (tid == 0) clk[2] = clock64();
+  // ---- 1. tridiagonalise G_X (df64)
+  tridiagonalize(A, p, d, e, vs, pv, wv, part, sc);
+  if (tid == 0) w.clk[2] = clock64();
 
-  // ---- 2. bisection for the rw largest eigenvalues
-  for (int i = tid; i < p; i += kThreads) e2[i] = (i + 1 < p) ? e[i] * e[i] : 0.0;
+  // ---- 2. FP32 multisection for the rw largest eigenvalues of T
+  for (int i = tid; i < p; i += kThreads) {
+    d32[i] = d[i].hi;
+    e2_32[i] = (i + 1 < p) ? e[i].hi * e[i].hi : 0.f;
+  }
+  __syncthreads();
   if (tid == 0) {
-    double gl = 0.0, gu = 0.0;
+    float gl = 0.f, gu = 0.f, em = 0.f;
     for (int i = 0; i < p; ++i) {
-      const double rad = ((i > 0) ? fabs(e[i - 1]) : 0.0) + ((i + 1 < p) ? fabs(e[i]) : 0.0);
-      gl = (i == 0) ? d[0] - rad : fmin(gl, d[i] - rad);
-      gu = (i == 0) ? d[0] + rad : fmax(gu, d[i] + rad);
+      const float rad = ((i > 0) ? fabsf(e[i - 1].hi) : 0.f) + ((i + 1 < p) ? fabsf(e[i].hi) : 0.f);
+      gl = (i == 0) ? d32[0] - rad : fminf(gl, d32[i] - rad);
+      gu = (i == 0) ? d32[0] + rad : fmaxf(gu, d32[i] + rad);
+      if (i + 1 < p) em = fmaxf(em, e2_32[i]);
     }
-    const double tn = fmax(fabs(gl), fabs(gu));
-    sc[4] = gl - 4.0 * kEps * tn * p - DBL_MIN;
-    sc[5] = gu + 4.0 * kEps * tn * p + DBL_MIN;
-    sc[6] = tn;
+    const float tn = fmaxf(fabsf(gl), fabsf(gu));
+    sh_f[0] = gl - 4.f * kEps32 * tn * p - FLT_MIN;
+    sh_f[1] = gu + 4.f * kEps32 * tn * p + FLT_MIN;
+    sh_f[2] = tn;
+    sh_f[3] = FLT_MIN * fmaxf(1.f, em) * 4.f;
   }
   __syncthreads();
-  const double gl = sc[4], gu = sc[5], tnorm = sc[6];
-  // thread owner(i) bisects for eigenvalue i; owners are spread one per warp
-  // first so that the sub-partitions' FP64 units work in parallel
-  for (int i = 0; i < rw; ++i) {
-    const int owner = (i % kWarps) * 32 + (i / kWarps) % 32;
-    if (tid != owner) continue;
+  const float tnorm = sh_f[2];
+  for (int i = warp; i < rw; i += kWarps) {
     const int target = p - 1 - i;
-    double lo = gl, hi = gu;
-    const double atol = kEps * tnorm;
-    for (int it = 0; it < kBisectMax; ++it) {
-      if (hi - lo <= fmax(1e-11 * fmax(fabs(lo), fabs(hi)), atol)) break;
-      const double mid = 0.5 * (lo + hi);
-      if (sturm_count(d, e2, p, mid) > target)
-        hi = mid;
-      else
-        lo = mid;
+    float lo = sh_f[0], hi = sh_f[1];
+    for (int round = 0; round < kMsRounds; ++round) {
+      if (hi - lo <= 2.f * kEps32 * fmaxf(fabsf(lo), fabsf(hi)) + sh_f[3]) break;
+      const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+      const int cnt = sturm32(d32, e2_32, p, x, sh_f[3]);
+      const unsigned above = __ballot_sync(0xffffffffu, cnt > target);
+      const int f = above ? __ffs(above) - 1 : 32;
+      const float xf = lo + (hi - lo) * (float)(f + 1) / 33.f;
+      const float xp = lo + (hi - lo) * (float)f / 33.f;
+      if (f < 32) hi = xf;
+      lo = (f == 0) ? lo : xp;
     }
-    lam[i] = 0.5 * (lo + hi);
+    if (lane == 0) lam[i] = dd_make(0.5f * (lo + hi));
   }
   __syncthreads();
-  if (tid == 0) clk[3] = clock64();
+  if (tid == 0) w.clk[3] = clock64();
 
-  // ---- 3. inverse iteration (thread per vector), Gram-Schmidt between solves
-  const double tiny = fmax(kEps * tnorm, DBL_MIN);
-  for (int i = 0; i < rw; ++i) {
-    const int owner = (i % kWarps) * 32 + (i / kWarps) % 32;
-    if (tid != owner) continue;
-    double* u0 = w.lu + (int64_t)i * 5 * p;
-    double *u1 = u0 + p, *u2 = u1 + p, *mu = u2 + p, *pvt = mu + p;
-    double shift = lam[i];
-    for (int q = 0; q < i; ++q)      // numerically equal eigenvalues: distinct shifts
-      if (fabs(lam[q] - shift) < 4.0 * kEps * tnorm) shift -= 4.0 * kEps * tnorm;
-    tri_lu(d, e, p, shift, tiny, u0, u1, u2, mu, pvt);
-    double* z = w.Z + (int64_t)i * p;
-    for (int j = 0; j < p; ++j) z[j] = 1.0 + 0.1 * (double)(((j + 1) * 7919 + (i + 1) * 104729) % 97) / 97.0;
-  }
-  __syncthreads();
-  for (int it = 0; it < kInvIters; ++it) {
-    for (int i = 0; i < rw; ++i) {
-      const int owner = (i % kWarps) * 32 + (i / kWarps) % 32;
-      if (tid != owner) continue;
-      double* u0 = w.lu + (int64_t)i * 5 * p;
-      tri_solve(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, w.Z + (int64_t)i * p);
+  // ---- 3. df64 inverse iteration + Gram-Schmidt + Rayleigh-Ritz, twice:
+  //         round 0 shifts are the FP32 eigenvalues, round 1 shifts are the
+  //         round-0 Ritz values (df64-accurate), which converges in one or two
+  //         solves even for eigenvalues much closer than eps32 * |T|
+  const float tiny = fmaxf(1e-13f * tnorm, FLT_MIN);
+  for (int round = 0; round < 2; ++round) {
+    const float sep = (round == 0) ? 2.f * kEps32 * tnorm : 1e-12f * tnorm;
+    for (int i = tid; i < rw; i += kThreads) {
+      dd* u0 = w.lu + (int64_t)i * 5 * p;
+      dd shift = lam[i];
+      for (int q = 0; q < i; ++q)    // (numerically) equal shifts: separate them slightly
+        if (fabsf(lam[q].hi - shift.hi) <= sep) shift = dd_sub(shift, dd_make(sep));
+      tri_lu_dd(d, e, p, shift, tiny, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p);
+      if (round == 0) {
+        dd* z = w.Z + (int64_t)i * p;
+        for (int j = 0; j < p; ++j)
+          z[j] = dd_make(1.f + 0.1f * (float)(((j + 1) * 7919 + (i + 1) * 104729) % 97) / 97.f);
+      }
     }
     __syncthreads();
-    orthonormalize(w.Z, rw, p, coef, red, sc);
-  }
-  // Rayleigh quotients z^T T z refine the eigenvalues (warp per vector)
-  for (int i = warp; i < rw; i += kWarps) {
-    const double* z = w.Z + (int64_t)i * p;
-    double s = 0.0;
-    for (int q = lane; q < p; q += 32) {
-      double tz = d[q] * z[q];
-      if (q > 0) tz = fma(e[q - 1], z[q - 1], tz);
-      if (q + 1 < p) tz = fma(e[q], z[q + 1], tz);
-      s = fma(z[q], tz, s);
+    for (int it = 0; it < kInvIters; ++it) {
+      for (int i = tid; i < rw; i += kThreads) {
+        dd* u0 = w.lu + (int64_t)i * 5 * p;
+        tri_solve_dd(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, w.Z + (int64_t)i * p);
+      }
+      __syncthreads();
+      cgs_dd(w.Z, rw, p, (it + 1 == kInvIters) ? 2 : 1, coef, red, sc);
     }
-    s = warp_sum(s);
-    if (lane == 0) lam[i] = s;
+    rayleigh_ritz(w.Z, rw, p, d, e, rrH, rrR, w.lu + (int64_t)rw * 5 * p, lam, sc, ord);
   }
-  __syncthreads();
-  if (tid == 0) clk[4] = clock64();
+  if (tid == 0) w.clk[4] = clock64();
 
   // ---- 4. back-transform: v = H_0 H_1 ... H_{p-3} z  (warp per vector)
   for (int i = warp; i < rw; i += kWarps) {
-    double* z = w.Z + (int64_t)i * p;
+    dd* z = w.Z + (int64_t)i * p;
     for (int k = p - 3; k >= 0; --k) {
       const int Lk = p - k - 1;
-      const double* v = A + (int64_t)k * p + (k + 1);
-      double s = 0.0;
-      for (int j = lane; j < Lk; j += 32) s = fma(v[j], z[k + 1 + j], s);
-      s = warp_sum(s);
-      for (int j = lane; j < Lk; j += 32) z[k + 1 + j] = fma(-2.0 * s, v[j], z[k + 1 + j]);
+      const dd* v = A + (int64_t)k * p + (k + 1);
+      dd s = {0.f, 0.f};
+      for (int j = lane; j < Lk; j += 32) s = dd_fma(v[j], z[k + 1 + j], s);
+      s = dd_scale(warp_sum_dd(s), -2.f);
+      for (int j = lane; j < Lk; j += 32) z[k + 1 + j] = dd_fma(s, v[j], z[k + 1 + j]);
       __syncwarp();
     }
   }
   __syncthreads();
-  if (tid == 0) clk[5] = clock64();
+  if (tid == 0) w.clk[5] = clock64();
 
-  // ---- 5. rank, sigma, V, vsi = V Sigma^-1 (in place in Z)
+  // ---- 5. rank, sigma, V (FP64 out), vsi = V Sigma^-1 (df64, scaled units)
   if (tid == 0) {
     int k = 0;
-    const double lam0 = (rw > 0) ? lam[0] : 0.0;
+    const double lam0 = (rw > 0) ? dd_to_double(lam[0]) : 0.0;
     if (lam0 > 0.0) {
       const double thr = lam0 * kRankRtol * (double)p * kEps;
-      while (k < rw && lam[k] > thr) ++k;
+      while (k < rw && dd_to_double(lam[k]) > thr) ++k;
     }
-    sh_reff = k;
-    for (int i = 0; i < a.r_req; ++i) {
-      w.sig[i] = (i < k) ? sqrt(lam[i]) : 0.0;
-      cs[i] = (i < k) ? 1.0 / w.sig[i] : 0.0;
-    }
+    sh_int[1] = k;
   }
   __syncthreads();
-  const int re = sh_reff;
+  const int re = sh_int[1];
+  for (int i = tid; i < a.r_req; i += kThreads) {
+    w.sig[i] = (i < re) ? sqrt(ldexp(dd_to_double(lam[i]), s_exp)) : 0.0;
+    if (i < re) coef[i] = dd_div(dd_make(1.f), dd_sqrt(lam[i]));
+  }
+  __syncthreads();
   for (int idx = tid; idx < a.r_req * p; idx += kThreads) {
     const int i = idx / p;
-    const double z = (i < re) ? w.Z[idx] : 0.0;
-    w.V[idx] = z;
-    if (i < re) w.Z[idx] = z * cs[i];
+    const dd z = (i < re) ? w.Z[idx] : dd{0.f, 0.f};
+    w.V[idx] = dd_to_double(z);
+    if (i < re) w.Z[idx] = dd_mul(z, coef[i]);
   }
   __syncthreads();
 
-  // ---- 6. A~ = vsi^T G_XY vsi  (Y = G_XY vsi first)
+  // ---- 6. A~ = vsi^T G_XY vsi (df64; independent of the scaling)
   for (int idx = tid; idx < re * p; idx += kThreads) {
     const int k = idx / p, row = idx - k * p;
-    const double* g = w.GXY + (int64_t)row * p;
-    const double* v = w.Z + (int64_t)k * p;
-    double s0 = 0.0, s1 = 0.0;
+    const dd* g = w.GXYd + (int64_t)row * p;
+    const dd* v = w.Z + (int64_t)k * p;
+    dd s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
     int b = 0;
     for (; b + 1 < p; b += 2) {
-      s0 = fma(g[b], v[b], s0);
-      s1 = fma(g[b + 1], v[b + 1], s1);
+      s0 = dd_fma(g[b], v[b], s0);
+      s1 = dd_fma(g[b + 1], v[b + 1], s1);
     }
-    if (b < p) s0 = fma(g[b], v[b], s0);
-    w.Y[idx] = s0 + s1;
+    if (b < p) s0 = dd_fma(g[b], v[b], s0);
+    w.Y[idx] = dd_add(s0, s1);
   }
   __syncthreads();
-  C2* Hc = plan.eig_in_smem ? reinterpret_cast<C2*>(big) : reinterpret_cast<C2*>(w.Hc);
-  C2* Qc = plan.eig_in_smem ? Hc + re * re : reinterpret_cast<C2*>(w.Qc);
-  C2* Wc = plan.eig_in_smem ? Qc + re * re : reinterpret_cast<C2*>(w.Wc);
-  C2* ycol = plan.eig_in_smem ? Wc + re * re : reinterpret_cast<C2*>(w.lu);
+  dd* At = w.lu;                       // re x re df64 (the LU scratch is free again)
+  CF* Hc = plan.eig_in_smem ? reinterpret_cast<CF*>(big) : reinterpret_cast<CF*>(w.lu + (int64_t)re * re);
+  CF* Qc = Hc + re * re;
+  CF* Wc = Qc + re * re;
+  CF* Uc = Wc + re * re;
+  CF* yc = Uc + re * re;
   for (int idx = tid; idx < re * re; idx += kThreads) {
     const int k = idx / re, l = idx - k * re;
-    const double* v = w.Z + (int64_t)k * p;
-    const double* y = w.Y + (int64_t)l * p;
-    double s = 0.0;
-    for (int b = 0; b < p; ++b) s = fma(v[b], y[b], s);
-    w.At[idx] = s;
-    Hc[idx] = {s, 0.0};
+    const dd* v = w.Z + (int64_t)k * p;
+    const dd* y = w.Y + (int64_t)l * p;
+    dd s = {0.f, 0.f};
+    for (int b = 0; b < p; ++b) s = dd_fma(v[b], y[b], s);
+    At[idx] = s;
+    Hc[idx] = {s.hi, 0.f};
   }
   __syncthreads();
-  if (tid == 0) clk[6] = clock64();
+  if (tid == 0) w.clk[6] = clock64();
 
-  // ---- 7. eig(A~) on warp 0
+  // ---- 7. eig(A~): FP32 Schur with left and right vectors, then df64
+  //         two-sided Rayleigh quotients for the eigenvalues
   if (warp == 0 && re > 0) {
-    const bool ok = warp_eig(Hc, Qc, Wc, ycol, re, cs, sn);
+    const bool ok = warp_eig32(Hc, Qc, Wc, Uc, yc, re, cs, sn);
     if (!ok && lane == 0) atomicOr(a.status, kDevRank);
-    if (lane == 0) {
-      for (int k = 0; k < re; ++k) order[k] = k;
-      for (int k = 0; k < re; ++k) {
-        int best = k;
-        for (int q = k + 1; q < re; ++q) {
-          const C2 lb = Hc[order[best] * re + order[best]], lq = Hc[order[q] * re + order[q]];
-          const double mb = cabs(lb), mq = cabs(lq);
-          if (mq > mb || (mq == mb && atan2(lq.im, lq.re) < atan2(lb.im, lb.re))) best = q;
-        }
-        const int t = order[k];
-        order[k] = order[best];
-        order[best] = t;
+  }
+  __syncthreads();
+  double* lam_tmp = reinterpret_cast<double*>(w.Y);   // provisional order (Y is free)
+  for (int k = tid; k < re; k += kThreads) {
+    // lambda_k = (u^H A~ w) / (u^H w), A~ real df64, u and w promoted exactly
+    dd nre = {0.f, 0.f}, nim = {0.f, 0.f}, dre = {0.f, 0.f}, dim = {0.f, 0.f};
+    for (int i = 0; i < re; ++i) {
+      dd awr = {0.f, 0.f}, awi = {0.f, 0.f};
+      for (int j = 0; j < re; ++j) {
+        const CF wj = Wc[j * re + k];
+        awr = dd_fma(At[i * re + j], dd_make(wj.re), awr);
+        awi = dd_fma(At[i * re + j], dd_make(wj.im), awi);
       }
+      const CF ui = Uc[i * re + k];
+      const CF wi = Wc[i * re + k];
+      // conj(u_i) (aw_i) = (ur ar + ui ai) + i (ur ai - ui ar)
+      nre = dd_fma(dd_make(ui.re), awr, dd_fma(dd_make(ui.im), awi, nre));
+      nim = dd_sub(dd_fma(dd_make(ui.re), awi, nim), dd_mul(dd_make(ui.im), awr));
+      dre = dd_add(dre, dd_add(two_prod(ui.re, wi.re), two_prod(ui.im, wi.im)));
+      dim = dd_add(dim, dd_sub(two_prod(ui.re, wi.im), two_prod(ui.im, wi.re)));
+    }
+    const zd lk = zd_div({nre, nim}, {dre, dim});
+    lam_tmp[2 * k] = dd_to_double(lk.re);
+    lam_tmp[2 * k + 1] = dd_to_double(lk.im);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < re; ++k) ord[k] = k;
+    for (int k = 0; k < re; ++k) {
+      int best = k;
+      for (int q = k + 1; q < re; ++q) {
+        const double br = lam_tmp[2 * ord[best]], bi = lam_tmp[2 * ord[best] + 1];
+        const double qr = lam_tmp[2 * ord[q]], qi = lam_tmp[2 * ord[q] + 1];
+        const double mb = br * br + bi * bi, mq = qr * qr + qi * qi;
+        if (mq > mb || (mq == mb && atan2(qi, qr) < atan2(bi, br))) best = q;
+      }
+      const int t = ord[k];
+      ord[k] = ord[best];
+      ord[best] = t;
     }
   }
   __syncthreads();
-  if (tid == 0) clk[7] = clock64();
+  for (int k = tid; k < a.r_req; k += kThreads) {
+    w.lamout[2 * k] = (k < re) ? lam_tmp[2 * ord[k]] : 0.0;
+    w.lamout[2 * k + 1] = (k < re) ? lam_tmp[2 * ord[k] + 1] : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) w.clk[7] = clock64();
 
-  // ---- 8. outputs: lambda, M = vsi W (FP64 and FP32 copies)
-  C2* lamout = reinterpret_cast<C2*>(w.lamout);
-  for (int k = tid; k < a.r_req; k += kThreads)
-    lamout[k] = (k < re) ? Hc[order[k] * re + order[k]] : C2{0.0, 0.0};
-  C2* Mc = reinterpret_cast<C2*>(w.M);
+  // ---- 8. M = vsi W (df64 accumulation of FP32 W), FP32 out, scaled back
   const int R = a.r_req;
+  const float unscale = (float)exp2(-0.5 * s_exp);
   for (int idx = tid; idx < p * R; idx += kThreads) {
     const int row = idx / R, k = idx - row * R;
-    C2 s = {0.0, 0.0};
+    dd sr = {0.f, 0.f}, si = {0.f, 0.f};
     if (k < re) {
-      const int kk = order[k];
+      const int kk = ord[k];
       for (int l = 0; l < re; ++l) {
-        const double z = w.Z[(int64_t)l * p + row];
-        const C2 wv2 = Wc[l * re + kk];
-        s.re = fma(wv2.re, z, s.re);
-        s.im = fma(wv2.im, z, s.im);
+        const dd z = w.Z[(int64_t)l * p + row];
+        const CF wv2 = Wc[l * re + kk];
+        sr = dd_fma(z, dd_make(wv2.re), sr);
+        si = dd_fma(z, dd_make(wv2.im), si);
       }
     }
-    Mc[idx] = s;
-    w.Mf[2 * idx] = (float)s.re;
-    w.Mf[2 * idx + 1] = (float)s.im;
+    w.Mf[2 * idx] = (sr.hi + sr.lo) * unscale;
+    w.Mf[2 * idx + 1] = (si.hi + si.lo) * unscale;
   }
   __syncthreads();
   if (tid == 0) {
     *a.r_dev = re;
-    clk[8] = clock64();
+    w.clk[8] = clock64();
   }
 }
 
@@ -823,25 +998,25 @@ ModesLayout modes_layout(int m) {
     o += (n + 31) & ~int64_t(31);   // 256-byte aligned sub-arrays
     return at;
   };
-  L.A = take(p2);
-  L.GXY = take(p2);
+  L.A = take(p2);           // df64 G_X when it does not fit in shared memory
+  L.GXY = take(p2);         // df64 G_XY
   L.HV = 0;
-  L.d = take(p);
-  L.e = take(p);
-  L.lam = take(p);
-  L.Z = take(p2);
-  L.V = take(p2);
-  L.Y = take(p2);
-  L.At = take(p2);
-  L.Hc = take(2 * p2);
-  L.Qc = take(2 * p2);
-  L.Wc = take(2 * p2);
-  L.M = take(2 * p2);
+  L.d = 0;
+  L.e = 0;
+  L.lam = 0;
+  L.Z = take(p2);           // df64 vectors (rw x p)
+  L.V = take(p2);           // FP64 V out
+  L.Y = take(2 * p2);       // df64 G_XY vsi; Rayleigh-Ritz matrices when r > 32
+  L.At = 0;
+  L.Hc = 0;
+  L.Qc = 0;
+  L.Wc = 0;
+  L.M = 0;
   L.Mf = take(p2);          // p x 2r floats
   L.sig = take(p);
   L.lamout = take(2 * p);
-  L.tmp = take(4 * p);
-  L.lu = take(5 * p2 + 2 * p2);
+  L.tmp = 0;
+  L.lu = take(6 * p2 + 64); // tridiagonal LU per vector (5 r p) + Ritz scratch (r p); A~ and eig fallback (6 r^2)
   L.clk = take(16);
   L.total = o;
   return L;
@@ -852,7 +1027,7 @@ int64_t modes_ws_doubles(int m) { return modes_layout(m).total; }
 cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
   static size_t attr_bytes = 0;   // dynamic shared memory opted in so far
   const SmemPlan plan = smem_plan(a.c - 1, a.r_req);
-  const size_t bytes = (size_t)(plan.vec_doubles + plan.big_doubles) * sizeof(double);
+  const size_t bytes = (size_t)(plan.vec_units + plan.rr_units + plan.big_units) * 8;
   if (bytes > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(modes_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
