@@ -56,8 +56,11 @@ typedef struct sdmd_s *sdmd_t;
 
 /* Snapshot element types. */
 enum {
-    SDMD_F32 = 0, /* dense float32 snapshots; G accumulated in FP64          */
-    SDMD_U8 = 1   /* dense uint8 (e.g. video pixels); G exact in int64       */
+    SDMD_F32 = 0,        /* dense float32 snapshots; G accumulated in FP64      */
+    SDMD_U8 = 1,         /* dense uint8 (e.g. video pixels); G exact in int64   */
+    SDMD_C64 = 2,        /* dense complex64 (interleaved re, im); G complex128  */
+    SDMD_C64_SPARSE = 3  /* sparse complex64 coefficients of an orthonormal
+                            transform (sdmd_create_sparse); G complex128      */
 };
 
 /* Status codes. */
@@ -81,7 +84,7 @@ enum {
  *   m      window length: number of resident snapshots, 2 <= m <= SDMD_MAX_M.
  *          G is m x m; DMD uses the c-1 snapshot pairs of the c <= m resident
  *          snapshots (X = oldest c-1, X' = newest c-1; Algorithm 2).
- *   dtype  SDMD_F32 or SDMD_U8.
+ *   dtype  SDMD_F32, SDMD_U8 or SDMD_C64 (sparse handles: sdmd_create_sparse).
  *   out    receives the handle (host pointer).
  * Device memory: m * round_up(n * sizeof(elem), 4096) bytes of ring plus
  * O(m^2) of G and workspaces. Ring padding is zero and never written, so
@@ -89,6 +92,20 @@ enum {
  * allocation fails (nothing is leaked). Synchronous.
  */
 SDMD_API int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t *out);
+
+/*
+ * sdmd_create_sparse -- allocate a streaming window of Fourier-sparse
+ * snapshots (Sec. 3.5: the SVD and DMD are invariant under unitary
+ * transforms, so the coefficients of an orthonormal FFT give the Gram of the
+ * physical fields by Parseval's identity).
+ *   n        length of the dense coefficient vector (e.g. 1024 * 1024),
+ *            1 <= n < 2^31.
+ *   m        window length, 2 <= m <= SDMD_MAX_M.
+ *   nnz_max  largest number of nonzero coefficients of one snapshot.
+ * Device memory: m * nnz_max * 12 bytes of ring, an n * 12-byte lookup
+ * table, and O(m^2) for G (complex128). Synchronous.
+ */
+SDMD_API int sdmd_create_sparse(int64_t n, int32_t m, int32_t nnz_max, sdmd_t *out);
 
 /* sdmd_destroy -- wait for the handle's device work and free it. NULL is OK. */
 SDMD_API int sdmd_destroy(sdmd_t h);
@@ -106,6 +123,21 @@ SDMD_API int sdmd_destroy(sdmd_t h);
  */
 SDMD_API int sdmd_push(sdmd_t h, const void *x, void *stream);
 
+/*
+ * sdmd_push_sparse -- append one sparse snapshot (sparse handles only).
+ *   nnz   number of coefficients, 0 <= nnz <= nnz_max.
+ *   idx   nnz distinct int32 indices in [0, n) (host or device pointer).
+ *   vals  nnz complex64 values (interleaved re, im floats), same order.
+ * Computes g_j = sum over indices present in both of conj(x_j[k]) x_new[k]
+ * for every resident snapshot j (Sec. 3.1, Eq. 12b on the coefficients),
+ * products in FP32 and sums in FP64 in a fixed order, and writes row and
+ * column `head` of the Hermitian G. Host index arrays are checked (range,
+ * strictly increasing) and rejected with SDMD_ERR_ARG; device index arrays
+ * are range-checked by the kernel, which skips offending entries and makes
+ * sdmd_status report SDMD_ERR_ARG.
+ */
+SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const void *vals, void *stream);
+
 /* sdmd_count -- number of snapshots pushed so far (host pointer). Host-side
  * bookkeeping only; does not touch the device. */
 SDMD_API int sdmd_count(sdmd_t h, int64_t *count);
@@ -113,7 +145,9 @@ SDMD_API int sdmd_count(sdmd_t h, int64_t *count);
 /*
  * sdmd_gram -- copy the window's Gram in time order (test and inspection
  * hook). G receives c x c row-major values, c = min(count, m), oldest
- * snapshot first: double for SDMD_F32, int64_t for SDMD_U8.
+ * snapshot first: double for SDMD_F32, int64_t for SDMD_U8, complex128
+ * (interleaved re, im doubles; G[i][j] = <x_i, x_j> = x_i^H x_j) for the
+ * complex handles.
  */
 SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
 
@@ -135,7 +169,8 @@ SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
  *           |lambda| then by angle; entries beyond the kept rank are zero.
  *   r_out   receives the kept rank (int32), or NULL.
  * phi must be device memory (SDMD_ERR_ARG otherwise); lambda and r_out may
- * be device or host memory. Needs c >= 3 snapshots (else
+ * be device or host memory. Complex handles (SDMD_C64, SDMD_C64_SPARSE)
+ * return SDMD_ERR_UNSUPPORTED: they provide the streaming Gram only. Needs c >= 3 snapshots (else
  * SDMD_ERR_NOT_READY). The eigensolvers have iteration caps; if one is
  * reached the call still completes and sdmd_status reports SDMD_ERR_RANK.
  */
@@ -152,8 +187,9 @@ SDMD_API int sdmd_svd(sdmd_t h, int32_t r, double *sigma, double *V, void *strea
 
 /*
  * sdmd_status -- waits for `stream`, then reports the device-side status
- * word of the handle (SDMD_OK, or SDMD_ERR_RANK / SDMD_ERR_TIMEOUT raised by
- * a kernel since the last sdmd_status call) and clears it.
+ * word of the handle (SDMD_OK, or SDMD_ERR_RANK / SDMD_ERR_TIMEOUT /
+ * SDMD_ERR_ARG (sparse index out of range) raised by a kernel since the last
+ * sdmd_status call) and clears it.
  */
 SDMD_API int sdmd_status(sdmd_t h, void *stream);
 

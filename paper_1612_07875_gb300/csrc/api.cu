@@ -37,6 +37,15 @@ struct sdmd_s {
   int32_t head = 0;
   int32_t last_r = 0;         // r of the last sdmd_modes call (0 = none)
   int32_t last_p = 0;
+  int64_t gsz = 8;            // bytes per G entry (16 for complex handles)
+  // sparse handles
+  int32_t nnz_max = 0;
+  int* idx_ring = nullptr;    // m x nnz_max indices
+  float2* val_ring = nullptr; // m x nnz_max complex64 values
+  int* tag = nullptr;         // n lookup tags
+  float2* tval = nullptr;     // n lookup values
+  int stamp = 0;
+  std::vector<int> nnz;       // entries per physical slot
   // tracing: per kernel class, event pairs recorded since the last read
   bool trace = false;
   std::vector<cudaEvent_t> tr_ev[SDMD_K_COUNT];
@@ -111,11 +120,13 @@ int copy_out(void* dst, const void* src_dev, size_t bytes, cudaStream_t st) {
   return SDMD_OK;
 }
 
-__global__ void gather_gram_kernel(const uint64_t* G, int m, int c, int start, uint64_t* out) {
+// Time-ordered copy of the physical G; `words` 8-byte words per entry.
+__global__ void gather_gram_kernel(const uint64_t* G, int m, int c, int start, int words, uint64_t* out) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= c * c) return;
   const int i = idx / c, j = idx - i * c;
-  out[idx] = G[(int64_t)((start + i) % m) * m + (start + j) % m];
+  const int64_t src = (int64_t)((start + i) % m) * m + (start + j) % m;
+  for (int q = 0; q < words; ++q) out[(int64_t)idx * words + q] = G[src * words + q];
 }
 
 // Brackets one enqueued operation with a pair of events when tracing is on.
@@ -144,7 +155,15 @@ struct TraceScope {
   }
 };
 
+void free_sparse(sdmd_s* h) {
+  cudaFree(h->idx_ring);
+  cudaFree(h->val_ring);
+  cudaFree(h->tag);
+  cudaFree(h->tval);
+}
+
 void free_all(sdmd_s* h) {
+  free_sparse(h);
   for (int k = 0; k < SDMD_K_COUNT; ++k)
     for (cudaEvent_t e : h->tr_ev[k]) cudaEventDestroy(e);
   cudaFree(h->ring);
@@ -176,7 +195,8 @@ int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) {
   *out = nullptr;
   if (n < 1 || n > (int64_t(1) << 34)) return fail(SDMD_ERR_ARG, "sdmd_create: n=%lld out of range", (long long)n);
   if (m < 2 || m > SDMD_MAX_M) return fail(SDMD_ERR_ARG, "sdmd_create: m=%d not in [2, %d]", m, SDMD_MAX_M);
-  if (dtype != SDMD_F32 && dtype != SDMD_U8) return fail(SDMD_ERR_ARG, "sdmd_create: dtype %d unknown", dtype);
+  if (dtype != SDMD_F32 && dtype != SDMD_U8 && dtype != SDMD_C64)
+    return fail(SDMD_ERR_ARG, "sdmd_create: dtype %d unknown (sparse handles: sdmd_create_sparse)", dtype);
   sdmd_s* h = new (std::nothrow) sdmd_s();
   if (!h) return fail(SDMD_ERR_OOM, "sdmd_create: host allocation failed");
   CK(cudaGetDevice(&h->device));
@@ -184,22 +204,23 @@ int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) {
   h->n = n;
   h->m = m;
   h->dtype = dtype;
-  h->elem = (dtype == SDMD_U8) ? 1 : 4;
+  h->elem = (dtype == SDMD_U8) ? 1 : (dtype == SDMD_C64 ? 8 : 4);
+  h->gsz = (dtype == SDMD_C64) ? 16 : 8;
   h->slot_bytes = ((n * h->elem + kSlotAlign - 1) / kSlotAlign) * kSlotAlign;
   gram_row_schedule(h->slot_bytes, h->num_sms, &h->chunk, &h->nblk);
   const size_t ring_bytes = (size_t)m * (size_t)h->slot_bytes;
   const size_t ws_bytes = (size_t)modes_ws_doubles(m) * sizeof(double);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&h->ring, ring_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * 8);
-  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * h->gsz);
+  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * h->gsz);
+  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * h->gsz);
   if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->ring, 0, ring_bytes);
-  if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * 8);
+  if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * h->gsz);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->ws, 0, ws_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
@@ -216,6 +237,111 @@ int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) {
   return SDMD_OK;
 }
 
+int sdmd_create_sparse(int64_t n, int32_t m, int32_t nnz_max, sdmd_t* out) {
+  if (!out) return fail(SDMD_ERR_ARG, "sdmd_create_sparse: out is NULL");
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(SDMD_ERR_ARG, "sdmd_create_sparse: n=%lld out of range", (long long)n);
+  if (m < 2 || m > SDMD_MAX_M) return fail(SDMD_ERR_ARG, "sdmd_create_sparse: m=%d not in [2, %d]", m, SDMD_MAX_M);
+  if (nnz_max < 1) return fail(SDMD_ERR_ARG, "sdmd_create_sparse: nnz_max=%d", nnz_max);
+  sdmd_s* h = new (std::nothrow) sdmd_s();
+  if (!h) return fail(SDMD_ERR_OOM, "sdmd_create_sparse: host allocation failed");
+  CK(cudaGetDevice(&h->device));
+  CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
+  h->n = n;
+  h->m = m;
+  h->dtype = SDMD_C64_SPARSE;
+  h->elem = 8;
+  h->gsz = 16;
+  h->nnz_max = nnz_max;
+  h->nnz.assign(m, 0);
+  h->nblk = m * sparse_chunks(nnz_max);
+  const size_t ws_bytes = (size_t)modes_ws_doubles(2) * sizeof(double);
+  cudaError_t e = cudaSuccess;
+  if (e == cudaSuccess) e = cudaMalloc(&h->idx_ring, (size_t)m * nnz_max * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->val_ring, (size_t)m * nnz_max * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tag, (size_t)n * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->tval, (size_t)n * sizeof(float2));
+  if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->nblk * 16);
+  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(h->tag, 0xff, (size_t)n * sizeof(int));   // tag -1: no stamp
+  if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * 16);
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    const int code = (e == cudaErrorMemoryAllocation) ? SDMD_ERR_OOM : SDMD_ERR_CUDA;
+    cudaGetLastError();
+    free_all(h);
+    delete h;
+    return fail(code, "sdmd_create_sparse(n=%lld, m=%d, nnz_max=%d): %s", (long long)n, m, nnz_max,
+                cudaGetErrorString(e));
+  }
+  *out = h;
+  return SDMD_OK;
+}
+
+int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t* idx, const void* vals, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_push_sparse: NULL handle");
+  if (h->dtype != SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_push_sparse: dense handle");
+  if (nnz < 0 || nnz > h->nnz_max) return fail(SDMD_ERR_ARG, "sdmd_push_sparse: nnz=%d not in [0, %d]", nnz, h->nnz_max);
+  if (nnz > 0 && (!idx || !vals)) return fail(SDMD_ERR_ARG, "sdmd_push_sparse: NULL idx or vals");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (nnz > 0 && ptr_kind(idx) != kDevice) {
+    for (int32_t i = 0; i < nnz; ++i) {
+      if (idx[i] < 0 || (int64_t)idx[i] >= h->n)
+        return fail(SDMD_ERR_ARG, "sdmd_push_sparse: idx[%d]=%d outside [0, %lld)", i, idx[i], (long long)h->n);
+      if (i > 0 && idx[i] <= idx[i - 1])
+        return fail(SDMD_ERR_ARG, "sdmd_push_sparse: indices not strictly increasing at %d", i);
+    }
+  }
+  const int32_t s = h->head;
+  int* sidx = h->idx_ring + (int64_t)s * h->nnz_max;
+  float2* sval = h->val_ring + (int64_t)s * h->nnz_max;
+  if (nnz > 0) {
+    TraceScope ts(h, SDMD_K_INGEST, st);
+    CK(cudaMemcpyAsync(sidx, idx, (size_t)nnz * sizeof(int), cudaMemcpyDefault, st));
+    CK(cudaMemcpyAsync(sval, vals, (size_t)nnz * sizeof(float2), cudaMemcpyDefault, st));
+  }
+  h->nnz[s] = nnz;
+  h->stamp = (h->stamp == 0x7ffffffe) ? 1 : h->stamp + 1;
+  SparseRowArgs a;
+  a.idx_ring = h->idx_ring;
+  a.val_ring = h->val_ring;
+  a.nnz_max = h->nnz_max;
+  a.tag = h->tag;
+  a.tval = h->tval;
+  a.n = h->n;
+  a.stamp = h->stamp;
+  a.c = (int32_t)(h->count + 1 < h->m ? h->count + 1 : h->m);
+  a.s_first = (h->count + 1 <= h->m) ? 0 : (s + 1) % h->m;
+  a.s_new = s;
+  a.m = h->m;
+  int nb = 0;
+  for (int jj = 0; jj < a.c; ++jj) {
+    a.chunk_start[jj] = nb;
+    nb += sparse_chunks(h->nnz[(a.s_first + jj) % h->m]);
+  }
+  for (int j = 0; j < h->m; ++j) a.nnz[j] = h->nnz[j];
+  a.nblk = nb;
+  a.partials = static_cast<double2*>(h->partials);
+  a.ticket = h->ticket;
+  a.G = h->G;
+  {
+    TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+    CK(launch_sparse_scatter(sidx, sval, nnz, h->n, h->stamp, h->tag, h->tval, h->status, st));
+    CK(launch_sparse_row(a, st));
+  }
+  h->head = (s + 1) % h->m;
+  h->count += 1;
+  return SDMD_OK;
+}
+
 int sdmd_destroy(sdmd_t h) {
   if (!h) return SDMD_OK;
   DeviceScope ds(h->device);
@@ -227,6 +353,7 @@ int sdmd_destroy(sdmd_t h) {
 
 int sdmd_push(sdmd_t h, const void* x, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_push: NULL handle");
+  if (h->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_push: sparse handle (use sdmd_push_sparse)");
   if (!x) return fail(SDMD_ERR_ARG, "sdmd_push: NULL snapshot");
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -273,14 +400,16 @@ int sdmd_gram(sdmd_t h, void* G, void* stream) {
   const bool direct = ptr_kind(G) == kDevice;
   uint64_t* dst = direct ? static_cast<uint64_t*>(G) : static_cast<uint64_t*>(h->gtmp);
   gather_gram_kernel<<<(c * c + 255) / 256, 256, 0, st>>>(static_cast<const uint64_t*>(h->G), h->m, c,
-                                                           oldest_slot(h), dst);
+                                                           oldest_slot(h), (int)(h->gsz / 8), dst);
   CK(cudaGetLastError());
-  if (!direct) return copy_out(G, h->gtmp, (size_t)c * c * 8, st);
+  if (!direct) return copy_out(G, h->gtmp, (size_t)c * c * h->gsz, st);
   return SDMD_OK;
 }
 
 int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_modes: NULL handle");
+  if (h->dtype == SDMD_C64 || h->dtype == SDMD_C64_SPARSE)
+    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes: complex handles provide the streaming Gram only");
   const int c = resident(h);
   if (c < 3) return fail(SDMD_ERR_NOT_READY, "sdmd_modes: %d snapshots resident, need >= 3", c);
   if (r < 1 || r > c - 1) return fail(SDMD_ERR_ARG, "sdmd_modes: r=%d not in [1, %d]", r, c - 1);
@@ -395,6 +524,7 @@ int sdmd_status(sdmd_t h, void* stream) {
   CK(cudaStreamSynchronize(st));
   if (v & kDevTimeout) return fail(SDMD_ERR_TIMEOUT, "device wait timed out");
   if (v & kDevRank) return fail(SDMD_ERR_RANK, "eigensolver iteration cap reached");
+  if (v & kDevRange) return fail(SDMD_ERR_ARG, "sparse coefficient index outside [0, n) (entry skipped)");
   return SDMD_OK;
 }
 

@@ -23,6 +23,8 @@
 //  - float32: four FP32 FMA chains of 8 products per piece per lane, then the
 //    piece's sum is added in FP64; cross-lane and cross-CTA sums are FP64 in a
 //    fixed order, so results are deterministic for a given schedule.
+//  - complex64: the same with conj(x_j) x_new split into real and imaginary
+//    FP32 chains; G is Hermitian (complex128).
 //
 // Every mbarrier wait is bounded (about one second of SM clock); on expiry
 // the kernel raises kDevTimeout in the handle's status word, stops issuing
@@ -99,8 +101,12 @@ struct Smem {
   unsigned long long xbar;                    // x_new barrier
   long long acc_i[SDMD_MAX_M];
   double acc_d[SDMD_MAX_M];
+  double acc_im[SDMD_MAX_M];                  // imaginary parts (complex snapshots)
   int last;
 };
+
+// Element modes of the kernel.
+enum { kModeU8 = 0, kModeF32 = 1, kModeC64 = 2 };
 
 template <typename Acc>
 __device__ void finish_row(const GramRowArgs& a, Smem& sm) {
@@ -129,8 +135,42 @@ __device__ void finish_row(const GramRowArgs& a, Smem& sm) {
   if (threadIdx.x == 0) *a.ticket = 0u;  // ready for the next launch
 }
 
-template <bool kU8>
+// Complex version: G[j][s_new] = <x_j, x_new> = g_j and G[s_new][j] = conj(g_j).
+__device__ void finish_row_c64(const GramRowArgs& a, Smem& sm) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned int t = atomicAdd(a.ticket, 1u);
+    sm.last = (t == (unsigned int)a.nblk - 1u);
+  }
+  __syncthreads();
+  if (!sm.last) return;
+  __threadfence();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double2* P = static_cast<const double2*>(a.partials);
+  double2* G = static_cast<double2*>(a.G);
+  for (int jj = warp; jj < a.c; jj += kGrWarps) {
+    double sr = 0.0, si = 0.0;
+    for (int b = lane; b < a.nblk; b += 32) {
+      const double2 v = __ldcg(P + (int64_t)jj * a.nblk + b);
+      sr += v.x;
+      si += v.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      const int j = (a.s_first + jj) % a.m;
+      if (j == a.s_new) si = 0.0;   // <x, x> is real; drop the rounding residue
+      G[(int64_t)j * a.m + a.s_new] = make_double2(sr, si);
+      G[(int64_t)a.s_new * a.m + j] = make_double2(sr, -si);
+    }
+  }
+  if (threadIdx.x == 0) *a.ticket = 0u;
+}
+
+template <int kMode>
 __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArgs a) {
+  constexpr bool kU8 = (kMode == kModeU8);
   extern __shared__ __align__(128) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -139,6 +179,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
   for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
     sm.acc_i[j] = 0;
     sm.acc_d[j] = 0.0;
+    sm.acc_im[j] = 0.0;
   }
   if (threadIdx.x == 0) {
     for (int w = 0; w < kGrWarps; ++w)
@@ -178,7 +219,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
     failed = __any_sync(0xffffffffu, failed);
     if (live && failed) fail_it = 0;
     unsigned int su = 0;
-    double sd = 0.0;
+    double sd = 0.0, si = 0.0;
     for (int it = 0; it < nitems; ++it) {
       const unsigned gi = g + it, s = gi % kStages, par = (gi / kStages) & 1;
       const int q = it % npieces;
@@ -201,7 +242,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
             su = __dp4a(v.z, w.z, su);
             su = __dp4a(v.w, w.w, su);
           }
-        } else {
+        } else if constexpr (kMode == kModeF32) {
           float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
 #pragma unroll
           for (int u = 0; u < kPiece / 512; ++u) {
@@ -213,6 +254,20 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
             f3 = fmaf(v.w, w.w, f3);
           }
           sd += (double)((f0 + f1) + (f2 + f3));
+        } else {
+          // two complex64 values per 16 bytes: conj(v) * w
+          float r0 = 0.f, r1 = 0.f, i0 = 0.f, i1 = 0.f;
+#pragma unroll
+          for (int u = 0; u < kPiece / 512; ++u) {
+            const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+            const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+            r0 = fmaf(v.x, w.x, fmaf(v.y, w.y, r0));
+            r1 = fmaf(v.z, w.z, fmaf(v.w, w.w, r1));
+            i0 = fmaf(v.x, w.y, fmaf(-v.y, w.x, i0));
+            i1 = fmaf(v.z, w.w, fmaf(-v.w, w.z, i1));
+          }
+          sd += (double)(r0 + r1);
+          si += (double)(i0 + i1);
         }
       }
       __syncwarp();                // all lanes are done reading stage s
@@ -234,6 +289,11 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
           const double t = warp_sum(sd);
           if (lane == 0) sm.acc_d[jj] += t;
           sd = 0.0;
+          if constexpr (kMode == kModeC64) {
+            const double ti = warp_sum(si);
+            if (lane == 0) sm.acc_im[jj] += ti;
+            si = 0.0;
+          }
         }
       }
     }
@@ -254,10 +314,15 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
     long long* P = static_cast<long long*>(a.partials);
     for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = sm.acc_i[j];
     finish_row<long long>(a, sm);
-  } else {
+  } else if constexpr (kMode == kModeF32) {
     double* P = static_cast<double*>(a.partials);
     for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = sm.acc_d[j];
     finish_row<double>(a, sm);
+  } else {
+    double2* P = static_cast<double2*>(a.partials);
+    for (int j = threadIdx.x; j < a.c; j += blockDim.x)
+      P[(int64_t)j * a.nblk + blockIdx.x] = make_double2(sm.acc_d[j], sm.acc_im[j]);
+    finish_row_c64(a, sm);
   }
 }
 
@@ -276,16 +341,20 @@ cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
   static bool attr = false;
   const size_t smem = sizeof(Smem);
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_row_bulk_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeU8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_row_bulk_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeC64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   if (dtype == SDMD_U8)
-    gram_row_bulk_kernel<true><<<a.nblk, kGrThreads, smem, st>>>(a);
+    gram_row_bulk_kernel<kModeU8><<<a.nblk, kGrThreads, smem, st>>>(a);
+  else if (dtype == SDMD_C64)
+    gram_row_bulk_kernel<kModeC64><<<a.nblk, kGrThreads, smem, st>>>(a);
   else
-    gram_row_bulk_kernel<false><<<a.nblk, kGrThreads, smem, st>>>(a);
+    gram_row_bulk_kernel<kModeF32><<<a.nblk, kGrThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ constexpr int kGrWarps = kGrThreads / 32;
 constexpr int kDevOk = 0;
 constexpr int kDevRank = 1;      // an eigensolver reached its iteration cap
 constexpr int kDevTimeout = 2;   // a bounded wait gave up
+constexpr int kDevRange = 4;     // a sparse coefficient index was outside [0, n)
 
 struct GramRowArgs {
   const uint8_t* ring;   // slot j starts at ring + j * slot_bytes
@@ -83,6 +84,29 @@ struct PhiArgs {
 };
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
+
+struct SparseRowArgs {
+  const int* idx_ring;       // slot j's indices at idx_ring + j * nnz_max
+  const float2* val_ring;    // slot j's complex64 values
+  int nnz_max;
+  const int* tag;            // lookup table tags (length n)
+  const float2* tval;        // lookup table values (length n)
+  int64_t n;
+  int stamp;                 // tag value of the new snapshot's entries
+  int c, s_first, s_new, m;
+  int nnz[SDMD_MAX_M];          // entries per physical slot
+  int chunk_start[SDMD_MAX_M];  // first CTA of window slot jj
+  int nblk;
+  double2* partials;         // one per CTA
+  unsigned int* ticket;
+  void* G;                   // m x m complex128
+};
+
+// CTAs a snapshot with nnz entries takes in the sparse row kernel.
+int sparse_chunks(int nnz);
+cudaError_t launch_sparse_scatter(const int* idx, const float2* val, int nnz, int64_t n, int stamp, int* tag,
+                                  float2* tval, int* status, cudaStream_t st);
+cudaError_t launch_sparse_row(const SparseRowArgs& a, cudaStream_t st);
 
 // Records `msg` as this thread's sdmd_last_error() text; returns `code`.
 int set_last_error(int code, const char* msg);

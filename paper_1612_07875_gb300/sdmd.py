@@ -13,6 +13,8 @@ import threading
 
 SDMD_F32 = 0
 SDMD_U8 = 1
+SDMD_C64 = 2
+SDMD_C64_SPARSE = 3
 
 SDMD_OK = 0
 SDMD_ERR_ARG = -1
@@ -43,6 +45,8 @@ _I32 = ctypes.c_int32
 _SIGNATURES = {
     "sdmd_create": [_I64, _I32, _I32, ctypes.POINTER(_VP)],
     "sdmd_destroy": [_VP],
+    "sdmd_create_sparse": [_I64, _I32, _I32, ctypes.POINTER(_VP)],
+    "sdmd_push_sparse": [_VP, _I32, _VP, _VP, _VP],
     "sdmd_push": [_VP, _VP, _VP],
     "sdmd_count": [_VP, ctypes.POINTER(_I64)],
     "sdmd_gram": [_VP, _VP, _VP],
@@ -118,6 +122,16 @@ def sdmd_create(n, m, dtype):
     h = _VP()
     _check(lib().sdmd_create(int(n), int(m), int(dtype), ctypes.byref(h)), "sdmd_create")
     return h.value
+
+
+def sdmd_create_sparse(n, m, nnz_max):
+    h = _VP()
+    _check(lib().sdmd_create_sparse(int(n), int(m), int(nnz_max), ctypes.byref(h)), "sdmd_create_sparse")
+    return h.value
+
+
+def sdmd_push_sparse(h, nnz, idx, vals, stream=None):
+    _check(lib().sdmd_push_sparse(h, int(nnz), ptr(idx), ptr(vals), stream_handle(stream)), "sdmd_push_sparse")
 
 
 def sdmd_destroy(h):
