@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the rebuild and Fourier-sparse measurements")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     return ap.parse_args()
 
@@ -216,6 +218,57 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def measure_rebuild(S, h, stream, n):
+    """One full-window rebuild of G on the benchmark handle."""
+    import torch
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    r0.record(stream)
+    S.sdmd_rebuild(h, stream.cuda_stream)
+    r1.record(stream)
+    stream.synchronize()
+    ms = r0.elapsed_time(r1)
+    return {"ms": ms, "passes": M_WIN, "algorithmic_GB/s": M_WIN * M_WIN * n / (ms * 1e-3) / 1e9,
+            "note": "one Gram-row pass per resident snapshot; bit-identical to the streamed G"}
+
+
+def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
+    """Per-push time of the Fourier-sparse Gram row (scatter + row kernels)."""
+    import torch
+    fs = synth.FourierSparseStream(seed=synth.config_seed(3))
+    snaps = [fs.snapshot(t) for t in range(m + 3 + pushes)]
+    dev_snaps = [(torch.from_numpy(i).to(dev), torch.from_numpy(v.view(np.float32)).to(dev)) for i, v in snaps]
+    sh = stream.cuda_stream
+    h = S.sdmd_create_sparse(fs.N, m, fs.nnz + 16)
+    try:
+        for t in range(m + 3):
+            i, v = dev_snaps[t]
+            S.sdmd_push_sparse(h, i.numel(), i, v, sh)
+        stream.synchronize()
+        S.sdmd_trace(h, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(m + 3, m + 3 + pushes):
+            i, v = dev_snaps[t]
+            S.sdmd_push_sparse(h, i.numel(), i, v, sh)
+        e1.record(stream)
+        stream.synchronize()
+        tot = e0.elapsed_time(e1)
+        rl, rms = S.sdmd_trace_read(h, S.SDMD_K_GRAM_ROW)
+        S.sdmd_trace(h, False)
+        ok = S.sdmd_status(h, sh) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h)
+    nnz = fs.nnz
+    return {"config": "1024x1024 complex64 field, nnz=%d (1%%), window m=%d" % (nnz, m),
+            "snapshots/s": pushes / (tot * 1e-3), "push_us": 1e3 * tot / pushes,
+            "row_kernels_us": 1e3 * rms / max(rl, 1),
+            "algorithmic_bytes_per_push": m * nnz * 12 + nnz * 12, "status_ok": ok,
+            "bound": "latency / L2 (lookup table 12 MB and window 8 MB are L2-resident)"}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -333,12 +386,21 @@ def run_ours(args):
         ems = e0.elapsed_time(e1)
         e2e = {"value": world * Ke / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n,
                "d2h_bytes_per_step": 2 * R_MODES * 8 + 4, "steps": Ke}
+    # ---- a9: full-window rebuild of G (one Gram-row pass per resident slot)
+    rebuild = sparse = None
+    if not args.no_secondary:
+        rebuild = measure_rebuild(S, h, stream, n)
     S.sdmd_destroy(h)
+    band_frames = frames[:, :n // 64].cpu().numpy()     # CPU oracle sample (generated above)
+    del frames
+    torch.cuda.empty_cache()
+    # ---- a10: Fourier-sparse Gram row, 1024x1024 field, nnz 10,486, m = 64
+    if not args.no_secondary:
+        sparse = measure_sparse(S, synth, dev, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        bf = frames[:, :n // 64].cpu().numpy()
-        rate, info = oracle_rate(bf, n, args.cpu_sample_seconds)
+        rate, info = oracle_rate(band_frames, n, args.cpu_sample_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
                "sample": "%d oracle steps (exact int64 Gram recompute + dense FP64 DMD r=10) on a "
                          "%d-pixel band (1/64 of each frame), %.1f s; rate scaled to full frames by "
@@ -362,6 +424,8 @@ def run_ours(args):
         "latency_ms": {"p50": float(np.percentile(per_step, 50)), "p99": float(np.percentile(per_step, 99)),
                        "max": float(per_step.max())},
         "gpu_launches": 3 * K,
+        "rebuild": rebuild,
+        "sparse_row": sparse,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -138,6 +138,16 @@ SDMD_API int sdmd_push(sdmd_t h, const void *x, void *stream);
  */
 SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const void *vals, void *stream);
 
+/*
+ * sdmd_rebuild -- recompute the whole Gram of the resident window from the
+ * ring buffer (Algorithm 1's first-step branch, G = X^T X; Sec. 2.1 Eq. 3),
+ * e.g. to resynchronise G after the ring was modified outside the library.
+ * Runs one Gram-row pass per resident snapshot, in time order, so every
+ * entry is computed with the same reduction as when it was streamed: the
+ * result equals the streamed G bit for bit. Cost: c passes over the window.
+ */
+SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
+
 /* sdmd_count -- number of snapshots pushed so far (host pointer). Host-side
  * bookkeeping only; does not touch the device. */
 SDMD_API int sdmd_count(sdmd_t h, int64_t *count);

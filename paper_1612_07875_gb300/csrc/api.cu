@@ -385,6 +385,65 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   return SDMD_OK;
 }
 
+int sdmd_rebuild(sdmd_t h, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_rebuild: NULL handle");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int c = resident(h);
+  const int first = oldest_slot(h);
+  // rows in time order: the final value of entry (i, j) comes from the row of
+  // the later snapshot, exactly as when it was streamed
+  for (int jj = 0; jj < c; ++jj) {
+    const int s = (first + jj) % h->m;
+    if (h->dtype == SDMD_C64_SPARSE) {
+      h->stamp = (h->stamp == 0x7ffffffe) ? 1 : h->stamp + 1;
+      SparseRowArgs a;
+      a.idx_ring = h->idx_ring;
+      a.val_ring = h->val_ring;
+      a.nnz_max = h->nnz_max;
+      a.tag = h->tag;
+      a.tval = h->tval;
+      a.n = h->n;
+      a.stamp = h->stamp;
+      a.c = c;
+      a.s_first = first;
+      a.s_new = s;
+      a.m = h->m;
+      int nb = 0;
+      for (int k = 0; k < c; ++k) {
+        a.chunk_start[k] = nb;
+        nb += sparse_chunks(h->nnz[(first + k) % h->m]);
+      }
+      for (int j = 0; j < h->m; ++j) a.nnz[j] = h->nnz[j];
+      a.nblk = nb;
+      a.partials = static_cast<double2*>(h->partials);
+      a.ticket = h->ticket;
+      a.G = h->G;
+      TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+      CK(launch_sparse_scatter(h->idx_ring + (int64_t)s * h->nnz_max, h->val_ring + (int64_t)s * h->nnz_max,
+                               h->nnz[s], h->n, h->stamp, h->tag, h->tval, h->status, st));
+      CK(launch_sparse_row(a, st));
+    } else {
+      GramRowArgs a;
+      a.ring = h->ring;
+      a.slot_bytes = h->slot_bytes;
+      a.chunk = h->chunk;
+      a.nblk = h->nblk;
+      a.c = c;
+      a.s_first = first;
+      a.s_new = s;
+      a.m = h->m;
+      a.partials = h->partials;
+      a.ticket = h->ticket;
+      a.G = h->G;
+      a.status = h->status;
+      TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+      CK(launch_gram_row(h->dtype, a, st));
+    }
+  }
+  return SDMD_OK;
+}
+
 int sdmd_count(sdmd_t h, int64_t* count) {
   if (!h || !count) return fail(SDMD_ERR_ARG, "sdmd_count: NULL argument");
   *count = h->count;

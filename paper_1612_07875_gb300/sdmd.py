@@ -49,6 +49,7 @@ _SIGNATURES = {
     "sdmd_push_sparse": [_VP, _I32, _VP, _VP, _VP],
     "sdmd_push": [_VP, _VP, _VP],
     "sdmd_count": [_VP, ctypes.POINTER(_I64)],
+    "sdmd_rebuild": [_VP, _VP],
     "sdmd_gram": [_VP, _VP, _VP],
     "sdmd_modes": [_VP, _I32, _VP, _VP, _VP, _VP],
     "sdmd_svd": [_VP, _I32, _VP, _VP, _VP],
@@ -140,6 +141,10 @@ def sdmd_destroy(h):
 
 def sdmd_push(h, x, stream=None):
     _check(lib().sdmd_push(h, ptr(x), stream_handle(stream)), "sdmd_push")
+
+
+def sdmd_rebuild(h, stream=None):
+    _check(lib().sdmd_rebuild(h, stream_handle(stream)), "sdmd_rebuild")
 
 
 def sdmd_count(h):

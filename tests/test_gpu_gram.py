@@ -181,3 +181,41 @@ def test_error_paths(cuda_device):
         assert ei.value.code == S.SDMD_ERR_ARG
     finally:
         S.sdmd_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32", "c64", "sparse"])
+def test_full_window_rebuild_equals_streamed_gram_bitwise(cuda_device, kind):
+    # Algorithm 1's first-step branch (G = X^T X from scratch) against the
+    # streamed G: same per-entry reduction, so equal bit for bit.
+    rng = np.random.default_rng(12)
+    m, T = 9, 23
+    if kind == "sparse":
+        fs = synth.FourierSparseStream(side=64, nnz=41, churn=0.2, seed=33)
+        h = S.sdmd_create_sparse(fs.N, m, 64)
+    else:
+        n = 40009
+        dt = {"u8": S.SDMD_U8, "f32": S.SDMD_F32, "c64": S.SDMD_C64}[kind]
+        h = S.sdmd_create(n, m, dt)
+    try:
+        for t in range(T):
+            if kind == "sparse":
+                idx, val = fs.snapshot(t)
+                S.sdmd_push_sparse(h, idx.size, idx, val)
+            elif kind == "u8":
+                S.sdmd_push(h, torch.from_numpy(rng.integers(0, 256, n, dtype=np.uint8)).to(cuda_device))
+            elif kind == "f32":
+                S.sdmd_push(h, torch.from_numpy(rng.standard_normal(n).astype(np.float32)).to(cuda_device))
+            else:
+                x = (rng.standard_normal(n) + 1j * rng.standard_normal(n)).astype(np.complex64)
+                S.sdmd_push(h, torch.from_numpy(x.view(np.float32)).to(cuda_device))
+        words = 2 if kind in ("c64", "sparse") else 1
+        G1 = torch.empty(m, m, words, dtype=torch.int64, device=cuda_device)
+        S.sdmd_gram(h, G1)
+        S.sdmd_rebuild(h)
+        G2 = torch.empty(m, m, words, dtype=torch.int64, device=cuda_device)
+        S.sdmd_gram(h, G2)
+        torch.cuda.synchronize()
+        assert torch.equal(G1, G2)
+        assert S.sdmd_status(h) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h)
