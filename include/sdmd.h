@@ -77,6 +77,8 @@ enum {
 
 /* Largest window (number of resident snapshots) a handle may hold. */
 #define SDMD_MAX_M 256
+/* Largest number of DMD frames in flight in a pipelined handle. */
+#define SDMD_MAX_DEPTH 16
 
 /*
  * sdmd_create -- allocate a streaming window.
@@ -92,6 +94,15 @@ enum {
  * allocation fails (nothing is leaked). Synchronous.
  */
 SDMD_API int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t *out);
+
+/*
+ * sdmd_create_ex -- as sdmd_create, with `depth` DMD frames in flight for
+ * sdmd_step (1 <= depth <= SDMD_MAX_DEPTH; 1 = no pipelining). A pipelined
+ * handle keeps m + depth snapshots in its ring (so the X' of frames still
+ * being decomposed is not overwritten), one workspace, G snapshot and CUDA
+ * stream per frame in flight.
+ */
+SDMD_API int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t *out);
 
 /*
  * sdmd_create_sparse -- allocate a streaming window of Fourier-sparse
@@ -171,7 +182,8 @@ SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
  *        lambda_1 * 64 * (c-1) * 2^-52)
  *   vsi = V Sigma^-1; A~ = vsi^T G_XY vsi; A~ W = W Lambda (unit-norm columns)
  *   Phi = X' vsi W   (X' read in place from the ring)
- *   r       requested number of modes, 1 <= r <= c-1.
+ *   r       requested number of modes, 1 <= r <= m-1. While the window is
+ *           ramping up (c-1 < r) the modes beyond c-1 come out as zero.
  *   phi     n x r complex64, column-major (mode k at phi + 2*k*n floats,
  *           interleaved re, im), or NULL to skip forming Phi. Columns at or
  *           beyond the kept rank are zero.
@@ -185,6 +197,27 @@ SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
  * reached the call still completes and sdmd_status reports SDMD_ERR_RANK.
  */
 SDMD_API int sdmd_modes(sdmd_t h, int32_t r, void *phi, void *lambda, int32_t *r_out, void *stream);
+
+/*
+ * sdmd_step -- pipelined streaming DMD: push x (as sdmd_push), then compute
+ * the exact DMD of the new window (as sdmd_modes) on an internal stream so
+ * that it overlaps with the following pushes. The window's G is copied on
+ * `stream` right after the push; the eigensolvers, Phi and the output copies
+ * run on the internal stream of one of `depth` frame contexts. `stream` only
+ * waits for a context when its workspace or the ring slots it reads are
+ * about to be reused (depth pushes later).
+ * Results of this call (phi, lambda, r_out) are complete once `stream`
+ * passes sdmd_sync, or the sdmd_step call `depth` calls later. phi must be
+ * a distinct device buffer per frame in flight; lambda / r_out must be
+ * device or pinned host memory. Until 3 snapshots are resident only the
+ * push happens. Real dense handles only; all pushes and steps of a handle
+ * must use one stream. With depth 1 this is sdmd_push + sdmd_modes.
+ */
+SDMD_API int sdmd_step(sdmd_t h, const void *x, int32_t r, void *phi, void *lambda, int32_t *r_out,
+                       void *stream);
+
+/* sdmd_sync -- make `stream` wait for every sdmd_step frame still in flight. */
+SDMD_API int sdmd_sync(sdmd_t h, void *stream);
 
 /*
  * sdmd_svd -- singular values and right singular vectors of X from the last
@@ -209,7 +242,8 @@ enum {
     SDMD_K_GRAM_ROW = 1,  /* Gram-row multi-dot + symmetric insert            */
     SDMD_K_MODES = 2,     /* FP64 eigensolvers / small products (one CTA)     */
     SDMD_K_PHI = 3,       /* Phi = X' (V Sigma^-1 W)                          */
-    SDMD_K_COUNT = 4
+    SDMD_K_FRAME = 4,     /* one sdmd_step frame: call start to outputs done  */
+    SDMD_K_COUNT = 5
 };
 
 /*
@@ -227,6 +261,13 @@ SDMD_API int sdmd_trace(sdmd_t h, int32_t enable);
  * enabled), then resets that class's counters.
  */
 SDMD_API int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t *launches, double *total_ms);
+
+/*
+ * sdmd_trace_times -- like sdmd_trace_read, but returns the individual
+ * durations (ms) of up to `cap` traced launches of class `kernel` in `ms`
+ * and their number in `count` (host pointers); resets that class.
+ */
+SDMD_API int sdmd_trace_times(sdmd_t h, int32_t kernel, double *ms, int32_t cap, int32_t *count);
 
 /*
  * sdmd_modes_phase_cycles -- SM clock counter (clock64) at the phase

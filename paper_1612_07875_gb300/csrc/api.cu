@@ -15,11 +15,28 @@
 
 using namespace sdmd;
 
+// One in-flight DMD of the pipelined step (sdmd_step): its own workspace,
+// G snapshot and stream, and events ordering it against the push stream.
+struct PipeCtx {
+  double* ws = nullptr;       // modes workspace (window m)
+  int* r_dev = nullptr;
+  void* gsnap = nullptr;      // time-ordered c x c copy of G for this frame
+  cudaStream_t st = nullptr;
+  cudaEvent_t ev_g = nullptr;     // G snapshot taken (push stream)
+  cudaEvent_t ev_done = nullptr;  // modes, Phi and output copies done (ctx stream)
+  bool busy = false;
+  int64_t frame = -1;         // push count of the frame being processed
+};
+
 struct sdmd_s {
   int device = 0;
   int num_sms = 0;
   int64_t n = 0;
-  int32_t m = 0;
+  int32_t m = 0;              // window length (resident snapshots)
+  int32_t cap = 0;            // ring slots (m, or m + depth when pipelined)
+  int32_t depth = 1;          // DMD frames in flight (sdmd_step)
+  std::vector<PipeCtx> ctx;
+  int64_t steps = 0;
   int32_t dtype = 0;
   int64_t elem = 0;
   int64_t slot_bytes = 0;
@@ -49,7 +66,7 @@ struct sdmd_s {
   // tracing: per kernel class, event pairs recorded since the last read
   bool trace = false;
   std::vector<cudaEvent_t> tr_ev[SDMD_K_COUNT];
-  size_t tr_used[SDMD_K_COUNT] = {0, 0, 0, 0};
+  size_t tr_used[SDMD_K_COUNT] = {0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -129,6 +146,21 @@ __global__ void gather_gram_kernel(const uint64_t* G, int m, int c, int start, i
   for (int q = 0; q < words; ++q) out[(int64_t)idx * words + q] = G[src * words + q];
 }
 
+// Event pair for class k (created on first use); false if tracing is off.
+bool trace_pair(sdmd_s* h, int k, cudaEvent_t* a, cudaEvent_t* b) {
+  if (!h->trace) return false;
+  auto& v = h->tr_ev[k];
+  while (v.size() < 2 * (h->tr_used[k] + 1)) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return false;
+    v.push_back(e);
+  }
+  *a = v[2 * h->tr_used[k]];
+  *b = v[2 * h->tr_used[k] + 1];
+  h->tr_used[k] += 1;
+  return true;
+}
+
 // Brackets one enqueued operation with a pair of events when tracing is on.
 struct TraceScope {
   sdmd_s* h;
@@ -162,7 +194,21 @@ void free_sparse(sdmd_s* h) {
   cudaFree(h->tval);
 }
 
+void free_ctx(sdmd_s* h) {
+  for (PipeCtx& c : h->ctx) {
+    if (c.st) cudaStreamSynchronize(c.st);
+    cudaFree(c.ws);
+    cudaFree(c.r_dev);
+    cudaFree(c.gsnap);
+    if (c.ev_g) cudaEventDestroy(c.ev_g);
+    if (c.ev_done) cudaEventDestroy(c.ev_done);
+    if (c.st) cudaStreamDestroy(c.st);
+  }
+  h->ctx.clear();
+}
+
 void free_all(sdmd_s* h) {
+  free_ctx(h);
   free_sparse(h);
   for (int k = 0; k < SDMD_K_COUNT; ++k)
     for (cudaEvent_t e : h->tr_ev[k]) cudaEventDestroy(e);
@@ -177,7 +223,19 @@ void free_all(sdmd_s* h) {
 }
 
 inline int32_t resident(const sdmd_s* h) { return (int32_t)(h->count < h->m ? h->count : h->m); }
-inline int32_t oldest_slot(const sdmd_s* h) { return h->count >= h->m ? h->head : 0; }
+inline int32_t oldest_slot(const sdmd_s* h) { return (int32_t)((h->count - resident(h)) % h->cap); }
+
+// Before push number t overwrites slot t % cap (the snapshot pushed cap
+// earlier), wait for every in-flight DMD whose X' still contains it.
+void wait_ring_readers(sdmd_s* h, cudaStream_t st) {
+  const int64_t t = h->count;
+  for (PipeCtx& c : h->ctx) {
+    if (c.busy && c.frame - h->m + 2 <= t - h->cap) {
+      cudaStreamWaitEvent(st, c.ev_done, 0);
+      c.busy = false;
+    }
+  }
+}
 
 }  // namespace
 
@@ -190,8 +248,11 @@ extern "C" {
 
 const char* sdmd_last_error(void) { return g_err.c_str(); }
 
-int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) {
+int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) { return sdmd_create_ex(n, m, dtype, 1, out); }
+
+int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* out) {
   if (!out) return fail(SDMD_ERR_ARG, "sdmd_create: out is NULL");
+  if (depth < 1 || depth > SDMD_MAX_DEPTH) return fail(SDMD_ERR_ARG, "sdmd_create_ex: depth=%d not in [1, %d]", depth, SDMD_MAX_DEPTH);
   *out = nullptr;
   if (n < 1 || n > (int64_t(1) << 34)) return fail(SDMD_ERR_ARG, "sdmd_create: n=%lld out of range", (long long)n);
   if (m < 2 || m > SDMD_MAX_M) return fail(SDMD_ERR_ARG, "sdmd_create: m=%d not in [2, %d]", m, SDMD_MAX_M);
@@ -203,26 +264,41 @@ int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t* out) {
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   h->n = n;
   h->m = m;
+  h->depth = depth;
+  h->cap = m + (depth > 1 ? depth : 0);
   h->dtype = dtype;
   h->elem = (dtype == SDMD_U8) ? 1 : (dtype == SDMD_C64 ? 8 : 4);
   h->gsz = (dtype == SDMD_C64) ? 16 : 8;
   h->slot_bytes = ((n * h->elem + kSlotAlign - 1) / kSlotAlign) * kSlotAlign;
   gram_row_schedule(h->slot_bytes, h->num_sms, &h->chunk, &h->nblk);
-  const size_t ring_bytes = (size_t)m * (size_t)h->slot_bytes;
+  const size_t ring_bytes = (size_t)h->cap * (size_t)h->slot_bytes;
   const size_t ws_bytes = (size_t)modes_ws_doubles(m) * sizeof(double);
+  const size_t gbytes = (size_t)h->cap * h->cap * h->gsz;
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&h->ring, ring_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * h->gsz);
-  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * h->gsz);
+  if (e == cudaSuccess) e = cudaMalloc(&h->G, gbytes);
+  if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * h->gsz);
   if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->ring, 0, ring_bytes);
-  if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * h->gsz);
+  if (e == cudaSuccess) e = cudaMemset(h->G, 0, gbytes);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->ws, 0, ws_bytes);
+  if (depth > 1) {
+    h->ctx.resize(depth);
+    for (PipeCtx& c : h->ctx) {
+      if (e == cudaSuccess) e = cudaMalloc(&c.ws, ws_bytes);
+      if (e == cudaSuccess) e = cudaMemset(c.ws, 0, ws_bytes);
+      if (e == cudaSuccess) e = cudaMalloc(&c.r_dev, sizeof(int));
+      if (e == cudaSuccess) e = cudaMalloc(&c.gsnap, (size_t)m * m * h->gsz);
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_g, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming);
+    }
+  }
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->r_dev, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -249,6 +325,7 @@ int sdmd_create_sparse(int64_t n, int32_t m, int32_t nnz_max, sdmd_t* out) {
   CK(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device));
   h->n = n;
   h->m = m;
+  h->cap = m;
   h->dtype = SDMD_C64_SPARSE;
   h->elem = 8;
   h->gsz = 16;
@@ -319,13 +396,13 @@ int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t* idx, const void* vals
   a.n = h->n;
   a.stamp = h->stamp;
   a.c = (int32_t)(h->count + 1 < h->m ? h->count + 1 : h->m);
-  a.s_first = (h->count + 1 <= h->m) ? 0 : (s + 1) % h->m;
+  a.s_first = (h->count + 1 <= h->m) ? 0 : (s + 1) % h->cap;
   a.s_new = s;
-  a.m = h->m;
+  a.m = h->cap;
   int nb = 0;
   for (int jj = 0; jj < a.c; ++jj) {
     a.chunk_start[jj] = nb;
-    nb += sparse_chunks(h->nnz[(a.s_first + jj) % h->m]);
+    nb += sparse_chunks(h->nnz[(a.s_first + jj) % h->cap]);
   }
   for (int j = 0; j < h->m; ++j) a.nnz[j] = h->nnz[j];
   a.nblk = nb;
@@ -337,7 +414,7 @@ int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t* idx, const void* vals
     CK(launch_sparse_scatter(sidx, sval, nnz, h->n, h->stamp, h->tag, h->tval, h->status, st));
     CK(launch_sparse_row(a, st));
   }
-  h->head = (s + 1) % h->m;
+  h->head = (s + 1) % h->cap;
   h->count += 1;
   return SDMD_OK;
 }
@@ -357,6 +434,7 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   if (!x) return fail(SDMD_ERR_ARG, "sdmd_push: NULL snapshot");
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  wait_ring_readers(h, st);
   const int32_t s = h->head;
   {
     TraceScope ts(h, SDMD_K_INGEST, st);
@@ -369,9 +447,9 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   a.chunk = h->chunk;
   a.nblk = h->nblk;
   a.c = (int32_t)(h->count + 1 < h->m ? h->count + 1 : h->m);
-  a.s_first = (h->count + 1 <= h->m) ? 0 : (s + 1) % h->m;
+  a.s_first = (int32_t)((h->count + 1 - a.c) % h->cap);
   a.s_new = s;
-  a.m = h->m;
+  a.m = h->cap;
   a.partials = h->partials;
   a.ticket = h->ticket;
   a.G = h->G;
@@ -380,7 +458,7 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
     TraceScope ts(h, SDMD_K_GRAM_ROW, st);
     CK(launch_gram_row(h->dtype, a, st));
   }
-  h->head = (s + 1) % h->m;
+  h->head = (s + 1) % h->cap;
   h->count += 1;
   return SDMD_OK;
 }
@@ -394,7 +472,7 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   // rows in time order: the final value of entry (i, j) comes from the row of
   // the later snapshot, exactly as when it was streamed
   for (int jj = 0; jj < c; ++jj) {
-    const int s = (first + jj) % h->m;
+    const int s = (first + jj) % h->cap;
     if (h->dtype == SDMD_C64_SPARSE) {
       h->stamp = (h->stamp == 0x7ffffffe) ? 1 : h->stamp + 1;
       SparseRowArgs a;
@@ -408,11 +486,11 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
       a.c = c;
       a.s_first = first;
       a.s_new = s;
-      a.m = h->m;
+      a.m = h->cap;
       int nb = 0;
       for (int k = 0; k < c; ++k) {
         a.chunk_start[k] = nb;
-        nb += sparse_chunks(h->nnz[(first + k) % h->m]);
+        nb += sparse_chunks(h->nnz[(first + k) % h->cap]);
       }
       for (int j = 0; j < h->m; ++j) a.nnz[j] = h->nnz[j];
       a.nblk = nb;
@@ -432,7 +510,7 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
       a.c = c;
       a.s_first = first;
       a.s_new = s;
-      a.m = h->m;
+      a.m = h->cap;
       a.partials = h->partials;
       a.ticket = h->ticket;
       a.G = h->G;
@@ -458,7 +536,7 @@ int sdmd_gram(sdmd_t h, void* G, void* stream) {
   if (c == 0) return SDMD_OK;
   const bool direct = ptr_kind(G) == kDevice;
   uint64_t* dst = direct ? static_cast<uint64_t*>(G) : static_cast<uint64_t*>(h->gtmp);
-  gather_gram_kernel<<<(c * c + 255) / 256, 256, 0, st>>>(static_cast<const uint64_t*>(h->G), h->m, c,
+  gather_gram_kernel<<<(c * c + 255) / 256, 256, 0, st>>>(static_cast<const uint64_t*>(h->G), h->cap, c,
                                                            oldest_slot(h), (int)(h->gsz / 8), dst);
   CK(cudaGetLastError());
   if (!direct) return copy_out(G, h->gtmp, (size_t)c * c * h->gsz, st);
@@ -471,7 +549,7 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
     return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes: complex handles provide the streaming Gram only");
   const int c = resident(h);
   if (c < 3) return fail(SDMD_ERR_NOT_READY, "sdmd_modes: %d snapshots resident, need >= 3", c);
-  if (r < 1 || r > c - 1) return fail(SDMD_ERR_ARG, "sdmd_modes: r=%d not in [1, %d]", r, c - 1);
+  if (r < 1 || r > h->m - 1) return fail(SDMD_ERR_ARG, "sdmd_modes: r=%d not in [1, %d]", r, h->m - 1);
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (phi && ptr_kind(phi) != kDevice)
@@ -479,7 +557,8 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
   ModesArgs a;
   a.G = h->G;
   a.g_is_int = (h->dtype == SDMD_U8) ? 1 : 0;
-  a.m = h->m;
+  a.m = h->cap;
+  a.ws_m = h->m;
   a.c = c;
   a.start = oldest_slot(h);
   a.r_req = r;
@@ -497,7 +576,7 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
     pa.slot_bytes = h->slot_bytes;
     pa.n = h->n;
     pa.dtype = h->dtype;
-    pa.m = h->m;
+    pa.m = h->cap;
     pa.start = a.start;
     pa.p = c - 1;
     pa.r = r;
@@ -516,6 +595,95 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
   if (r_out) {
     const int rc = copy_out(r_out, h->r_dev, sizeof(int32_t), st);
     if (rc != SDMD_OK) return rc;
+  }
+  return SDMD_OK;
+}
+
+int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32_t* r_out, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_step: NULL handle");
+  if (h->dtype != SDMD_F32 && h->dtype != SDMD_U8)
+    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_step: real dense handles only");
+  if (r < 1 || r > h->m - 1) return fail(SDMD_ERR_ARG, "sdmd_step: r=%d not in [1, %d]", r, h->m - 1);
+  if (h->depth < 2) {                // no pipeline: push + modes in stream order
+    int rc = sdmd_push(h, x, stream);
+    if (rc != SDMD_OK) return rc;
+    return resident(h) >= 3 ? sdmd_modes(h, r, phi, lambda, r_out, stream) : SDMD_OK;
+  }
+  if (r < 1 || r > h->m - 1) return fail(SDMD_ERR_ARG, "sdmd_step: r=%d not in [1, %d]", r, h->m - 1);
+  if (phi && ptr_kind(phi) != kDevice) return fail(SDMD_ERR_ARG, "sdmd_step: phi must be device memory");
+  if ((lambda && ptr_kind(lambda) == kPageable) || (r_out && ptr_kind(r_out) == kPageable))
+    return fail(SDMD_ERR_ARG, "sdmd_step: lambda / r_out must be device or pinned host memory");
+  cudaEvent_t fr0 = nullptr, fr1 = nullptr;
+  const bool ftrace = (h->count + 1 >= 3) && trace_pair(h, SDMD_K_FRAME, &fr0, &fr1);
+  if (ftrace) CK(cudaEventRecord(fr0, static_cast<cudaStream_t>(stream)));
+  int rc = sdmd_push(h, x, stream);
+  if (rc != SDMD_OK) return rc;
+  const int c = resident(h);
+  if (c < 3) return SDMD_OK;         // window too short: push only
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  PipeCtx& k = h->ctx[h->steps % h->depth];
+  if (k.busy) {                      // its workspace still belongs to an older frame
+    CK(cudaStreamWaitEvent(st, k.ev_done, 0));
+    k.busy = false;
+  }
+  // snapshot the window's G (time order) on the push stream
+  gather_gram_kernel<<<(c * c + 255) / 256, 256, 0, st>>>(static_cast<const uint64_t*>(h->G), h->cap, c,
+                                                           oldest_slot(h), 1, static_cast<uint64_t*>(k.gsnap));
+  CK(cudaGetLastError());
+  CK(cudaEventRecord(k.ev_g, st));
+  CK(cudaStreamWaitEvent(k.st, k.ev_g, 0));
+  ModesArgs a;
+  a.G = k.gsnap;
+  a.g_is_int = (h->dtype == SDMD_U8) ? 1 : 0;
+  a.m = c;
+  a.ws_m = h->m;
+  a.c = c;
+  a.start = 0;
+  a.r_req = r;
+  a.ws = k.ws;
+  a.status = h->status;
+  a.r_dev = k.r_dev;
+  {
+    TraceScope ts(h, SDMD_K_MODES, k.st);
+    CK(launch_modes_small(a, k.st));
+  }
+  const ModesLayout L = modes_layout(h->m);
+  if (phi) {
+    PhiArgs pa;
+    pa.ring = h->ring;
+    pa.slot_bytes = h->slot_bytes;
+    pa.n = h->n;
+    pa.dtype = h->dtype;
+    pa.m = h->cap;
+    pa.start = oldest_slot(h);
+    pa.p = c - 1;
+    pa.r = r;
+    pa.Mf = reinterpret_cast<const float*>(k.ws + L.Mf);
+    pa.r_dev = k.r_dev;
+    pa.phi = static_cast<float*>(phi);
+    TraceScope ts(h, SDMD_K_PHI, k.st);
+    CK(launch_phi(pa, k.st));
+  }
+  if (lambda) CK(cudaMemcpyAsync(lambda, k.ws + L.lamout, (size_t)r * 16, cudaMemcpyDefault, k.st));
+  if (r_out) CK(cudaMemcpyAsync(r_out, k.r_dev, sizeof(int32_t), cudaMemcpyDefault, k.st));
+  CK(cudaEventRecord(k.ev_done, k.st));
+  if (ftrace) CK(cudaEventRecord(fr1, k.st));
+  k.busy = true;
+  k.frame = h->count - 1;
+  h->steps += 1;
+  return SDMD_OK;
+}
+
+int sdmd_sync(sdmd_t h, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_sync: NULL handle");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (PipeCtx& k : h->ctx) {
+    if (k.busy) {
+      CK(cudaStreamWaitEvent(st, k.ev_done, 0));
+      k.busy = false;
+    }
   }
   return SDMD_OK;
 }
@@ -563,6 +731,23 @@ int sdmd_trace_read(sdmd_t h, int32_t kernel, int64_t* launches, double* total_m
   return SDMD_OK;
 }
 
+int sdmd_trace_times(sdmd_t h, int32_t kernel, double* ms, int32_t cap, int32_t* count) {
+  if (!h || !ms || !count || cap < 0) return fail(SDMD_ERR_ARG, "sdmd_trace_times: bad argument");
+  if (kernel < 0 || kernel >= SDMD_K_COUNT) return fail(SDMD_ERR_ARG, "sdmd_trace_times: kernel %d", kernel);
+  DeviceScope ds(h->device);
+  const size_t used = h->tr_used[kernel];
+  int32_t k = 0;
+  for (size_t i = 0; i < used; ++i) {
+    float t = 0.f;
+    CK(cudaEventSynchronize(h->tr_ev[kernel][2 * i + 1]));
+    CK(cudaEventElapsedTime(&t, h->tr_ev[kernel][2 * i], h->tr_ev[kernel][2 * i + 1]));
+    if (k < cap) ms[k++] = t;
+  }
+  *count = k;
+  h->tr_used[kernel] = 0;
+  return SDMD_OK;
+}
+
 int sdmd_modes_phase_cycles(sdmd_t h, int64_t* cycles, int32_t count, void* stream) {
   if (!h || !cycles || count < 1 || count > 16) return fail(SDMD_ERR_ARG, "sdmd_modes_phase_cycles: bad argument");
   DeviceScope ds(h->device);
@@ -577,6 +762,8 @@ int sdmd_status(sdmd_t h, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_status: NULL handle");
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (PipeCtx& k : h->ctx)
+    if (k.busy) CK(cudaStreamWaitEvent(st, k.ev_done, 0));
   int v = 0;
   CK(cudaMemcpyAsync(&v, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));

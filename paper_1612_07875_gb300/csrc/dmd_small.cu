@@ -1034,7 +1034,7 @@ cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_bytes = bytes;
   }
-  modes_small_kernel<<<1, kThreads, bytes, st>>>(a, modes_layout(a.m));
+  modes_small_kernel<<<1, kThreads, bytes, st>>>(a, modes_layout(a.ws_m));
   return cudaGetLastError();
 }
 

@@ -48,7 +48,8 @@ void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t*
 struct ModesArgs {
   const void* G;        // m x m physical (double or int64)
   int32_t g_is_int;     // 1: int64 entries
-  int32_t m;
+  int32_t m;            // stride of G and modulus of its slot indices
+  int32_t ws_m;         // window length the workspace `ws` was laid out for
   int32_t c;            // resident snapshots (>= 3)
   int32_t start;        // physical slot of the oldest resident snapshot
   int32_t r_req;        // requested modes (1 <= r_req <= c-1)

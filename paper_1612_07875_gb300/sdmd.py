@@ -25,12 +25,14 @@ SDMD_ERR_TIMEOUT = -5
 SDMD_ERR_RANK = -6
 SDMD_ERR_UNSUPPORTED = -7
 SDMD_MAX_M = 256
+SDMD_MAX_DEPTH = 16
 
 SDMD_K_INGEST = 0
 SDMD_K_GRAM_ROW = 1
 SDMD_K_MODES = 2
 SDMD_K_PHI = 3
-SDMD_K_COUNT = 4
+SDMD_K_FRAME = 4
+SDMD_K_COUNT = 5
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsdmd.so")
 
@@ -45,6 +47,10 @@ _I32 = ctypes.c_int32
 _SIGNATURES = {
     "sdmd_create": [_I64, _I32, _I32, ctypes.POINTER(_VP)],
     "sdmd_destroy": [_VP],
+    "sdmd_create_ex": [_I64, _I32, _I32, _I32, ctypes.POINTER(_VP)],
+    "sdmd_step": [_VP, _VP, _I32, _VP, _VP, _VP, _VP],
+    "sdmd_sync": [_VP, _VP],
+    "sdmd_trace_times": [_VP, _I32, ctypes.POINTER(ctypes.c_double), _I32, ctypes.POINTER(_I32)],
     "sdmd_create_sparse": [_I64, _I32, _I32, ctypes.POINTER(_VP)],
     "sdmd_push_sparse": [_VP, _I32, _VP, _VP, _VP],
     "sdmd_push": [_VP, _VP, _VP],
@@ -125,6 +131,20 @@ def sdmd_create(n, m, dtype):
     return h.value
 
 
+def sdmd_create_ex(n, m, dtype, depth):
+    h = _VP()
+    _check(lib().sdmd_create_ex(int(n), int(m), int(dtype), int(depth), ctypes.byref(h)), "sdmd_create_ex")
+    return h.value
+
+
+def sdmd_step(h, x, r, phi, lam, r_out=None, stream=None):
+    _check(lib().sdmd_step(h, ptr(x), int(r), ptr(phi), ptr(lam), ptr(r_out), stream_handle(stream)), "sdmd_step")
+
+
+def sdmd_sync(h, stream=None):
+    _check(lib().sdmd_sync(h, stream_handle(stream)), "sdmd_sync")
+
+
 def sdmd_create_sparse(n, m, nnz_max):
     h = _VP()
     _check(lib().sdmd_create_sparse(int(n), int(m), int(nnz_max), ctypes.byref(h)), "sdmd_create_sparse")
@@ -200,6 +220,14 @@ def sdmd_gram_row_static(dtype, X, ld, c, y, n, g, stream=None):
     """g[j] = <x_j, y> for j < c with no device allocation (see sdmd.h)."""
     _check(lib().sdmd_gram_row_static(int(dtype), ptr(X), int(ld), int(c), ptr(y), int(n), ptr(g),
                                       stream_handle(stream)), "sdmd_gram_row_static")
+
+
+def sdmd_trace_times(h, kernel, cap=100000):
+    """Individual traced durations (ms) of class `kernel` since the last read."""
+    buf = (ctypes.c_double * cap)()
+    cnt = _I32()
+    _check(lib().sdmd_trace_times(h, int(kernel), buf, int(cap), ctypes.byref(cnt)), "sdmd_trace_times")
+    return [buf[i] for i in range(cnt.value)]
 
 
 def exported_symbols():

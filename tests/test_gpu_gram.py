@@ -167,7 +167,7 @@ def test_error_paths(cuda_device):
         assert ei.value.code == S.SDMD_ERR_NOT_READY
         S.sdmd_push(h, x + 1)
         with pytest.raises(S.SdmdError) as ei:
-            S.sdmd_modes(h, 3, None, None)           # r > c-1
+            S.sdmd_modes(h, 4, None, None)           # r > m-1
         assert ei.value.code == S.SDMD_ERR_ARG
         host_phi = np.zeros(2 * 1000 * 2, np.float32)
         with pytest.raises(S.SdmdError) as ei:
