@@ -236,6 +236,17 @@ SDMD_API int sdmd_svd(sdmd_t h, int32_t r, double *sigma, double *V, void *strea
  */
 SDMD_API int sdmd_status(sdmd_t h, void *stream);
 
+/* Options (sdmd_set_option). */
+enum {
+    SDMD_OPT_PHI_TENSOR = 1 /* 1 (default): Phi of uint8 handles on the tensor
+                               cores (tcgen05, bf16 operands: pixels exact,
+                               M = V Sigma^-1 W as three bf16 terms, FP32
+                               accumulation); 0: CUDA-core FP32 kernel */
+};
+
+/* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */
+SDMD_API int sdmd_set_option(sdmd_t h, int32_t option, int64_t value);
+
 /* Kernel classes for tracing. */
 enum {
     SDMD_K_INGEST = 0,    /* snapshot copy into its ring slot (a memcpy)       */

@@ -55,6 +55,7 @@ struct sdmd_s {
   int32_t last_r = 0;         // r of the last sdmd_modes call (0 = none)
   int32_t last_p = 0;
   int64_t gsz = 8;            // bytes per G entry (16 for complex handles)
+  int32_t phi_tensor = 1;     // SDMD_OPT_PHI_TENSOR
   // sparse handles
   int32_t nnz_max = 0;
   int* idx_ring = nullptr;    // m x nnz_max indices
@@ -583,6 +584,8 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
     pa.Mf = reinterpret_cast<const float*>(h->ws + L.Mf);
     pa.r_dev = h->r_dev;
     pa.phi = static_cast<float*>(phi);
+    pa.status = h->status;
+    pa.tensor = h->phi_tensor;
     TraceScope ts(h, SDMD_K_PHI, st);
     CK(launch_phi(pa, st));
   }
@@ -662,6 +665,8 @@ int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32
     pa.Mf = reinterpret_cast<const float*>(k.ws + L.Mf);
     pa.r_dev = k.r_dev;
     pa.phi = static_cast<float*>(phi);
+    pa.status = h->status;
+    pa.tensor = h->phi_tensor;
     TraceScope ts(h, SDMD_K_PHI, k.st);
     CK(launch_phi(pa, k.st));
   }
@@ -704,6 +709,17 @@ int sdmd_svd(sdmd_t h, int32_t r, double* sigma, double* V, void* stream) {
     if (rc != SDMD_OK) return rc;
   }
   return SDMD_OK;
+}
+
+int sdmd_set_option(sdmd_t h, int32_t option, int64_t value) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_set_option: NULL handle");
+  switch (option) {
+    case SDMD_OPT_PHI_TENSOR:
+      h->phi_tensor = value ? 1 : 0;
+      return SDMD_OK;
+    default:
+      return fail(SDMD_ERR_ARG, "sdmd_set_option: unknown option %d", option);
+  }
 }
 
 int sdmd_trace(sdmd_t h, int32_t enable) {

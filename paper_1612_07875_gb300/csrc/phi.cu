@@ -174,6 +174,10 @@ cudaError_t launch_for_type(const PhiArgs& a, cudaStream_t st, int sms) {
 }  // namespace
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st) {
+  if (a.tensor && a.dtype == SDMD_U8) {
+    const cudaError_t e = launch_phi_tc(a, st);
+    if (e != cudaErrorNotSupported) return e;
+  }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -82,9 +82,13 @@ struct PhiArgs {
   const float* Mf;      // p x 2r  (re, im) of V Sigma^-1 W, FP32
   const int* r_dev;     // kept rank; columns >= *r_dev are written as zero
   float* phi;           // n x r complex64, column-major
+  int* status;          // device status word
+  int32_t tensor;       // 1: use the tensor-core kernel where it applies
 };
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
+// tcgen05 kernel for uint8 windows; cudaErrorNotSupported outside its shapes
+cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st);
 
 struct SparseRowArgs {
   const int* idx_ring;       // slot j's indices at idx_ring + j * nnz_max

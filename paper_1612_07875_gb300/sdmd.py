@@ -27,6 +27,8 @@ SDMD_ERR_UNSUPPORTED = -7
 SDMD_MAX_M = 256
 SDMD_MAX_DEPTH = 16
 
+SDMD_OPT_PHI_TENSOR = 1
+
 SDMD_K_INGEST = 0
 SDMD_K_GRAM_ROW = 1
 SDMD_K_MODES = 2
@@ -50,6 +52,7 @@ _SIGNATURES = {
     "sdmd_create_ex": [_I64, _I32, _I32, _I32, ctypes.POINTER(_VP)],
     "sdmd_step": [_VP, _VP, _I32, _VP, _VP, _VP, _VP],
     "sdmd_sync": [_VP, _VP],
+    "sdmd_set_option": [_VP, _I32, _I64],
     "sdmd_trace_times": [_VP, _I32, ctypes.POINTER(ctypes.c_double), _I32, ctypes.POINTER(_I32)],
     "sdmd_create_sparse": [_I64, _I32, _I32, ctypes.POINTER(_VP)],
     "sdmd_push_sparse": [_VP, _I32, _VP, _VP, _VP],
@@ -188,6 +191,10 @@ def sdmd_svd(h, r, sigma, V, stream=None):
 
 def sdmd_status(h, stream=None):
     return lib().sdmd_status(h, stream_handle(stream))
+
+
+def sdmd_set_option(h, option, value):
+    _check(lib().sdmd_set_option(h, int(option), int(value)), "sdmd_set_option")
 
 
 def sdmd_trace(h, enable):

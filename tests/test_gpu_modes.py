@@ -219,3 +219,41 @@ def test_full_size_hd_video_modes(cuda_device):
         assert (np.abs(got - Pref).max(axis=0) <= 1e-4 * scale).all()
     finally:
         S.sdmd_destroy(h)
+
+
+@pytest.mark.parametrize("n,m,r", [(72 * 128 * 3, 20, 8), (1000, 12, 5), (4096 + 77, 40, 17), (128 * 40 + 3, 120, 3),
+                                   (5000, 150, 9), (3000, 256, 12)])
+def test_phi_tensor_core_matches_cuda_core_and_oracle(cuda_device, n, m, r):
+    # uint8 windows: Phi on tcgen05 (fp16 pixels exact, M in three fp16
+    # terms, FP32 accumulation) against the FP32 CUDA-core kernel and the
+    # FP64 oracle product X' M with the same M; the shapes cover every
+    # K padding / chunking configuration of the kernel.
+    rng = np.random.default_rng(n + m)
+    base = rng.integers(0, 200, n)
+    frames = [np.clip(base + rng.integers(-40, 41, n), 0, 255).astype(np.uint8) for _ in range(m + 2)]
+    h = S.sdmd_create(n, m, S.SDMD_U8)
+    try:
+        for f in frames:
+            S.sdmd_push(h, torch.from_numpy(f).to(cuda_device))
+        outs = {}
+        for tensor in (1, 0):
+            S.sdmd_set_option(h, S.SDMD_OPT_PHI_TENSOR, tensor)
+            phi = torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device)
+            lam = np.zeros(2 * r)
+            S.sdmd_modes(h, r, phi, lam)
+            torch.cuda.synchronize()
+            P = phi.cpu().numpy()
+            outs[tensor] = P[..., 0] + 1j * P[..., 1]
+        assert S.sdmd_status(h) == S.SDMD_OK
+        scale = np.abs(outs[0]).max(axis=1, keepdims=True) + 1e-30
+        assert (np.abs(outs[1] - outs[0]) <= 2e-5 * scale).all()
+        # against the oracle product with the oracle's M on the same window
+        W = np.stack(frames[-m:], axis=1)
+        ref = oracle.exact_dmd(W, r)
+        lam_c = lam[0::2] + 1j * lam[1::2]
+        err, perm = match_eigs(lam_c[:ref.r], ref.lam)
+        Pn = normalize_cols(outs[1][:ref.r].T)
+        Rn = normalize_cols(ref.Phi[:, perm])
+        assert rel_fro(Pn, Rn) <= 1e-4
+    finally:
+        S.sdmd_destroy(h)
