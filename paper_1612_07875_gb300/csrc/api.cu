@@ -20,6 +20,7 @@ using namespace sdmd;
 struct PipeCtx {
   double* ws = nullptr;       // modes workspace (window m)
   int* r_dev = nullptr;
+  unsigned* phi_sched = nullptr;  // Phi tile-scheduling words (zero between launches)
   void* gsnap = nullptr;      // time-ordered c x c copy of G for this frame
   cudaStream_t st = nullptr;
   cudaEvent_t ev_g = nullptr;     // G snapshot taken (push stream)
@@ -50,6 +51,7 @@ struct sdmd_s {
   double* ws = nullptr;       // modes workspace
   int* status = nullptr;      // device status word
   int* r_dev = nullptr;       // device int: kept rank of the last modes call
+  unsigned* phi_sched = nullptr;  // Phi tile-scheduling words (zero between launches)
   int64_t count = 0;
   int32_t head = 0;
   int32_t last_r = 0;         // r of the last sdmd_modes call (0 = none)
@@ -200,6 +202,7 @@ void free_ctx(sdmd_s* h) {
     if (c.st) cudaStreamSynchronize(c.st);
     cudaFree(c.ws);
     cudaFree(c.r_dev);
+    cudaFree(c.phi_sched);
     cudaFree(c.gsnap);
     if (c.ev_g) cudaEventDestroy(c.ev_g);
     if (c.ev_done) cudaEventDestroy(c.ev_done);
@@ -221,6 +224,7 @@ void free_all(sdmd_s* h) {
   cudaFree(h->ws);
   cudaFree(h->status);
   cudaFree(h->r_dev);
+  cudaFree(h->phi_sched);
 }
 
 inline int32_t resident(const sdmd_s* h) { return (int32_t)(h->count < h->m ? h->count : h->m); }
@@ -284,6 +288,8 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->phi_sched, kPhiSchedWords * sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->phi_sched, 0, kPhiSchedWords * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->ring, 0, ring_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->G, 0, gbytes);
   if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
@@ -294,6 +300,8 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
       if (e == cudaSuccess) e = cudaMalloc(&c.ws, ws_bytes);
       if (e == cudaSuccess) e = cudaMemset(c.ws, 0, ws_bytes);
       if (e == cudaSuccess) e = cudaMalloc(&c.r_dev, sizeof(int));
+      if (e == cudaSuccess) e = cudaMalloc(&c.phi_sched, kPhiSchedWords * sizeof(unsigned));
+      if (e == cudaSuccess) e = cudaMemset(c.phi_sched, 0, kPhiSchedWords * sizeof(unsigned));
       if (e == cudaSuccess) e = cudaMalloc(&c.gsnap, (size_t)m * m * h->gsz);
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_g, cudaEventDisableTiming);
@@ -586,6 +594,7 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
     pa.phi = static_cast<float*>(phi);
     pa.status = h->status;
     pa.tensor = h->phi_tensor;
+    pa.sched = h->phi_sched;
     TraceScope ts(h, SDMD_K_PHI, st);
     CK(launch_phi(pa, st));
   }
@@ -667,6 +676,7 @@ int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32
     pa.phi = static_cast<float*>(phi);
     pa.status = h->status;
     pa.tensor = h->phi_tensor;
+    pa.sched = k.phi_sched;
     TraceScope ts(h, SDMD_K_PHI, k.st);
     CK(launch_phi(pa, k.st));
   }

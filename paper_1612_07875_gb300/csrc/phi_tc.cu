@@ -18,18 +18,32 @@
 // 128 B between position groups (stride offset). B core (ng, kg) is K-major
 // at (kg * 12 + ng) * 128 bytes: LBO 1536 B, SBO 128 B.
 //
-// Warp roles in a persistent CTA of 9 warps (one CTA per SM):
-//   warps 4..7  load + convert: each thread owns fixed 16-byte chunks of the
-//               tile (one window slot x 16 positions) and streams them with
-//               cp.async (16 B, L2 only) through a private 4-deep staging
-//               ring (row pitch 144 B: the 16-byte reads of eight consecutive
-//               slots by a quarter warp hit distinct banks); it converts only
-//               chunks it loaded itself, so stages need no barrier, then
-//               writes the fp16 A tile (double-buffered);
-//   warp 8      lane 0 issues the K/16 MMAs of a tile into one of two TMEM
+// Scheduling: persistent CTAs take chunks of 8 consecutive tiles from a
+// per-pass global counter (atomicAdd), so a CTA that starts late (its SM
+// busy with another stream's kernel) just finds less work; the last CTA to
+// finish zeroes the counters for the next launch. Tile indices travel from
+// the converters to the MMA issuer and the epilogue through a 16-entry ring
+// in shared memory, ordered by the same mbarriers as the data; index -1 ends
+// every role's loop. Staging rows (128 bytes, one tile) have their 16-byte
+// chunks XOR-swizzled by the slot's low three bits (conflict-free copies
+// and reads).
+//
+// Warp roles in a persistent CTA of up to 12 warps (one CTA per SM):
+//   warps 5..   load + convert (K / 16, K / 32 or 4 warps: 4, 8 or 16 units
+//               per lane per tile). Warp-private units: per tile and step j
+//               a warp owns 8 slots x 64 positions; it copies them with
+//               cp.async (16 B, L2 only; a quarter warp reads two whole
+//               64-byte row pieces, since 16-byte accesses coalesce only
+//               within a quarter warp) and, after cp.async.wait_group and
+//               __syncwarp, every lane converts one 16-byte chunk of eight
+//               different slots, so its A-tile stores hit distinct banks.
+//               A tiles go into a ring of up to 4 buffers;
+//   warp 4      lane 0 issues the K/16 MMAs of a tile into one of four TMEM
 //               accumulators and commits them to mbarriers;
 //   warps 0..3  epilogue: tcgen05.ld of their 32 TMEM lanes, sum and scale,
 //               complex64 stores of Phi (coalesced per mode).
+// The A and accumulator rings are deep because a tile is small: the
+// hand-offs between the roles take longer than the work of one tile.
 // Every mbarrier wait is bounded (about one second): on expiry the kernel
 // raises kDevTimeout, every role stops at its next step, the converters
 // drain their copies in flight, the MMA issuer waits (bounded) for its last
@@ -53,9 +67,12 @@ constexpr int kModes = 16;           // modes per pass (gridDim.y covers r)
 constexpr int kCols = 2 * kModes;    // re/im columns of one fp16 term
 constexpr int kSplits = 3;
 constexpr int kN = kSplits * kCols;  // 96 accumulator columns per tile
-constexpr int kTmemCols = 256;       // two accumulators, power of two
-constexpr int kPitch = 144;          // staging row pitch, bytes
+constexpr int kAcc = 4;              // TMEM accumulators (ring)
+constexpr int kMaxA = 4;             // A-tile buffers (ring)
+constexpr int kTmemCols = 512;       // kAcc x kN = 384, power of two
 constexpr int kMaxRows = 256;        // K padded (p <= 255)
+constexpr int kChunk = 8;            // tiles per scheduling grab
+constexpr int kTix = 16;             // tile-index ring
 constexpr long long kWaitCycles = 2000000000LL;
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -66,6 +83,10 @@ __device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
 
 __device__ __forceinline__ void mbar_arrive(unsigned bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive2(unsigned bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], 2;\n" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
@@ -93,6 +114,17 @@ __device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// wait until at most n (0..5) of this thread's newest copy groups are pending
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: cp_async_wait<0>(); break;
+    case 1: cp_async_wait<1>(); break;
+    case 2: cp_async_wait<2>(); break;
+    case 3: cp_async_wait<3>(); break;
+    case 4: cp_async_wait<4>(); break;
+    default: cp_async_wait<5>(); break;
+  }
+}
 
 // tcgen05 shared-memory matrix descriptor, no swizzle: `lbo` is the byte
 // distance between core matrices adjacent along K, `sbo` along M or N.
@@ -155,15 +187,19 @@ __device__ __forceinline__ unsigned f16x2_of_bytes(unsigned w, unsigned sel) {
 }
 
 struct TcShared {
-  unsigned long long a_full[2];           // A buffer converted
-  unsigned long long a_free[2];           // MMAs reading the A buffer done
-  unsigned long long acc_full[2];         // accumulator complete
-  unsigned long long acc_empty[2];        // accumulator drained
+  unsigned long long a_full[kMaxA];       // A buffer converted
+  unsigned long long a_free[kMaxA];       // MMAs reading the A buffer done
+  unsigned long long acc_full[kAcc];      // accumulator complete (MMA commit + issuer's release)
+  unsigned long long acc_empty[kAcc];     // accumulator drained
   unsigned tmem_base;
   int stop;
+  unsigned long long chunk_bar[2];        // chunk start published (by chunk parity)
+  int chunk[2];                           // tile chunks grabbed by the converter leader (by parity)
+  int tix[kTix];                          // tile index of iteration it at it % kTix, -1: no more
   int expo[kCols];                        // per-column power-of-two scaling of M
 };
 
+// Dynamic shared memory: A ring, B, staging ring, slot offsets, state.
 struct TcLayout {
   int a_bytes, b_off, b_bytes, st_off, st_bytes, tab_off, sh_off, total;
 };
@@ -173,18 +209,36 @@ __host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages) {
   L.a_bytes = kTileM * kpad * 2;                 // multiple of 4096
   L.b_off = n_a * L.a_bytes;
   L.b_bytes = kN * kpad * 2;                     // multiple of 3072
-  L.st_off = L.b_off + L.b_bytes;                // 16-byte aligned (bulk copy destination)
-  L.st_bytes = kpad * kPitch;
+  L.st_off = L.b_off + L.b_bytes;                // 16-byte aligned (cp.async destination)
+  L.st_bytes = kpad * kTileM;
   L.tab_off = L.st_off + stages * L.st_bytes;    // window slot offsets (int64)
   L.sh_off = L.tab_off + kMaxRows * 8;
   L.total = L.sh_off + (int)sizeof(TcShared);
   return L;
 }
 
-template <int kStages, int kIpt>
-__global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, int kpad, int n_a) {
+// Position in a ring of `size` buffers and the parity of the current use.
+struct Ring {
+  int idx = 0;
+  unsigned phase = 0;
+  __device__ __forceinline__ void next(int size) {
+    if (++idx == size) {
+      idx = 0;
+      phase ^= 1u;
+    }
+  }
+};
+
+__device__ __forceinline__ void raise_timeout(const PhiArgs& a, volatile int* stop) {
+  atomicOr(a.status, kDevTimeout);
+  *stop = 1;
+}
+
+template <int kIpt>
+__global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, int kpad, int n_a, int stages) {
+  constexpr int kU = kTileM;             // staging row bytes
   extern __shared__ __align__(1024) uint8_t smem[];
-  const TcLayout L = tc_layout(kpad, n_a, kStages);
+  const TcLayout L = tc_layout(kpad, n_a, stages);
   uint8_t* abuf = smem;
   uint8_t* bbuf = smem + L.b_off;
   uint8_t* stg = smem + L.st_off;
@@ -196,15 +250,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   const int conv_warps = (nthreads >> 5) - kConvWarp0;   // = kpad / (4 kIpt)
   const int k0 = blockIdx.y * kModes;
   const int nks = kpad / 16;
-  const int64_t ntiles = (a.n + kTileM - 1) / kTileM;
-  const int64_t first = blockIdx.x, stride = gridDim.x;
-  const int64_t mine = (first < ntiles) ? (ntiles - first + stride - 1) / stride : 0;
+  const int ntiles = (int)((a.n + kTileM - 1) / kTileM);
 
   if (tid == 0) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kMaxA; ++b) {
       mbar_init(smem_u32(&sh.a_full[b]), (unsigned)conv_warps);
       mbar_init(smem_u32(&sh.a_free[b]), 1);
-      mbar_init(smem_u32(&sh.acc_full[b]), 1);
+    }
+    for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&sh.chunk_bar[b]), 1);
+    for (int b = 0; b < kAcc; ++b) {
+      mbar_init(smem_u32(&sh.acc_full[b]), 2);
       mbar_init(smem_u32(&sh.acc_empty[b]), kEpiWarps);
     }
     sh.stop = 0;
@@ -259,73 +314,133 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 
   if (warp >= kConvWarp0) {
     // ---------------- load + convert ----------------
-    // chunk j of this thread is item ct + j T of the tile's K x 8 items
-    // (T = converter threads): slot row q = 8 kg + kr, positions 16 pc ..
-    // 16 pc + 15; every thread owns exactly kIpt chunks
-    const int ct = tid - 32 * kConvWarp0;
-    const int T = 32 * conv_warps;
-    int64_t src[kIpt];                      // byte offset in the ring (without the tile), -1: row >= p
-    unsigned sto[kIpt], ao[kIpt];           // staging and A-tile byte offsets
+    // step j of converter warp cw covers u = cw + conv_warps j: slot group
+    // kg = u / 2 (slots 8 kg .. 8 kg + 7) and positions 64 h .. 64 h + 63
+    // (h = u % 2) of a tile; every (kg, h) is covered exactly once
+    const int cw = warp - kConvWarp0;
+    int64_t src[kIpt];                      // copy source in the ring (without tile), -1: slot >= p
+    unsigned ldo[kIpt];                     // copy destination in a stage (first tile's segment)
+    unsigned sto[kIpt], ao[kIpt];           // conversion source in a stage, A-tile destination
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
-      const int item = ct + j * T;
-      const int kr = item & 7, pc = (item >> 3) & 7, kg = item >> 6;
-      const int q = 8 * kg + kr;
-      src[j] = (q < a.p) ? tab[q] + 16 * pc : -1;
-      sto[j] = (unsigned)(q * kPitch + 16 * pc);
+      const int u = cw + conv_warps * j;
+      const int kg = u >> 1, h = u & 1;
+      // copy: lane -> slot 8 kg + lr, chunk pl (a quarter warp: slots r and r + 4, 4 chunks each)
+      const int lr = (lane >> 3) + 4 * ((lane >> 2) & 1), pl = 4 * h + (lane & 3);
+      const int ql = 8 * kg + lr;
+      src[j] = (ql < a.p) ? tab[ql] + 16 * pl : -1;
+      ldo[j] = (unsigned)(ql * kU + 16 * (pl ^ lr));
+      // conversion: lane -> slot 8 kg + kr, chunk pc (a quarter warp: 8 slots, one chunk)
+      const int kr = lane & 7, pc = 4 * h + (lane >> 3);
+      sto[j] = (unsigned)((8 * kg + kr) * kU + 16 * (pc ^ kr));
       ao[j] = (unsigned)((kg * 16 + 2 * pc) * 128 + kr * 16);   // core (2 pc, kg), row kr
     }
-    const unsigned stg0 = smem_u32(stg);
-    auto load_tile = [&](int64_t it) {
-      const int64_t i0 = (first + it * stride) * kTileM;
-      const unsigned dst = stg0 + (unsigned)((it % kStages) * L.st_bytes);
-#pragma unroll
-      for (int j = 0; j < kIpt; ++j)
-        if (src[j] >= 0) cp_async16(dst + sto[j], a.ring + src[j] + i0);
+    // tile sequence: chunk c (iterations 8 c .. 8 c + 7 of this CTA) starts
+    // at the tile index the leader grabbed and published through chunk_bar
+    // (by chunk parity: the A ring keeps every converter warp within a few
+    // tiles of the leader, so a slot is rewritten only after all have read
+    // it); an index is fixed when its copies are issued, kStages - 1
+    // iterations before the tile is converted
+    const int ct = tid - 32 * kConvWarp0;
+    int ld_count = 0;                        // tiles whose index is fixed
+    bool ended = false;                      // an index past the last tile was seen
+    int nvalid = 0;                          // (once ended) iterations 0 .. nvalid - 1 have tiles
+    int cbase = 0;                           // start of the chunk being fixed
+    auto fix_next = [&]() -> int {           // all converter threads, in step
+      int t = -1;
+      if (!ended) {
+        const int c = ld_count / kChunk, o = ld_count % kChunk;
+        if (o == 0) {
+          const unsigned bar = smem_u32(&sh.chunk_bar[c & 1]);
+          if (ct == 0) {
+            sh.chunk[c & 1] = (int)atomicAdd(&a.sched[blockIdx.y], (unsigned)kChunk);
+            mbar_arrive(bar);
+          }
+          int ok = 1;
+          if (lane == 0) ok = mbar_wait(bar, (unsigned)((c >> 1) & 1));
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          __syncwarp();
+          if (ok) {
+            cbase = sh.chunk[c & 1];
+          } else {
+            if (lane == 0) raise_timeout(a, stop);
+            cbase = ntiles;                  // end the sequence here
+          }
+        }
+        t = cbase + o;
+        if (t >= ntiles) {
+          t = -1;
+          ended = true;
+          nvalid = ld_count;
+        }
+      }
+      if (ct == 0) sh.tix[ld_count % kTix] = t;
+      ++ld_count;
+      return t;
     };
+    const unsigned stg0 = smem_u32(stg);
+    int ld_stage = 0;
+    auto load_next = [&]() {
+      const int t = fix_next();
+      if (t >= 0) {
+        const unsigned dst = stg0 + (unsigned)(ld_stage * L.st_bytes);
+        const uint8_t* tsrc = a.ring + (int64_t)t * kTileM;
 #pragma unroll
-    for (int st = 0; st < kStages - 1; ++st) {
-      if (st < mine) load_tile(st);
+        for (int j = 0; j < kIpt; ++j)
+          if (src[j] >= 0) cp_async16(dst + ldo[j], tsrc + src[j]);
+      }
+      ld_stage = (ld_stage + 1 == stages) ? 0 : ld_stage + 1;
+    };
+    for (int st = 0; st < stages - 1; ++st) {
+      load_next();
       cp_async_commit();
     }
-    for (int64_t it = 0; it < mine; ++it) {
-      if (*stop) break;
-      if (it + kStages - 1 < mine) load_tile(it + kStages - 1);
+    int stage = 0;
+    Ring ab;                                 // A buffer of the current tile
+    for (int it = 0; !*stop; ++it) {
+      const bool valid = !(ended && it >= nvalid);   // tile `it` exists
+      load_next();
       cp_async_commit();
-      cp_async_wait<kStages - 1>();          // this thread's chunks of tile `it` have landed
-      const int b = (int)(it % n_a);
-      int ok = 1;
-      if (lane == 0 && it >= n_a) ok = mbar_wait(smem_u32(&sh.a_free[b]), (unsigned)(((it / n_a) - 1) & 1));
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      if (!ok) {
-        if (lane == 0) {
-          atomicOr(a.status, kDevTimeout);
-          *stop = 1;
+      cp_async_wait_pending(stages - 1);     // this lane's copies of tile `it` have landed
+      __syncwarp();                          // ... and those of the other lanes of the warp
+      const uint8_t* sb = stg + stage * L.st_bytes;
+      stage = (stage + 1 == stages) ? 0 : stage + 1;
+      {
+        int ok = 1;
+        if (lane == 0 && it >= n_a) ok = mbar_wait(smem_u32(&sh.a_free[ab.idx]), ab.phase ^ 1u);
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (!ok) {
+          if (lane == 0) raise_timeout(a, stop);
+          break;
         }
-        break;
-      }
-      const uint8_t* sb = stg + (size_t)(it % kStages) * L.st_bytes;
-      uint8_t* ab = abuf + (size_t)b * L.a_bytes;
-      uint4 w[kIpt];
+        if (!valid) {                        // past the last tile: hand the end on and stop
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&sh.a_full[ab.idx]));
+          break;
+        }
+        uint8_t* abt = abuf + (size_t)ab.idx * L.a_bytes;
+        uint4 w[kIpt];
 #pragma unroll
-      for (int j = 0; j < kIpt; ++j) w[j] = *reinterpret_cast<const uint4*>(sb + sto[j]);
+        for (int j = 0; j < kIpt; ++j) w[j] = *reinterpret_cast<const uint4*>(sb + sto[j]);
 #pragma unroll
-      for (int j = 0; j < kIpt; ++j) {
-        uint4 lo, hi;
-        lo.x = f16x2_of_bytes(w[j].x, 0x4140u);
-        lo.y = f16x2_of_bytes(w[j].x, 0x4342u);
-        lo.z = f16x2_of_bytes(w[j].y, 0x4140u);
-        lo.w = f16x2_of_bytes(w[j].y, 0x4342u);
-        hi.x = f16x2_of_bytes(w[j].z, 0x4140u);
-        hi.y = f16x2_of_bytes(w[j].z, 0x4342u);
-        hi.z = f16x2_of_bytes(w[j].w, 0x4140u);
-        hi.w = f16x2_of_bytes(w[j].w, 0x4342u);
-        *reinterpret_cast<uint4*>(ab + ao[j]) = lo;
-        *reinterpret_cast<uint4*>(ab + ao[j] + 128) = hi;
+        for (int j = 0; j < kIpt; ++j) {
+          uint4 lo, hi;
+          lo.x = f16x2_of_bytes(w[j].x, 0x4140u);
+          lo.y = f16x2_of_bytes(w[j].x, 0x4342u);
+          lo.z = f16x2_of_bytes(w[j].y, 0x4140u);
+          lo.w = f16x2_of_bytes(w[j].y, 0x4342u);
+          hi.x = f16x2_of_bytes(w[j].z, 0x4140u);
+          hi.y = f16x2_of_bytes(w[j].z, 0x4342u);
+          hi.z = f16x2_of_bytes(w[j].w, 0x4140u);
+          hi.w = f16x2_of_bytes(w[j].w, 0x4342u);
+          *reinterpret_cast<uint4*>(abt + ao[j]) = lo;
+          *reinterpret_cast<uint4*>(abt + ao[j] + 128) = hi;
+        }
+        fence_proxy_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&sh.a_full[ab.idx]));
+        ab.next(n_a);
       }
-      fence_proxy_async();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sh.a_full[b]));
     }
     cp_async_wait<0>();                      // no copy lands after the CTA exits
   } else if (warp == kMmaWarp) {
@@ -333,30 +448,38 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     if (lane == 0) {
       const uint32_t idesc = idesc_f16_amn(kTileM, kN);
       const unsigned bbase = smem_u32(bbuf);
-      int64_t commits = 0;
-      for (int64_t it = 0; it < mine; ++it) {
+      Ring ab, acc, last;
+      int issued = 0;
+      for (int it = 0;; ++it) {
         if (*stop) break;
-        const int b = (int)(it % n_a), ab = (int)(it & 1);
-        bool ok = mbar_wait(smem_u32(&sh.a_full[b]), (unsigned)((it / n_a) & 1));
-        if (ok && it >= 2) ok = mbar_wait(smem_u32(&sh.acc_empty[ab]), (unsigned)(((it >> 1) - 1) & 1));
+        bool ok = mbar_wait(smem_u32(&sh.a_full[ab.idx]), ab.phase);
+        if (ok && it >= kAcc) ok = mbar_wait(smem_u32(&sh.acc_empty[acc.idx]), acc.phase ^ 1u);
         if (!ok) {
-          atomicOr(a.status, kDevTimeout);
-          *stop = 1;
+          raise_timeout(a, stop);
+          break;
+        }
+        if (sh.tix[it % kTix] < 0) {         // no more tiles: hand the end to the epilogue
+          mbar_arrive2(smem_u32(&sh.acc_full[acc.idx]));
           break;
         }
         fence_after();
-        const unsigned abase = smem_u32(abuf + (size_t)b * L.a_bytes);
+        const unsigned abase = smem_u32(abuf + (size_t)ab.idx * L.a_bytes);
+        const unsigned dt = tbase + (unsigned)(acc.idx * kN);
         for (int ks = 0; ks < nks; ++ks) {
           const uint64_t ad = smem_desc(abase + (unsigned)ks * 4096u, 2048u, 128u);
           const uint64_t bd = smem_desc(bbase + (unsigned)ks * 2u * (kN / 8) * 128u, (kN / 8) * 128u, 128u);
-          mma_f16(tbase + (unsigned)(ab * kN), ad, bd, idesc, ks > 0 ? 1u : 0u);
+          mma_f16(dt, ad, bd, idesc, ks > 0 ? 1u : 0u);
         }
-        mma_commit(smem_u32(&sh.a_free[b]));
-        mma_commit(smem_u32(&sh.acc_full[ab]));
-        commits = it + 1;
+        mma_commit(smem_u32(&sh.a_free[ab.idx]));
+        mma_commit(smem_u32(&sh.acc_full[acc.idx]));
+        mbar_arrive(smem_u32(&sh.acc_full[acc.idx]));   // release: the epilogue sees tix[]
+        issued = it + 1;
+        last = acc;
+        ab.next(n_a);
+        acc.next(kAcc);
       }
       // no MMA may still write tensor memory when it is freed
-      if (commits > 0) mbar_wait(smem_u32(&sh.acc_full[(commits - 1) & 1]), (unsigned)(((commits - 1) >> 1) & 1));
+      if (issued > 0) mbar_wait(smem_u32(&sh.acc_full[last.idx]), last.phase);
     }
   } else {
     // ---------------- epilogue (warps 0..3 own TMEM lanes 32w .. 32w + 31) ----------------
@@ -364,22 +487,22 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 #pragma unroll
     for (int c = 0; c < kCols; ++c) sc[c] = ldexpf(1.f, -sh.expo[c]);
     float2* out = reinterpret_cast<float2*>(a.phi);
-    for (int64_t it = 0; it < mine; ++it) {
+    Ring acc;
+    for (int it = 0;; ++it) {
       if (*stop) break;
-      const int ab = (int)(it & 1);
       int ok = 1;
-      if (lane == 0) ok = mbar_wait(smem_u32(&sh.acc_full[ab]), (unsigned)((it >> 1) & 1));
+      if (lane == 0) ok = mbar_wait(smem_u32(&sh.acc_full[acc.idx]), acc.phase);
       ok = __shfl_sync(0xffffffffu, ok, 0);
       if (!ok) {
-        if (lane == 0) {
-          atomicOr(a.status, kDevTimeout);
-          *stop = 1;
-        }
+        if (lane == 0) raise_timeout(a, stop);
         break;
       }
+      const int t = sh.tix[it % kTix];
+      if (t < 0) break;                      // no more tiles
+      const int64_t i = (int64_t)t * kTileM + 32 * warp + lane;
       fence_after();
       unsigned v0[32], v1[32], v2[32];
-      const unsigned taddr = tbase + ((unsigned)(32 * warp) << 16) + (unsigned)(ab * kN);
+      const unsigned taddr = tbase + ((unsigned)(32 * warp) << 16) + (unsigned)(acc.idx * kN);
       tmem_ld32_nowait(taddr, v0);
       tmem_ld32_nowait(taddr + kCols, v1);
       tmem_ld32_nowait(taddr + 2 * kCols, v2);
@@ -392,8 +515,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       }
       fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sh.acc_empty[ab]));
-      const int64_t i = (first + it * stride) * kTileM + 32 * warp + lane;
+      if (lane == 0) mbar_arrive(smem_u32(&sh.acc_empty[acc.idx]));
+      acc.next(kAcc);
       if (i < a.n) {
 #pragma unroll
         for (int q = 0; q < kModes; ++q) {
@@ -412,14 +535,24 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   __syncwarp();
   if (warp == kMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(kTmemCols) : "memory");
+  // the last CTA out (all grabs are done) zeroes the counters for the next launch
+  if (tid == 0) {
+    __threadfence();
+    const unsigned total = gridDim.x * gridDim.y;
+    if (atomicAdd(&a.sched[kPhiSchedPasses], 1u) == total - 1u) {
+      for (unsigned y = 0; y < gridDim.y; ++y) a.sched[y] = 0u;
+      a.sched[kPhiSchedPasses] = 0u;
+      __threadfence();
+    }
+  }
 }
 
-template <int kStages, int kIpt>
-cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, size_t smem) {
+template <int kIpt>
+cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem) {
   static size_t attr = 0;
   if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(phi_tc_u8_kernel<kStages, kIpt>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(phi_tc_u8_kernel<kIpt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = smem;
   }
@@ -433,7 +566,7 @@ cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, siz
   if (bx > ntiles) bx = ntiles;
   if (bx < 1) bx = 1;
   const int threads = 32 * (kConvWarp0 + kpad / (4 * kIpt));
-  phi_tc_u8_kernel<kStages, kIpt><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a);
+  phi_tc_u8_kernel<kIpt><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
   return cudaGetLastError();
 }
 
@@ -443,10 +576,10 @@ cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, siz
 // shape is outside what this kernel handles (the caller then uses the SIMT
 // kernel).
 cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st) {
-  if (a.dtype != SDMD_U8 || a.p < 1 || a.p >= kMaxRows) return cudaErrorNotSupported;
-  // K padding and chunks per converter thread, at most 7 converter warps:
-  // K <= 112: 4 chunks (K / 16 warps); K <= 224: K to a multiple of 32 and
-  // 8 chunks (K / 32 warps); else K = 256 and 16 chunks (4 warps)
+  if (a.dtype != SDMD_U8 || a.p < 1 || a.p >= kMaxRows || a.sched == nullptr) return cudaErrorNotSupported;
+  // K padding and units per converter lane, at most 7 converter warps:
+  // K <= 112: 4 units (K / 16 warps); K <= 224: K to a multiple of 32 and
+  // 8 units (K / 32 warps); else K = 256 and 16 units (4 warps)
   int kpad = ((a.p + 15) / 16) * 16, ipt = 4;
   if (kpad > 112) {
     kpad = ((a.p + 31) / 32) * 32;
@@ -456,21 +589,18 @@ cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st) {
       ipt = 16;
     }
   }
-  // the deepest copy ring and double-buffered A that fit in 227 KiB
-  static const int kConfigs[4][2] = {{2, 6}, {2, 3}, {1, 6}, {1, 3}};
+  // deepest A ring first, then the deepest staging ring, within 227 KiB
+  static const int kConfigs[][2] = {{4, 6}, {4, 5}, {4, 4}, {3, 5}, {3, 4}, {2, 6}, {2, 4}, {2, 3}, {1, 4}, {1, 3}};
   const int kLimit = 227 * 1024;
   for (const auto& cf : kConfigs) {
     const TcLayout L = tc_layout(kpad, cf[0], cf[1]);
     if (L.total > kLimit) continue;
-    // at least 80 KiB: at most two of these CTAs share an SM, so their tensor
-    // memory (256 columns each) always fits the SM's 512 columns
-    const size_t smem = L.total < 80 * 1024 ? 80 * 1024 : (size_t)L.total;
-    // instantiated combinations: K <= 112 always fits (2, 6); K = 256 only
-    // fits (1, 3)
-    const bool deep = cf[1] == 6;
-    if (ipt == 4 && deep) return launch_cfg<6, 4>(a, st, kpad, cf[0], smem);
-    if (ipt == 8) return deep ? launch_cfg<6, 8>(a, st, kpad, cf[0], smem) : launch_cfg<3, 8>(a, st, kpad, cf[0], smem);
-    if (ipt == 16 && !deep) return launch_cfg<3, 16>(a, st, kpad, cf[0], smem);
+    // at least 116 KiB: one of these CTAs per SM, so its 512 tensor-memory
+    // columns are always free
+    const size_t smem = L.total < 116 * 1024 ? 116 * 1024 : (size_t)L.total;
+    if (ipt == 4) return launch_cfg<4>(a, st, kpad, cf[0], cf[1], smem);
+    if (ipt == 8) return launch_cfg<8>(a, st, kpad, cf[0], cf[1], smem);
+    return launch_cfg<16>(a, st, kpad, cf[0], cf[1], smem);
   }
   return cudaErrorNotSupported;
 }

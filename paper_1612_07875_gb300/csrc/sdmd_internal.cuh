@@ -84,7 +84,10 @@ struct PhiArgs {
   float* phi;           // n x r complex64, column-major
   int* status;          // device status word
   int32_t tensor;       // 1: use the tensor-core kernel where it applies
+  unsigned* sched;      // kPhiSchedWords zeroed words: per-pass tile counters, CTA-done counter
 };
+constexpr int kPhiSchedPasses = 16;                 // mode passes of 16 (r <= 256)
+constexpr int kPhiSchedWords = kPhiSchedPasses + 1;
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
 // tcgen05 kernel for uint8 windows; cudaErrorNotSupported outside its shapes
