@@ -229,6 +229,40 @@ SDMD_API int sdmd_sync(sdmd_t h, void *stream);
 SDMD_API int sdmd_svd(sdmd_t h, int32_t r, double *sigma, double *V, void *stream);
 
 /*
+ * sdmd_amplitudes -- DMD mode amplitudes b of the last sdmd_modes call, from
+ * the POD coefficients of x_1 (Sec. 3.3, Eq. 14a-e: b = (W Lambda)^-1 alpha_1,
+ * alpha_1 = Sigma V^H e_1, x_1 the oldest snapshot of X), in the order of that
+ * call's lambda. b receives r complex128 (interleaved re, im; zero beyond the
+ * kept rank), host or device memory; bg_index (host, may be NULL) receives the
+ * background mode argmin_k |log lambda_k| (Algorithm 3, principal log), -1 if
+ * no mode was kept; with bg_index the call waits for the stream.
+ * SDMD_ERR_NOT_READY if no sdmd_modes call has run since the last push;
+ * SDMD_ERR_UNSUPPORTED on pipelined (depth > 1) handles, whose frames keep
+ * their results per frame.
+ */
+SDMD_API int sdmd_amplitudes(sdmd_t h, void *b, int32_t *bg_index, void *stream);
+
+/* What sdmd_reconstruct returns. */
+enum {
+    SDMD_RECON_MODES = 0,       /* sum_k b_k phi_k lambda_k^t over the kept modes */
+    SDMD_RECON_BACKGROUND = 1,  /* b_i phi_i lambda_i^t, i = background mode (Algorithm 3) */
+    SDMD_RECON_FOREGROUND = 2   /* x_t minus its background (Eq. 11's sparse part) */
+};
+
+/*
+ * sdmd_reconstruct -- the window's DMD reconstruction at time index t from
+ * the last sdmd_modes call (Sec. 2.2, Eq. 11; Algorithm 3): t = 0 is x_1, the
+ * oldest snapshot of X, and t = c-1 the newest resident snapshot; larger t
+ * extrapolates. Computed as X' Re(M c), c_k = b_k lambda_k^t, without forming
+ * Phi (the snapshots are real). out receives n float32 values (real part),
+ * device memory, 16-byte aligned. SDMD_RECON_FOREGROUND needs 0 <= t <= c-1.
+ * Real dense handles (SDMD_F32, SDMD_U8) with depth 1 only
+ * (SDMD_ERR_UNSUPPORTED otherwise); SDMD_ERR_NOT_READY if no sdmd_modes call
+ * has run since the last push; SDMD_ERR_ARG for a bad t, `what` or pointer.
+ */
+SDMD_API int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float *out, void *stream);
+
+/*
  * sdmd_status -- waits for `stream`, then reports the device-side status
  * word of the handle (SDMD_OK, or SDMD_ERR_RANK / SDMD_ERR_TIMEOUT /
  * SDMD_ERR_ARG (sparse index out of range) raised by a kernel since the last
@@ -239,9 +273,10 @@ SDMD_API int sdmd_status(sdmd_t h, void *stream);
 /* Options (sdmd_set_option). */
 enum {
     SDMD_OPT_PHI_TENSOR = 1 /* 1 (default): Phi of uint8 handles on the tensor
-                               cores (tcgen05, bf16 operands: pixels exact,
-                               M = V Sigma^-1 W as three bf16 terms, FP32
-                               accumulation); 0: CUDA-core FP32 kernel */
+                               cores (tcgen05, fp16 operands: pixels exact,
+                               M = V Sigma^-1 W as three power-of-two-scaled
+                               fp16 terms, FP32 accumulation); 0: CUDA-core
+                               FP32 kernel */
 };
 
 /* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */

@@ -178,3 +178,15 @@ def background_column(res, b, t):
     """l_t = b_idx phi_idx lambda_idx^t for window column t (Eq. 11, Alg. 3)."""
     idx = background_index(res.lam)
     return b[idx] * res.Phi[:, idx] * (res.lam[idx] ** t)
+
+
+def reconstruct(res, b, t):
+    """x_hat(t) = sum_k b_k phi_k lambda_k^t over the kept modes (Sec. 2.2,
+    Eq. 11 without the background/foreground split); t = 0 is x_1."""
+    return res.Phi @ (b * res.lam ** t)
+
+
+def foreground_column(W, res, b, t):
+    """x_t minus its background (Eq. 11's sparse part, Algorithm 3), where
+    W[:, t] is the window column at time index t (t = 0 is x_1)."""
+    return np.asarray(W)[:, t].astype(np.float64) - background_column(res, b, t).real

@@ -56,6 +56,7 @@ struct sdmd_s {
   int32_t head = 0;
   int32_t last_r = 0;         // r of the last sdmd_modes call (0 = none)
   int32_t last_p = 0;
+  int64_t modes_count = -1;   // push count when sdmd_modes last ran (reconstruction window)
   int64_t gsz = 8;            // bytes per G entry (16 for complex handles)
   int32_t phi_tensor = 1;     // SDMD_OPT_PHI_TENSOR
   // sparse handles
@@ -600,6 +601,7 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
   }
   h->last_r = r;
   h->last_p = c - 1;
+  h->modes_count = h->count;
   if (lambda) {
     const int rc = copy_out(lambda, h->ws + L.lamout, (size_t)r * 16, st);
     if (rc != SDMD_OK) return rc;
@@ -771,6 +773,69 @@ int sdmd_trace_times(sdmd_t h, int32_t kernel, double* ms, int32_t cap, int32_t*
   }
   *count = k;
   h->tr_used[kernel] = 0;
+  return SDMD_OK;
+}
+
+int sdmd_amplitudes(sdmd_t h, void* b, int32_t* bg_index, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_amplitudes: NULL handle");
+  if (!h->ctx.empty()) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_amplitudes: pipelined handle");
+  if (h->modes_count != h->count || h->last_r < 1)
+    return fail(SDMD_ERR_NOT_READY, "sdmd_amplitudes: no sdmd_modes call since the last push");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ModesLayout L = modes_layout(h->m);
+  if (b) {
+    const int rc = copy_out(b, h->ws + L.bamp, (size_t)h->last_r * 16, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  if (bg_index) {
+    double v = -1.0;
+    const int64_t pl = h->m - 1 > 1 ? h->m - 1 : 1;
+    CK(cudaMemcpyAsync(&v, h->ws + L.bamp + 2 * pl, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *bg_index = (int32_t)v;
+  }
+  return SDMD_OK;
+}
+
+int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float* out, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_reconstruct: NULL handle");
+  if (h->dtype != SDMD_U8 && h->dtype != SDMD_F32)
+    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_reconstruct: real dense handles only");
+  if (!h->ctx.empty()) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_reconstruct: pipelined handle");
+  if (h->modes_count != h->count || h->last_r < 1)
+    return fail(SDMD_ERR_NOT_READY, "sdmd_reconstruct: no sdmd_modes call since the last push");
+  if (what != SDMD_RECON_MODES && what != SDMD_RECON_BACKGROUND && what != SDMD_RECON_FOREGROUND)
+    return fail(SDMD_ERR_ARG, "sdmd_reconstruct: what=%d", what);
+  const int c = h->last_p + 1;
+  if (t < 0 || (what == SDMD_RECON_FOREGROUND && t > c - 1))
+    return fail(SDMD_ERR_ARG, "sdmd_reconstruct: t=%lld out of range", (long long)t);
+  if (!out || ptr_kind(out) != kDevice || (reinterpret_cast<uintptr_t>(out) & 15u) != 0)
+    return fail(SDMD_ERR_ARG, "sdmd_reconstruct: out must be 16-byte aligned device memory (n floats)");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ModesLayout L = modes_layout(h->m);
+  const int64_t pl = h->m - 1 > 1 ? h->m - 1 : 1;
+  ReconArgs ra;
+  ra.ring = h->ring;
+  ra.slot_bytes = h->slot_bytes;
+  ra.n = h->n;
+  ra.dtype = h->dtype;
+  ra.m = h->cap;
+  ra.start = oldest_slot(h);
+  ra.p = h->last_p;
+  ra.R = h->last_r;
+  ra.Mf = reinterpret_cast<const float*>(h->ws + L.Mf);
+  ra.lamout = h->ws + L.lamout;
+  ra.bamp = h->ws + L.bamp;
+  ra.bgi = h->ws + L.bamp + 2 * pl;
+  ra.r_dev = h->r_dev;
+  ra.t = t;
+  ra.what = what;
+  ra.urec = reinterpret_cast<float*>(h->ws + L.urec);
+  ra.out = out;
+  ra.xt_slot = (what == SDMD_RECON_FOREGROUND) ? (int32_t)((ra.start + t) % h->cap) : -1;
+  CK(launch_reconstruct(ra, st));
   return SDMD_OK;
 }
 

@@ -111,7 +111,7 @@ __device__ __forceinline__ int tri_row(int f) {
 
 struct WS {
   dd *GXYd, *Ad, *Z, *Y, *lu;
-  double *V, *sig, *lamout;
+  double *V, *sig, *lamout, *bamp;
   float* Mf;
   long long* clk;
 };
@@ -126,6 +126,7 @@ __device__ WS carve(double* base, const ModesLayout& L) {
   w.V = base + L.V;
   w.sig = base + L.sig;
   w.lamout = base + L.lamout;
+  w.bamp = base + L.bamp;
   w.Mf = reinterpret_cast<float*>(base + L.Mf);
   w.clk = reinterpret_cast<long long*>(base + L.clk);
   return w;
@@ -979,6 +980,53 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
     w.Mf[2 * idx] = (sr.hi + sr.lo) * unscale;
     w.Mf[2 * idx + 1] = (si.hi + si.lo) * unscale;
   }
+
+  // ---- 9. amplitudes b = (W Lambda)^-1 alpha_1 (Sec. 3.3, Eq. 14a-e) with
+  //         alpha_1 = Sigma V^H e_1 (the POD coefficients of x_1). The left
+  //         eigenvectors give W^-1 = diag(1 / u_k^H w_k) U^H, so
+  //         b_k = u_k^H alpha_1 / (lambda_k u_k^H w_k): O(r^2), no solve.
+  //         Then the background index argmin_k |log lambda_k| (Algorithm 3,
+  //         principal log).
+  for (int k = tid; k < R; k += kThreads) {
+    double br = 0.0, bi = 0.0;
+    if (k < re) {
+      const int kk = ord[k];
+      double nr = 0.0, ni = 0.0, dr = 0.0, di = 0.0;
+      for (int i = 0; i < re; ++i) {
+        const CF u = Uc[i * re + kk], wv = Wc[i * re + kk];
+        const double a1 = w.sig[i] * w.V[(int64_t)i * p];   // G_X real: V real
+        nr += (double)u.re * a1;                            // conj(u_i) alpha_1[i]
+        ni -= (double)u.im * a1;
+        dr += (double)u.re * wv.re + (double)u.im * wv.im;  // conj(u_i) w_i
+        di += (double)u.re * wv.im - (double)u.im * wv.re;
+      }
+      const double lr = w.lamout[2 * k], li = w.lamout[2 * k + 1];
+      const double er = lr * dr - li * di, ei = lr * di + li * dr;
+      const double q = er * er + ei * ei;
+      if (q > 0.0) {
+        br = (nr * er + ni * ei) / q;
+        bi = (ni * er - nr * ei) / q;
+      } else {
+        atomicOr(a.status, kDevRank);
+      }
+    }
+    w.bamp[2 * k] = br;
+    w.bamp[2 * k + 1] = bi;
+  }
+  if (tid == 0) {
+    int best = -1;
+    double bv = 0.0;
+    for (int k = 0; k < re; ++k) {
+      const double lr = w.lamout[2 * k], li = w.lamout[2 * k + 1];
+      const double lm = 0.5 * log(lr * lr + li * li), th = atan2(li, lr);
+      const double v = lm * lm + th * th;
+      if (best < 0 || v < bv) {
+        best = k;
+        bv = v;
+      }
+    }
+    w.bamp[2 * (a.ws_m - 1 > 1 ? a.ws_m - 1 : 1)] = (double)best;   // fixed slot for any window length
+  }
   __syncthreads();
   if (tid == 0) {
     *a.r_dev = re;
@@ -1018,6 +1066,8 @@ ModesLayout modes_layout(int m) {
   L.tmp = 0;
   L.lu = take(6 * p2 + 64); // tridiagonal LU per vector (5 r p) + Ritz scratch (r p); A~ and eig fallback (6 r^2)
   L.clk = take(16);
+  L.bamp = take(2 * p + 2);  // b (re, im) per mode, then [2p] = background index
+  L.urec = take(p);          // 2p floats
   L.total = o;
   return L;
 }

@@ -64,6 +64,8 @@ int64_t modes_ws_doubles(int m);
 // Offsets (in doubles) of the named arrays inside the modes workspace.
 struct ModesLayout {
   int64_t A, GXY, HV, d, e, lam, Z, V, Y, At, Hc, Qc, Wc, M, Mf, sig, lamout, tmp, lu, clk;
+  int64_t bamp;   // r complex128 mode amplitudes b (Sec. 3.3), then the background index (as double)
+  int64_t urec;   // p x 2 floats: reconstruction weights (hi, lo) of X' columns
   int64_t total;
 };
 ModesLayout modes_layout(int m);
@@ -90,6 +92,28 @@ constexpr int kPhiSchedPasses = 16;                 // mode passes of 16 (r <= 2
 constexpr int kPhiSchedWords = kPhiSchedPasses + 1;
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
+
+struct ReconArgs {
+  const uint8_t* ring;
+  int64_t slot_bytes;
+  int64_t n;
+  int32_t dtype;        // SDMD_U8 or SDMD_F32
+  int32_t m;            // ring modulus
+  int32_t start;        // physical slot of the oldest snapshot of the modes window
+  int32_t p;            // columns of X'
+  int32_t R;            // modes requested in the modes call (stride of Mf)
+  const float* Mf;      // p x 2R (re, im) of M = V Sigma^-1 W
+  const double* lamout; // R complex eigenvalues
+  const double* bamp;   // R complex amplitudes
+  const double* bgi;    // background mode index (stored as double)
+  const int* r_dev;     // kept rank
+  int64_t t;            // time index, 0 = x_1
+  int32_t what;         // SDMD_RECON_*
+  float* urec;          // workspace: p x 2 floats
+  float* out;           // n floats, 16-byte aligned
+  int32_t xt_slot;      // physical slot of x_t (foreground), -1 otherwise
+};
+cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t st);
 // tcgen05 kernel for uint8 windows; cudaErrorNotSupported outside its shapes
 cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st);
 

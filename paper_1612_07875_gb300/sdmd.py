@@ -29,6 +29,10 @@ SDMD_MAX_DEPTH = 16
 
 SDMD_OPT_PHI_TENSOR = 1
 
+SDMD_RECON_MODES = 0
+SDMD_RECON_BACKGROUND = 1
+SDMD_RECON_FOREGROUND = 2
+
 SDMD_K_INGEST = 0
 SDMD_K_GRAM_ROW = 1
 SDMD_K_MODES = 2
@@ -67,6 +71,8 @@ _SIGNATURES = {
     "sdmd_trace_read": [_VP, _I32, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
     "sdmd_gram_row_static": [_I32, _VP, _I64, _I32, _VP, _I64, _VP, _VP],
     "sdmd_modes_phase_cycles": [_VP, ctypes.POINTER(_I64), _I32, _VP],
+    "sdmd_amplitudes": [_VP, _VP, ctypes.POINTER(_I32), _VP],
+    "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
 }
 
 
@@ -187,6 +193,19 @@ def sdmd_modes(h, r, phi, lam, r_out=None, stream=None):
 
 def sdmd_svd(h, r, sigma, V, stream=None):
     _check(lib().sdmd_svd(h, int(r), ptr(sigma), ptr(V), stream_handle(stream)), "sdmd_svd")
+
+
+def sdmd_amplitudes(h, b, stream=None, want_index=True):
+    """Copy the mode amplitudes into `b` (r complex128 as 2r float64, host or
+    device; may be None); returns the background mode index (or None)."""
+    idx = _I32(-1)
+    _check(lib().sdmd_amplitudes(h, ptr(b), ctypes.byref(idx) if want_index else None, stream_handle(stream)),
+           "sdmd_amplitudes")
+    return idx.value if want_index else None
+
+
+def sdmd_reconstruct(h, t, what, out, stream=None):
+    _check(lib().sdmd_reconstruct(h, int(t), int(what), ptr(out), stream_handle(stream)), "sdmd_reconstruct")
 
 
 def sdmd_status(h, stream=None):

@@ -340,6 +340,47 @@ def test_pod_amplitudes_equal_least_squares_and_reconstruct():
     assert np.allclose(l5, b_pod[idx] * res.Phi[:, idx] * 0.97 ** 5)
 
 
+def _planted_rotation_window(steps, static=None, seed=50):
+    # x_k = B + Q R^k z: a rotation by theta (|lambda| = 1) and a decay 0.97
+    theta = 0.4
+    rng = np.random.default_rng(seed)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 4)))
+    z = np.array([1.0, -0.5, 2.0])
+    Rm = np.array([[math.cos(theta), -math.sin(theta), 0],
+                   [math.sin(theta), math.cos(theta), 0], [0, 0, 0.97]])
+    B = np.zeros(40) if static is None else static * Q[:, 3]
+    cols = []
+    for _ in range(steps):
+        cols.append(B + Q[:, :3] @ z)
+        z = Rm @ z
+    return np.stack(cols, axis=1), B
+
+
+def test_reconstruct_reproduces_window_and_extrapolates_planted_dynamics():
+    # Eq. 11 with every mode: x_hat(t) = x_{t+1} inside the window (t = 0 is
+    # x_1), and beyond it the planted dynamics continue (exactly linear data).
+    W_all, _ = _planted_rotation_window(12)
+    W = W_all[:, :9]
+    res = oracle.exact_dmd(W, r=3)
+    b = oracle.pod_amplitudes(res)
+    for t in range(12):
+        assert np.allclose(oracle.reconstruct(res, b, t).real, W_all[:, t], atol=1e-9)
+        assert np.abs(oracle.reconstruct(res, b, t).imag).max() < 1e-9
+
+
+def test_background_and_foreground_of_planted_static_scene():
+    # A static part B is the lambda = 1 mode: Algorithm 3's background column
+    # is B at every t and the foreground is the dynamic part x_t - B.
+    W, B = _planted_rotation_window(10, static=3.0, seed=51)
+    res = oracle.exact_dmd(W, r=4)
+    b = oracle.pod_amplitudes(res)
+    idx = oracle.background_index(res.lam)
+    assert abs(res.lam[idx] - 1.0) < 1e-10
+    for t in (0, 4, 9):
+        assert np.allclose(oracle.background_column(res, b, t).real, B, atol=1e-9)
+        assert np.allclose(oracle.foreground_column(W, res, b, t), W[:, t] - B, atol=1e-9)
+
+
 def test_background_index_principal_log():
     lam = np.array([0.5, 1.0001 * cmath.exp(0.001j), 0.9 * cmath.exp(2j), -1.0])
     # |log(-1)| = pi: a unit-modulus but fast mode is not background
