@@ -285,7 +285,7 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
   if (e == cudaSuccess) e = cudaMalloc(&h->G, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * h->gsz);
-  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 2 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
@@ -293,7 +293,7 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
   if (e == cudaSuccess) e = cudaMemset(h->phi_sched, 0, kPhiSchedWords * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->ring, 0, ring_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->G, 0, gbytes);
-  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, 2 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->ws, 0, ws_bytes);
   if (depth > 1) {
     h->ctx.resize(depth);
@@ -351,13 +351,13 @@ int sdmd_create_sparse(int64_t n, int32_t m, int32_t nnz_max, sdmd_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * 16);
   if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * 16);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->nblk * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 2 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->tag, 0xff, (size_t)n * sizeof(int));   // tag -1: no stamp
   if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * 16);
-  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, 2 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {

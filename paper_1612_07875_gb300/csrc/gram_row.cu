@@ -4,7 +4,9 @@
 // each window byte exactly once, so the kernel is HBM-bound.
 //
 // Decomposition: the n dimension (bytes, padded to whole 4 KiB units) is cut
-// into `nblk` contiguous chunks, one CTA per SM. A CTA walks its chunk in
+// into `nblk` contiguous chunks, about two per SM. One persistent CTA per SM
+// takes chunks from a counter (atomicAdd), so a launch is not held back by
+// SMs that another stream's kernel occupies, and walks each chunk in
 // sub-chunks of up to 32 KiB: thread 0 brings the sub-chunk of x_new into
 // shared memory with one bulk copy (TMA, cp.async.bulk), then each of the 8
 // warps streams its slots (warp w takes slots w, w+8, ...) in 4 KiB pieces
@@ -13,9 +15,10 @@
 // barrier, consume the piece (16 bytes per lane per step) and hand the stage
 // back. That keeps 128 KiB of loads in flight per SM without register
 // pressure. Each slot's sub-chunk sum is reduced with warp shuffles into a
-// per-CTA accumulator; the per-CTA partials go to a [slot][CTA] array and the
-// last CTA to finish (atomic ticket, no waiting) sums them in a fixed order
-// and writes row and column `s_new` of G.
+// per-chunk accumulator; the per-chunk partials go to a [slot][chunk] array
+// and the last CTA to finish (atomic ticket, no waiting) sums them in a
+// fixed order and writes row and column `s_new` of G, so the result does not
+// depend on which CTA took which chunk.
 //
 //  - uint8: __dp4a (4 u8 x u8 products into u32). A lane sums at most
 //    32 KiB / 32 = 1024 products (< 2^32 / 255^2) before the value goes to
@@ -99,6 +102,7 @@ struct Smem {
   uint8_t xs[kXSub];                          // x_new sub-chunk
   unsigned long long bar[kGrWarps][kStages];  // one mbarrier per stage
   unsigned long long xbar;                    // x_new barrier
+  int chunk;                                  // chunk taken by the CTA
   long long acc_i[SDMD_MAX_M];
   double acc_d[SDMD_MAX_M];
   double acc_im[SDMD_MAX_M];                  // imaginary parts (complex snapshots)
@@ -114,7 +118,7 @@ __device__ void finish_row(const GramRowArgs& a, Smem& sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int t = atomicAdd(a.ticket, 1u);
-    sm.last = (t == (unsigned int)a.nblk - 1u);
+    sm.last = (t == gridDim.x - 1u);
   }
   __syncthreads();
   if (!sm.last) return;
@@ -132,7 +136,10 @@ __device__ void finish_row(const GramRowArgs& a, Smem& sm) {
       G[(int64_t)j * a.m + a.s_new] = s;
     }
   }
-  if (threadIdx.x == 0) *a.ticket = 0u;  // ready for the next launch
+  if (threadIdx.x == 0) {                // ready for the next launch
+    a.ticket[0] = 0u;
+    a.ticket[1] = 0u;
+  }
 }
 
 // Complex version: G[j][s_new] = <x_j, x_new> = g_j and G[s_new][j] = conj(g_j).
@@ -141,7 +148,7 @@ __device__ void finish_row_c64(const GramRowArgs& a, Smem& sm) {
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned int t = atomicAdd(a.ticket, 1u);
-    sm.last = (t == (unsigned int)a.nblk - 1u);
+    sm.last = (t == gridDim.x - 1u);
   }
   __syncthreads();
   if (!sm.last) return;
@@ -165,7 +172,10 @@ __device__ void finish_row_c64(const GramRowArgs& a, Smem& sm) {
       G[(int64_t)a.s_new * a.m + j] = make_double2(sr, -si);
     }
   }
-  if (threadIdx.x == 0) *a.ticket = 0u;
+  if (threadIdx.x == 0) {
+    a.ticket[0] = 0u;
+    a.ticket[1] = 0u;
+  }
 }
 
 template <int kMode>
@@ -174,8 +184,6 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
   extern __shared__ __align__(128) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t beg = (int64_t)blockIdx.x * a.chunk;
-  const int64_t end = min(beg + a.chunk, a.slot_bytes);
   for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
     sm.acc_i[j] = 0;
     sm.acc_d[j] = 0.0;
@@ -192,7 +200,15 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
   const int nmine = (a.c > warp) ? (a.c - warp + kGrWarps - 1) / kGrWarps : 0;  // slots of this warp
   unsigned g = 0;                  // pieces this warp has consumed so far (all sub-chunks)
   bool failed = false;             // a bounded wait expired: stop issuing, drain, finish
-  int sub_i = 0;
+  int sub_i = 0;                   // sub-chunks processed (x_new barrier phase)
+  for (;;) {
+  __syncthreads();                 // the previous chunk's partials are out
+  if (threadIdx.x == 0) sm.chunk = failed ? a.nblk : (int)atomicAdd(a.ticket + 1, 1u);
+  __syncthreads();
+  const int ch = sm.chunk;
+  if (ch >= a.nblk) break;
+  const int64_t beg = (int64_t)ch * a.chunk;
+  const int64_t end = min(beg + a.chunk, a.slot_bytes);
   for (int64_t sub = beg; sub < end; sub += kXSub, ++sub_i) {
     const int len = (int)min((int64_t)kXSub, end - sub);          // multiple of kPiece
     const int npieces = len / kPiece;
@@ -309,28 +325,41 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
     }
     g += nitems;
   }
-  __syncthreads();
+  failed = __syncthreads_or(failed);
+  // this chunk's partials (each thread writes and clears its own slots)
+  for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
+    if constexpr (kU8) {
+      static_cast<long long*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_i[j];
+    } else if constexpr (kMode == kModeF32) {
+      static_cast<double*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_d[j];
+    } else {
+      static_cast<double2*>(a.partials)[(int64_t)j * a.nblk + ch] = make_double2(sm.acc_d[j], sm.acc_im[j]);
+    }
+    sm.acc_i[j] = 0;
+    sm.acc_d[j] = 0.0;
+    sm.acc_im[j] = 0.0;
+  }
+  }
   if constexpr (kU8) {
-    long long* P = static_cast<long long*>(a.partials);
-    for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = sm.acc_i[j];
     finish_row<long long>(a, sm);
   } else if constexpr (kMode == kModeF32) {
-    double* P = static_cast<double*>(a.partials);
-    for (int j = threadIdx.x; j < a.c; j += blockDim.x) P[(int64_t)j * a.nblk + blockIdx.x] = sm.acc_d[j];
     finish_row<double>(a, sm);
   } else {
-    double2* P = static_cast<double2*>(a.partials);
-    for (int j = threadIdx.x; j < a.c; j += blockDim.x)
-      P[(int64_t)j * a.nblk + blockIdx.x] = make_double2(sm.acc_d[j], sm.acc_im[j]);
     finish_row_c64(a, sm);
   }
 }
 
 }  // namespace
 
+// Two chunks per SM: persistent CTAs take chunks as they free
+// up, so a launch is not held back by SMs that another stream's kernel (a
+// frame's eigensolver) occupies; the partials stay indexed by chunk, so the
+// fixed-order reduction and the result do not change.
+constexpr int kChunksPerSm = 2;
+
 void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t* nblk) {
   const int64_t units = (slot_bytes + kPiece - 1) / kPiece;
-  int64_t want = (num_sms > 0 ? num_sms : 1);
+  int64_t want = (int64_t)kChunksPerSm * (num_sms > 0 ? num_sms : 1);
   if (want > units) want = units;
   const int64_t per = (units + want - 1) / want;     // units per CTA
   *chunk = per * kPiece;
@@ -349,12 +378,16 @@ cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = a.nblk < sms ? a.nblk : (sms > 0 ? sms : 1);   // persistent
   if (dtype == SDMD_U8)
-    gram_row_bulk_kernel<kModeU8><<<a.nblk, kGrThreads, smem, st>>>(a);
+    gram_row_bulk_kernel<kModeU8><<<ctas, kGrThreads, smem, st>>>(a);
   else if (dtype == SDMD_C64)
-    gram_row_bulk_kernel<kModeC64><<<a.nblk, kGrThreads, smem, st>>>(a);
+    gram_row_bulk_kernel<kModeC64><<<ctas, kGrThreads, smem, st>>>(a);
   else
-    gram_row_bulk_kernel<kModeF32><<<a.nblk, kGrThreads, smem, st>>>(a);
+    gram_row_bulk_kernel<kModeF32><<<ctas, kGrThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -25,15 +25,15 @@ constexpr int kDevRange = 4;     // a sparse coefficient index was outside [0, n
 struct GramRowArgs {
   const uint8_t* ring;   // slot j starts at ring + j * slot_bytes
   int64_t slot_bytes;    // multiple of kSlotAlign
-  int64_t chunk;         // bytes per CTA, multiple of 4096
-  int32_t nblk;          // CTAs; nblk * chunk >= slot_bytes
+  int64_t chunk;         // bytes per chunk, multiple of 4096
+  int32_t nblk;          // chunks; nblk * chunk >= slot_bytes
   int32_t c;             // resident snapshots (after this push)
   int32_t s_first;       // physical slot of the oldest resident snapshot;
                          // the window is slots s_first, s_first+1, ... (mod m)
   int32_t s_new;         // slot holding the new snapshot
   int32_t m;             // G is m x m
-  void* partials;        // [nblk][m] per-CTA partial sums (FP64 or int64)
-  unsigned int* ticket;  // CTA completion counter, zero between launches
+  void* partials;        // [m][nblk] per-chunk partial sums (FP64 or int64)
+  unsigned int* ticket;  // two words, zero between launches: CTAs finished, chunks taken
   void* G;               // m x m, double (f32) or int64 (u8), physical slots
   int* status;           // device status word (kDevTimeout on an expired wait)
 };
