@@ -241,6 +241,21 @@ def measure_isolated(S, h, frames, t0, stream, phi, n, steps=8):
     out["gram_row"]["GB/s"] = M_WIN * n / (out["gram_row"]["us"] * 1e-6) / 1e9
     out["phi"]["GB/s"] = ((M_WIN - 1) * n + n * R_MODES * 8) / (out["phi"]["us"] * 1e-6) / 1e9
     out["serial_step_us"] = sum(out[k]["us"] for k in ("gram_row", "phi", "modes_small_f64", "ingest_copy"))
+    # streaming background subtraction of the newest frame (Algorithm 3):
+    # background column and foreground x_t - background, one pass over X'
+    fg = torch.empty(n, dtype=torch.float32, device=frames.device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for what, name, extra in ((S.SDMD_RECON_BACKGROUND, "background", 0), (S.SDMD_RECON_FOREGROUND, "foreground", n)):
+        with torch.cuda.stream(stream):
+            S.sdmd_reconstruct(h, M_WIN - 1, what, fg, sh)      # warm-up
+            ev0.record(stream)
+            for _ in range(steps):
+                S.sdmd_reconstruct(h, M_WIN - 1, what, fg, sh)
+            ev1.record(stream)
+        stream.synchronize()
+        us = 1e3 * ev0.elapsed_time(ev1) / steps
+        out[name] = {"launches": 2 * steps, "us": us,
+                     "GB/s": ((M_WIN - 1) * n + 4 * n + extra) / (us * 1e-6) / 1e9}
     return out
 
 

@@ -236,9 +236,8 @@ SDMD_API int sdmd_svd(sdmd_t h, int32_t r, double *sigma, double *V, void *strea
  * kept rank), host or device memory; bg_index (host, may be NULL) receives the
  * background mode argmin_k |log lambda_k| (Algorithm 3, principal log), -1 if
  * no mode was kept; with bg_index the call waits for the stream.
- * SDMD_ERR_NOT_READY if no sdmd_modes call has run since the last push;
- * SDMD_ERR_UNSUPPORTED on pipelined (depth > 1) handles, whose frames keep
- * their results per frame.
+ * SDMD_ERR_NOT_READY if no sdmd_modes call has run since the last push (the
+ * frames of sdmd_step keep their results per frame and do not count).
  */
 SDMD_API int sdmd_amplitudes(sdmd_t h, void *b, int32_t *bg_index, void *stream);
 
@@ -256,9 +255,10 @@ enum {
  * extrapolates. Computed as X' Re(M c), c_k = b_k lambda_k^t, without forming
  * Phi (the snapshots are real). out receives n float32 values (real part),
  * device memory, 16-byte aligned. SDMD_RECON_FOREGROUND needs 0 <= t <= c-1.
- * Real dense handles (SDMD_F32, SDMD_U8) with depth 1 only
- * (SDMD_ERR_UNSUPPORTED otherwise); SDMD_ERR_NOT_READY if no sdmd_modes call
- * has run since the last push; SDMD_ERR_ARG for a bad t, `what` or pointer.
+ * Real dense handles (SDMD_F32, SDMD_U8; SDMD_ERR_UNSUPPORTED otherwise);
+ * SDMD_ERR_NOT_READY if no sdmd_modes call has run since the last push
+ * (sdmd_step frames do not count); SDMD_ERR_ARG for a bad t, `what` or
+ * pointer.
  */
 SDMD_API int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float *out, void *stream);
 

@@ -778,7 +778,6 @@ int sdmd_trace_times(sdmd_t h, int32_t kernel, double* ms, int32_t cap, int32_t*
 
 int sdmd_amplitudes(sdmd_t h, void* b, int32_t* bg_index, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_amplitudes: NULL handle");
-  if (!h->ctx.empty()) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_amplitudes: pipelined handle");
   if (h->modes_count != h->count || h->last_r < 1)
     return fail(SDMD_ERR_NOT_READY, "sdmd_amplitudes: no sdmd_modes call since the last push");
   DeviceScope ds(h->device);
@@ -802,7 +801,6 @@ int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float* out, void* stream
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_reconstruct: NULL handle");
   if (h->dtype != SDMD_U8 && h->dtype != SDMD_F32)
     return fail(SDMD_ERR_UNSUPPORTED, "sdmd_reconstruct: real dense handles only");
-  if (!h->ctx.empty()) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_reconstruct: pipelined handle");
   if (h->modes_count != h->count || h->last_r < 1)
     return fail(SDMD_ERR_NOT_READY, "sdmd_reconstruct: no sdmd_modes call since the last push");
   if (what != SDMD_RECON_MODES && what != SDMD_RECON_BACKGROUND && what != SDMD_RECON_FOREGROUND)

@@ -10,8 +10,9 @@
 //    two floats hi + lo so that the pass below carries ~48 bits of u;
 //  - pass kernel: each thread owns 16 consecutive uint8 positions (or 4
 //    float32), loops over the p slots of X' (a CTA reads 4 KiB contiguous per
-//    slot per step), accumulates x * hi and x * lo in FP32 and writes
-//    x_hat, or x_t - x_hat (foreground: the snapshot minus its background).
+//    slot per step; 8 slots' loads in flight per thread), accumulates
+//    x * hi + x * lo in FP32 and writes x_hat, or x_t - x_hat (foreground:
+//    the snapshot minus its background).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -90,7 +91,7 @@ struct ReconVec<float> {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) recon_pass_kernel(ReconArgs a) {
+__global__ void __launch_bounds__(kThreads, 3) recon_pass_kernel(ReconArgs a) {
   using V = typename ReconVec<T>::V;
   constexpr int kN = ReconVec<T>::kN;
   __shared__ float uh[SDMD_MAX_M], ul[SDMD_MAX_M];
@@ -104,24 +105,18 @@ __global__ void __launch_bounds__(kThreads) recon_pass_kernel(ReconArgs a) {
   const int64_t nvec = (a.n + kN - 1) / kN;
   for (int64_t v = (int64_t)blockIdx.x * kThreads + threadIdx.x; v < nvec; v += (int64_t)gridDim.x * kThreads) {
     const int64_t byte = v * kN * (int64_t)sizeof(T);   // in bounds: slots are padded to 4 KiB
-    float acc[kN], acc2[kN];
+    float y[kN];
 #pragma unroll
-    for (int i = 0; i < kN; ++i) acc[i] = acc2[i] = 0.f;
-#pragma unroll 4
+    for (int i = 0; i < kN; ++i) y[i] = 0.f;
+#pragma unroll 8
     for (int q = 0; q < a.p; ++q) {
       const V w = __ldcs(reinterpret_cast<const V*>(a.ring + off[q] + byte));
       float x[kN];
       to_floats(w, x);
       const float h = uh[q], l = ul[q];
 #pragma unroll
-      for (int i = 0; i < kN; ++i) {
-        acc[i] = fmaf(x[i], h, acc[i]);
-        acc2[i] = fmaf(x[i], l, acc2[i]);
-      }
+      for (int i = 0; i < kN; ++i) y[i] = fmaf(x[i], l, fmaf(x[i], h, y[i]));
     }
-    float y[kN];
-#pragma unroll
-    for (int i = 0; i < kN; ++i) y[i] = acc[i] + acc2[i];
     if (a.xt_slot >= 0) {        // foreground: x_t - background
       const V w = *reinterpret_cast<const V*>(a.ring + (int64_t)a.xt_slot * a.slot_bytes + byte);
       float x[kN];
@@ -155,7 +150,7 @@ cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t st) {
   const int vec = (a.dtype == SDMD_U8) ? 16 : 4;
   const int64_t nvec = (a.n + vec - 1) / vec;
   int64_t blocks = (nvec + kThreads - 1) / kThreads;
-  if (blocks > (int64_t)sms * 8) blocks = (int64_t)sms * 8;
+  if (blocks > (int64_t)sms * 12) blocks = (int64_t)sms * 12;
   if (blocks < 1) blocks = 1;
   if (a.dtype == SDMD_U8)
     recon_pass_kernel<uint8_t><<<(unsigned)blocks, kThreads, 0, st>>>(a);

@@ -148,11 +148,32 @@ def test_reconstruct_error_paths(cuda_device):
         assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
-    for make in (lambda: S.sdmd_create(n, m, S.SDMD_C64), lambda: S.sdmd_create_ex(n, m, S.SDMD_F32, 3)):
-        h = make()
-        try:
-            with pytest.raises(S.SdmdError) as ei:
-                S.sdmd_reconstruct(h, 0, S.SDMD_RECON_MODES, out)
-            assert ei.value.code == S.SDMD_ERR_UNSUPPORTED
-        finally:
-            S.sdmd_destroy(h)
+    h = S.sdmd_create(n, m, S.SDMD_C64)
+    try:
+        with pytest.raises(S.SdmdError) as ei:
+            S.sdmd_reconstruct(h, 0, S.SDMD_RECON_MODES, out)
+        assert ei.value.code == S.SDMD_ERR_UNSUPPORTED
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_reconstruct_on_pipelined_handle_follows_serial_modes(cuda_device):
+    # sdmd_step frames keep their results per frame; a serial sdmd_modes call
+    # on the same handle is what sdmd_reconstruct reads
+    ps = synth.PlantedStream(side=16, noise_var=1e-6, seed=synth.config_seed(1) + 7)
+    n, m, r = ps.n, 10, 3
+    h = S.sdmd_create_ex(n, m, S.SDMD_F32, 3)
+    so = oracle.StreamOracle(n, m, "f32")
+    out = torch.zeros(n, dtype=torch.float32, device=cuda_device)
+    try:
+        for t in range(m + 2):
+            x = ps.snapshot(t)
+            S.sdmd_step(h, torch.from_numpy(x).to(cuda_device), r, None, None, None)
+            so.push(x)
+        with pytest.raises(S.SdmdError) as ei:      # only steps so far
+            S.sdmd_reconstruct(h, 0, S.SDMD_RECON_MODES, out)
+        assert ei.value.code == S.SDMD_ERR_NOT_READY
+        S.sdmd_sync(h, None)
+        _check_window(h, so, r, cuda_device, ts=(0, m - 1))
+    finally:
+        S.sdmd_destroy(h)
