@@ -153,9 +153,11 @@ SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const v
  * sdmd_rebuild -- recompute the whole Gram of the resident window from the
  * ring buffer (Algorithm 1's first-step branch, G = X^T X; Sec. 2.1 Eq. 3),
  * e.g. to resynchronise G after the ring was modified outside the library.
- * Runs one Gram-row pass per resident snapshot, in time order, so every
- * entry is computed with the same reduction as when it was streamed: the
- * result equals the streamed G bit for bit. Cost: c passes over the window.
+ * uint8 windows of at most 127 snapshots (with SDMD_OPT_REBUILD_TENSOR, the
+ * default): one pass over the window on the tensor cores, exact int64, so
+ * equal to the streamed G. Otherwise one Gram-row pass per resident snapshot,
+ * in time order, so every entry is computed with the same reduction as when
+ * it was streamed: the result equals the streamed G bit for bit (c passes).
  */
 SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
 
@@ -277,6 +279,13 @@ enum {
                                M = V Sigma^-1 W as three power-of-two-scaled
                                fp16 terms, FP32 accumulation); 0: CUDA-core
                                FP32 kernel */
+    ,
+    SDMD_OPT_REBUILD_TENSOR = 2 /* 1 (default): sdmd_rebuild of uint8 windows of
+                                   at most 127 snapshots in one pass on the
+                                   tensor cores (centred fp16 pixels, exact
+                                   int64 G); 0: one Gram-row pass per
+                                   snapshot (bit-identical to streaming for
+                                   every dtype) */
 };
 
 /* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */

@@ -59,6 +59,9 @@ struct sdmd_s {
   int64_t modes_count = -1;   // push count when sdmd_modes last ran (reconstruction window)
   int64_t gsz = 8;            // bytes per G entry (16 for complex handles)
   int32_t phi_tensor = 1;     // SDMD_OPT_PHI_TENSOR
+  int32_t rebuild_tensor = 1; // SDMD_OPT_REBUILD_TENSOR
+  long long* gf_partials = nullptr;  // tensor-core rebuild: per-CTA sums (allocated on first use)
+  unsigned* gf_sched = nullptr;      // tensor-core rebuild: chunk counter
   // sparse handles
   int32_t nnz_max = 0;
   int* idx_ring = nullptr;    // m x nnz_max indices
@@ -226,6 +229,8 @@ void free_all(sdmd_s* h) {
   cudaFree(h->status);
   cudaFree(h->r_dev);
   cudaFree(h->phi_sched);
+  cudaFree(h->gf_partials);
+  cudaFree(h->gf_sched);
 }
 
 inline int32_t resident(const sdmd_s* h) { return (int32_t)(h->count < h->m ? h->count : h->m); }
@@ -479,6 +484,29 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int c = resident(h);
   const int first = oldest_slot(h);
+  if (h->dtype == SDMD_U8 && h->rebuild_tensor && c >= 1 && c <= 127) {
+    // one pass over the window on the tensor cores, exact int64
+    if (!h->gf_partials) {
+      cudaError_t e = cudaMalloc(&h->gf_partials, (size_t)kGramFullMaxCtas * 128 * 128 * sizeof(long long));
+      if (e == cudaSuccess) e = cudaMalloc(&h->gf_sched, sizeof(unsigned));
+      if (e == cudaSuccess) e = cudaMemset(h->gf_sched, 0, sizeof(unsigned));
+      if (e != cudaSuccess) return fail(SDMD_ERR_OOM, "sdmd_rebuild: %s", cudaGetErrorString(e));
+    }
+    GramFullArgs ga;
+    ga.ring = h->ring;
+    ga.slot_bytes = h->slot_bytes;
+    ga.n = h->n;
+    ga.m = h->cap;
+    ga.start = first;
+    ga.c = c;
+    ga.partials = h->gf_partials;
+    ga.sched = h->gf_sched;
+    ga.G = static_cast<long long*>(h->G);
+    ga.status = h->status;
+    TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+    CK(launch_gram_full_tc(ga, nullptr, st));
+    return SDMD_OK;
+  }
   // rows in time order: the final value of entry (i, j) comes from the row of
   // the later snapshot, exactly as when it was streamed
   for (int jj = 0; jj < c; ++jj) {
@@ -728,6 +756,9 @@ int sdmd_set_option(sdmd_t h, int32_t option, int64_t value) {
   switch (option) {
     case SDMD_OPT_PHI_TENSOR:
       h->phi_tensor = value ? 1 : 0;
+      return SDMD_OK;
+    case SDMD_OPT_REBUILD_TENSOR:
+      h->rebuild_tensor = value ? 1 : 0;
       return SDMD_OK;
     default:
       return fail(SDMD_ERR_ARG, "sdmd_set_option: unknown option %d", option);

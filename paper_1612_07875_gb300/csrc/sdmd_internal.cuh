@@ -38,6 +38,23 @@ struct GramRowArgs {
   int* status;           // device status word (kDevTimeout on an expired wait)
 };
 
+// Full-window Gram of uint8 snapshots on the tensor cores (c <= 127).
+struct GramFullArgs {
+  const uint8_t* ring;
+  int64_t slot_bytes;
+  int64_t n;
+  int32_t m;             // ring modulus (G is m x m, physical slots)
+  int32_t start;         // physical slot of the oldest resident snapshot
+  int32_t c;             // resident snapshots
+  long long* partials;   // [kGramFullMaxCtas][128][128] per-CTA sums
+  unsigned* sched;       // chunk counter, zero between launches
+  long long* G;
+  int* status;
+};
+constexpr int kGramFullMaxCtas = 160;
+// Launches the two kernels on `st`; cudaErrorNotSupported outside c <= 127.
+cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream_t st);
+
 // Gram row for one pushed snapshot; launches one kernel on `st`.
 cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st);
 

@@ -28,6 +28,7 @@ SDMD_MAX_M = 256
 SDMD_MAX_DEPTH = 16
 
 SDMD_OPT_PHI_TENSOR = 1
+SDMD_OPT_REBUILD_TENSOR = 2
 
 SDMD_RECON_MODES = 0
 SDMD_RECON_BACKGROUND = 1

@@ -152,6 +152,10 @@ def test_full_size_hd_video_sampled_entries(cuda_device):
         for i, j in pairs:
             assert G[i, j] == oracle.dot_u8(frames[ts[i]], frames[ts[j]]), (i, j)
         assert np.array_equal(G, G.T)
+        # the tensor-core rebuild of the same full-size window: equal to the streamed G
+        S.sdmd_rebuild(h)
+        assert np.array_equal(_read_gram(h, m, "u8", cuda_device), G)
+        assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
 
@@ -216,6 +220,47 @@ def test_full_window_rebuild_equals_streamed_gram_bitwise(cuda_device, kind):
         S.sdmd_gram(h, G2)
         torch.cuda.synchronize()
         assert torch.equal(G1, G2)
+        assert S.sdmd_status(h) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h)
+
+
+@pytest.mark.parametrize("n,m,pushes,pattern", [
+    (40009, 9, 23, "random"),         # window full, ragged n
+    (4096 * 3 + 17, 127, 130, "random"),   # the largest window on the tensor path
+    (100003, 100, 40, "extreme"),     # ramp-up (40 of 100), pixels 0 / 255 only
+    (1, 3, 5, "random"),              # a single position
+    (5000, 128, 128, "random"),       # beyond the tensor path: row kernels
+])
+def test_tensor_core_rebuild_exact(cuda_device, n, m, pushes, pattern):
+    # Algorithm 1's first step on the tensor cores (centred fp16 pixels,
+    # FP32 accumulators drained into int64): equal to the oracle's exact
+    # int64 Gram and to the streamed G, and to the row-kernel rebuild.
+    rng = np.random.default_rng(n + m)
+    h = S.sdmd_create(n, m, S.SDMD_U8)
+    so = oracle.StreamOracle(n, m, "u8")
+    try:
+        for _ in range(pushes):
+            if pattern == "extreme":
+                x = (rng.integers(0, 2, n, dtype=np.uint8) * 255).astype(np.uint8)
+            else:
+                x = rng.integers(0, 256, n, dtype=np.uint8)
+            S.sdmd_push(h, torch.from_numpy(x).to(cuda_device))
+            so.push(x)
+        c = min(pushes, m)
+        G0 = torch.empty(c, c, dtype=torch.int64, device=cuda_device)
+        S.sdmd_gram(h, G0)
+        out = {}
+        for opt in (1, 0):
+            S.sdmd_set_option(h, S.SDMD_OPT_REBUILD_TENSOR, opt)
+            S.sdmd_rebuild(h)
+            G = torch.empty(c, c, dtype=torch.int64, device=cuda_device)
+            S.sdmd_gram(h, G)
+            out[opt] = G
+        torch.cuda.synchronize()
+        ref = so.gram()
+        assert np.array_equal(out[1].cpu().numpy(), ref)
+        assert torch.equal(out[1], out[0]) and torch.equal(out[1], G0)
         assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
