@@ -43,7 +43,7 @@ namespace {
 
 constexpr int kStages = 4;
 constexpr int kPiece = 4096;                       // bytes per bulk copy
-constexpr int kXSub = 32768;                       // x_new bytes staged per sub-chunk
+constexpr int kXSub = 24576;                       // largest chunk (x_new bytes staged per chunk)
 constexpr long long kWaitCycles = 2000000000LL;    // ~1 s at 2 GHz
 
 __device__ __forceinline__ long long warp_sum(long long v) {
@@ -99,10 +99,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
 
 struct Smem {
   uint8_t stage[kGrWarps][kStages][kPiece];   // per-warp piece rings
-  uint8_t xs[kXSub];                          // x_new sub-chunk
+  uint8_t xs[2][kXSub];                       // x_new pieces of the current and the next chunk
   unsigned long long bar[kGrWarps][kStages];  // one mbarrier per stage
-  unsigned long long xbar;                    // x_new barrier
-  int chunk;                                  // chunk taken by the CTA
+  unsigned long long xbar[2];                 // x_new barriers
+  int cq[2];                                  // chunk index of chunk ordinal k at [k & 1]
+  int fail;                                   // a wait expired in some warp
   long long acc_i[SDMD_MAX_M];
   double acc_d[SDMD_MAX_M];
   double acc_im[SDMD_MAX_M];                  // imaginary parts (complex snapshots)
@@ -192,111 +193,126 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
   if (threadIdx.x == 0) {
     for (int w = 0; w < kGrWarps; ++w)
       for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&sm.bar[w][s]), 1);
-    mbar_init(smem_u32(&sm.xbar), 1);
+    mbar_init(smem_u32(&sm.xbar[0]), 1);
+    mbar_init(smem_u32(&sm.xbar[1]), 1);
+    sm.fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   __syncthreads();
   const uint8_t* xnew = a.ring + (int64_t)a.s_new * a.slot_bytes;
   const int nmine = (a.c > warp) ? (a.c - warp + kGrWarps - 1) / kGrWarps : 0;  // slots of this warp
-  unsigned g = 0;                  // pieces this warp has consumed so far (all sub-chunks)
-  bool failed = false;             // a bounded wait expired: stop issuing, drain, finish
-  int sub_i = 0;                   // sub-chunks processed (x_new barrier phase)
-  for (;;) {
-  __syncthreads();                 // the previous chunk's partials are out
-  if (threadIdx.x == 0) sm.chunk = failed ? a.nblk : (int)atomicAdd(a.ticket + 1, 1u);
-  __syncthreads();
-  const int ch = sm.chunk;
-  if (ch >= a.nblk) break;
-  const int64_t beg = (int64_t)ch * a.chunk;
-  const int64_t end = min(beg + a.chunk, a.slot_bytes);
-  for (int64_t sub = beg; sub < end; sub += kXSub, ++sub_i) {
-    const int len = (int)min((int64_t)kXSub, end - sub);          // multiple of kPiece
-    const int npieces = len / kPiece;
-    const int nitems = nmine * npieces;
-    const bool live = !failed;     // copies are issued in this sub-chunk only if live
-    __syncthreads();               // xs is free again
-    if (threadIdx.x == 0 && live) {
-      const unsigned xb = smem_u32(&sm.xbar);
-      mbar_expect_tx(xb, (unsigned)len);
-      bulk_g2s(smem_u32(sm.xs), xnew + sub, (unsigned)len, xb);
-    }
-    if (lane == 0 && live) {       // prologue: this warp's first kStages pieces
-      for (int it = 0; it < kStages && it < nitems; ++it) {
-        const unsigned s = (g + it) % kStages;
-        const int j = (a.s_first + warp + kGrWarps * (it / npieces)) % a.m;
-        const unsigned b = smem_u32(&sm.bar[warp][s]);
-        mbar_expect_tx(b, kPiece);
-        bulk_g2s(smem_u32(sm.stage[warp][s]),
-                 a.ring + (int64_t)j * a.slot_bytes + sub + (int64_t)kPiece * (it % npieces), kPiece, b);
+  // chunk ordinal k of this CTA -> chunk index sm.cq[k & 1] (>= nblk: none)
+  auto chunk_len = [&](int ch) -> int { return (int)min(a.chunk, a.slot_bytes - (int64_t)ch * a.chunk); };
+  auto issue_x = [&](int k, int ch) {          // x_new's piece of chunk ordinal k
+    const unsigned xb = smem_u32(&sm.xbar[k & 1]);
+    const int len = chunk_len(ch);
+    mbar_expect_tx(xb, (unsigned)len);
+    bulk_g2s(smem_u32(sm.xs[k & 1]), xnew + (int64_t)ch * a.chunk, (unsigned)len, xb);
+  };
+  if (threadIdx.x == 0) {
+    const int c0 = (int)atomicAdd(a.ticket + 1, 1u);
+    sm.cq[0] = c0;
+    if (c0 < a.nblk) issue_x(0, c0);
+  }
+  // per-warp item stream: item (k, i) = piece i % np of slot i / np of chunk
+  // ordinal k; lane 0 keeps the ring kStages items ahead, into chunk k + 1
+  // once it is known
+  unsigned consumed = 0, issued = 0;   // items of this warp (all chunks)
+  int kc = 0, ic = 0;                  // issue cursor: chunk ordinal, item
+  bool failed = false;                 // a bounded wait expired: stop issuing, drain, finish
+  auto top_up = [&](int k) {           // chunk ordinals k and k + 1 are known
+    if (lane != 0 || failed) return;
+    while (issued - consumed < (unsigned)kStages && kc <= k + 1) {
+      const int ch = sm.cq[kc & 1];
+      if (ch >= a.nblk) break;
+      const int np = chunk_len(ch) / kPiece;
+      if (ic >= nmine * np) {
+        ++kc;
+        ic = 0;
+        continue;
       }
+      const unsigned s = issued % kStages;
+      const int j = (a.s_first + warp + kGrWarps * (ic / np)) % a.m;
+      const unsigned b = smem_u32(&sm.bar[warp][s]);
+      mbar_expect_tx(b, kPiece);
+      bulk_g2s(smem_u32(sm.stage[warp][s]),
+               a.ring + (int64_t)j * a.slot_bytes + (int64_t)ch * a.chunk + (int64_t)kPiece * (ic % np), kPiece, b);
+      ++ic;
+      ++issued;
     }
-    int fail_it = -1;              // first item not consumed after a failure
-    if (live && !mbar_wait(smem_u32(&sm.xbar), (unsigned)(sub_i & 1))) failed = true;
+  };
+  for (int k = 0;; ++k) {
+    __syncthreads();                   // chunk k - 1 fully consumed: xs[(k + 1) & 1] is free
+    if (threadIdx.x == 0) {
+      const int ch = sm.cq[k & 1];
+      int nx = a.nblk;
+      if (ch < a.nblk && !sm.fail) nx = (int)atomicAdd(a.ticket + 1, 1u);
+      sm.cq[(k + 1) & 1] = nx;
+      if (nx < a.nblk) issue_x(k + 1, nx);
+    }
+    __syncthreads();
+    const int ch = sm.cq[k & 1];
+    if (ch >= a.nblk) break;
+    const int np = chunk_len(ch) / kPiece;
+    const int nitems = nmine * np;
+    top_up(k);
+    if (!failed && !mbar_wait(smem_u32(&sm.xbar[k & 1]), (unsigned)((k >> 1) & 1))) failed = true;
     failed = __any_sync(0xffffffffu, failed);
-    if (live && failed) fail_it = 0;
     unsigned int su = 0;
     double sd = 0.0, si = 0.0;
-    for (int it = 0; it < nitems; ++it) {
-      const unsigned gi = g + it, s = gi % kStages, par = (gi / kStages) & 1;
-      const int q = it % npieces;
-      bool bad = false;
-      if (!failed && !mbar_wait(smem_u32(&sm.bar[warp][s]), par)) bad = true;
-      if (__any_sync(0xffffffffu, bad) && !failed) {
+    const uint8_t* xs = sm.xs[k & 1];
+    for (int it = 0; it < nitems && !failed; ++it) {
+      const unsigned s = consumed % kStages, par = (consumed / kStages) & 1;
+      const int q = it % np;
+      bool bad = !mbar_wait(smem_u32(&sm.bar[warp][s]), par);
+      if (__any_sync(0xffffffffu, bad)) {
         failed = true;
-        fail_it = it;
+        break;
       }
-      if (!failed) {
-        const uint8_t* piece = sm.stage[warp][s];
-        const uint8_t* xq = sm.xs + kPiece * q;
-        if constexpr (kU8) {
+      const uint8_t* piece = sm.stage[warp][s];
+      const uint8_t* xq = xs + kPiece * q;
+      if constexpr (kU8) {
 #pragma unroll
-          for (int u = 0; u < kPiece / 512; ++u) {
-            const uint4 v = *reinterpret_cast<const uint4*>(piece + 16 * lane + 512 * u);
-            const uint4 w = *reinterpret_cast<const uint4*>(xq + 16 * lane + 512 * u);
-            su = __dp4a(v.x, w.x, su);
-            su = __dp4a(v.y, w.y, su);
-            su = __dp4a(v.z, w.z, su);
-            su = __dp4a(v.w, w.w, su);
-          }
-        } else if constexpr (kMode == kModeF32) {
-          float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
-#pragma unroll
-          for (int u = 0; u < kPiece / 512; ++u) {
-            const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
-            const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
-            f0 = fmaf(v.x, w.x, f0);
-            f1 = fmaf(v.y, w.y, f1);
-            f2 = fmaf(v.z, w.z, f2);
-            f3 = fmaf(v.w, w.w, f3);
-          }
-          sd += (double)((f0 + f1) + (f2 + f3));
-        } else {
-          // two complex64 values per 16 bytes: conj(v) * w
-          float r0 = 0.f, r1 = 0.f, i0 = 0.f, i1 = 0.f;
-#pragma unroll
-          for (int u = 0; u < kPiece / 512; ++u) {
-            const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
-            const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
-            r0 = fmaf(v.x, w.x, fmaf(v.y, w.y, r0));
-            r1 = fmaf(v.z, w.z, fmaf(v.w, w.w, r1));
-            i0 = fmaf(v.x, w.y, fmaf(-v.y, w.x, i0));
-            i1 = fmaf(v.z, w.w, fmaf(-v.w, w.z, i1));
-          }
-          sd += (double)(r0 + r1);
-          si += (double)(i0 + i1);
+        for (int u = 0; u < kPiece / 512; ++u) {
+          const uint4 v = *reinterpret_cast<const uint4*>(piece + 16 * lane + 512 * u);
+          const uint4 w = *reinterpret_cast<const uint4*>(xq + 16 * lane + 512 * u);
+          su = __dp4a(v.x, w.x, su);
+          su = __dp4a(v.y, w.y, su);
+          su = __dp4a(v.z, w.z, su);
+          su = __dp4a(v.w, w.w, su);
         }
+      } else if constexpr (kMode == kModeF32) {
+        float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPiece / 512; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+          const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+          f0 = fmaf(v.x, w.x, f0);
+          f1 = fmaf(v.y, w.y, f1);
+          f2 = fmaf(v.z, w.z, f2);
+          f3 = fmaf(v.w, w.w, f3);
+        }
+        sd += (double)((f0 + f1) + (f2 + f3));
+      } else {
+        // two complex64 values per 16 bytes: conj(v) * w
+        float r0 = 0.f, r1 = 0.f, i0 = 0.f, i1 = 0.f;
+#pragma unroll
+        for (int u = 0; u < kPiece / 512; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+          const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+          r0 = fmaf(v.x, w.x, fmaf(v.y, w.y, r0));
+          r1 = fmaf(v.z, w.z, fmaf(v.w, w.w, r1));
+          i0 = fmaf(v.x, w.y, fmaf(-v.y, w.x, i0));
+          i1 = fmaf(v.z, w.w, fmaf(-v.w, w.z, i1));
+        }
+        sd += (double)(r0 + r1);
+        si += (double)(i0 + i1);
       }
-      __syncwarp();                // all lanes are done reading stage s
-      if (lane == 0 && !failed && it + kStages < nitems) {
-        const int nx = it + kStages;
-        const int j = (a.s_first + warp + kGrWarps * (nx / npieces)) % a.m;
-        const unsigned b = smem_u32(&sm.bar[warp][s]);
-        mbar_expect_tx(b, kPiece);
-        bulk_g2s(smem_u32(sm.stage[warp][s]),
-                 a.ring + (int64_t)j * a.slot_bytes + sub + (int64_t)kPiece * (nx % npieces), kPiece, b);
-      }
-      if (q == npieces - 1) {      // this slot is finished for the sub-chunk
-        const int jj = warp + kGrWarps * (it / npieces);
+      __syncwarp();                    // all lanes are done reading stage s
+      ++consumed;
+      top_up(k);
+      if (q == np - 1) {               // this slot is finished for the chunk
+        const int jj = warp + kGrWarps * (it / np);
         if constexpr (kU8) {
           const long long t = warp_sum((long long)su);
           if (lane == 0) sm.acc_i[jj] += t;
@@ -313,32 +329,34 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
         }
       }
     }
-    if (fail_it >= 0) {
-      // copies issued but not consumed are items [fail_it, fail_it + kStages):
-      // wait for each (bounded) before the shared memory is released
-      for (int k = fail_it; k < nitems && k < fail_it + kStages; ++k) {
-        const unsigned gk = g + k;
-        mbar_wait(smem_u32(&sm.bar[warp][gk % kStages]), (gk / kStages) & 1);
+    if (failed) {
+      if (lane == 0) {
+        atomicOr(a.status, kDevTimeout);
+        sm.fail = 1;
       }
-      mbar_wait(smem_u32(&sm.xbar), (unsigned)(sub_i & 1));
-      if (lane == 0) atomicOr(a.status, kDevTimeout);
     }
-    g += nitems;
-  }
-  failed = __syncthreads_or(failed);
-  // this chunk's partials (each thread writes and clears its own slots)
-  for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
-    if constexpr (kU8) {
-      static_cast<long long*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_i[j];
-    } else if constexpr (kMode == kModeF32) {
-      static_cast<double*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_d[j];
-    } else {
-      static_cast<double2*>(a.partials)[(int64_t)j * a.nblk + ch] = make_double2(sm.acc_d[j], sm.acc_im[j]);
+    __syncthreads();
+    // this chunk's partials (each thread writes and clears its own slots)
+    for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
+      if constexpr (kU8) {
+        static_cast<long long*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_i[j];
+      } else if constexpr (kMode == kModeF32) {
+        static_cast<double*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_d[j];
+      } else {
+        static_cast<double2*>(a.partials)[(int64_t)j * a.nblk + ch] = make_double2(sm.acc_d[j], sm.acc_im[j]);
+      }
+      sm.acc_i[j] = 0;
+      sm.acc_d[j] = 0.0;
+      sm.acc_im[j] = 0.0;
     }
-    sm.acc_i[j] = 0;
-    sm.acc_d[j] = 0.0;
-    sm.acc_im[j] = 0.0;
-  }
+    if (sm.fail) {
+      // copies issued but not consumed must land before the shared memory
+      // is released (bounded waits); then stop
+      if (lane == 0)
+        for (unsigned gk = consumed; gk < issued; ++gk) mbar_wait(smem_u32(&sm.bar[warp][gk % kStages]), (gk / kStages) & 1);
+      if (threadIdx.x == 0 && sm.cq[(k + 1) & 1] < a.nblk) mbar_wait(smem_u32(&sm.xbar[(k + 1) & 1]), (unsigned)(((k + 1) >> 1) & 1));
+      break;
+    }
   }
   if constexpr (kU8) {
     finish_row<long long>(a, sm);
@@ -361,7 +379,8 @@ void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t*
   const int64_t units = (slot_bytes + kPiece - 1) / kPiece;
   int64_t want = (int64_t)kChunksPerSm * (num_sms > 0 ? num_sms : 1);
   if (want > units) want = units;
-  const int64_t per = (units + want - 1) / want;     // units per CTA
+  int64_t per = (units + want - 1) / want;           // 4 KiB units per chunk
+  if (per > kXSub / kPiece) per = kXSub / kPiece;   // at most 24 KiB (x_new double buffer)
   *chunk = per * kPiece;
   *nblk = (int32_t)((units + per - 1) / per);
 }

@@ -27,12 +27,16 @@ __device__ __forceinline__ void mbar_arrive2(unsigned bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], 2;\n" ::"r"(bar) : "memory");
 }
 
+// The waiting thread is suspended until the phase completes or the hint
+// (ns) runs out, so waiting warps do not take issue slots from working ones.
+constexpr unsigned kTcSuspendHintNs = 20000;
+
 __device__ __forceinline__ bool mbar_try(unsigned bar, unsigned parity) {
   unsigned ok;
   asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(kTcSuspendHintNs)
       : "memory");
   return ok != 0;
 }
