@@ -161,6 +161,18 @@ SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const v
  */
 SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
 
+/*
+ * sdmd_push_batch -- append k snapshots at once (1 <= k <= m): the
+ * multi-column catch-up of a stream that fell behind. Snapshot j is at
+ * X + j * ld elements (ld >= n), host or device memory; each must stay valid
+ * until the stream reaches the call. The resulting G equals that of k
+ * sdmd_push calls. uint8 windows of at most 127 snapshots (with
+ * SDMD_OPT_REBUILD_TENSOR): the k new rows and columns of G in one pass over
+ * the window on the tensor cores (exact int64) instead of k passes; other
+ * handles: k sdmd_push calls. SDMD_ERR_ARG for a bad k, ld or pointer.
+ */
+SDMD_API int sdmd_push_batch(sdmd_t h, int32_t k, const void *X, int64_t ld, void *stream);
+
 /* sdmd_count -- number of snapshots pushed so far (host pointer). Host-side
  * bookkeeping only; does not touch the device. */
 SDMD_API int sdmd_count(sdmd_t h, int64_t *count);
@@ -280,12 +292,12 @@ enum {
                                fp16 terms, FP32 accumulation); 0: CUDA-core
                                FP32 kernel */
     ,
-    SDMD_OPT_REBUILD_TENSOR = 2 /* 1 (default): sdmd_rebuild of uint8 windows of
-                                   at most 127 snapshots in one pass on the
-                                   tensor cores (centred fp16 pixels, exact
-                                   int64 G); 0: one Gram-row pass per
-                                   snapshot (bit-identical to streaming for
-                                   every dtype) */
+    SDMD_OPT_REBUILD_TENSOR = 2 /* 1 (default): sdmd_rebuild and sdmd_push_batch
+                                   of uint8 windows of at most 127 snapshots
+                                   in one pass on the tensor cores (centred
+                                   fp16 pixels, exact int64 G); 0: one
+                                   Gram-row pass per snapshot (bit-identical
+                                   to streaming for every dtype) */
 };
 
 /* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */

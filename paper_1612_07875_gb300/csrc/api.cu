@@ -478,6 +478,67 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   return SDMD_OK;
 }
 
+namespace {
+
+// Lazily allocated scratch of the tensor-core Gram pass.
+int ensure_gram_full_scratch(sdmd_s* h) {
+  if (h->gf_partials) return SDMD_OK;
+  cudaError_t e = cudaMalloc(&h->gf_partials, (size_t)kGramFullMaxCtas * 128 * 128 * sizeof(long long));
+  if (e == cudaSuccess) e = cudaMalloc(&h->gf_sched, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->gf_sched, 0, sizeof(unsigned));
+  if (e != cudaSuccess) return fail(SDMD_ERR_OOM, "tensor-core Gram scratch: %s", cudaGetErrorString(e));
+  return SDMD_OK;
+}
+
+}  // namespace
+
+int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_push_batch: NULL handle");
+  if (h->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_push_batch: sparse handle");
+  if (!X || k < 1 || k > h->m || ld < h->n)
+    return fail(SDMD_ERR_ARG, "sdmd_push_batch: k=%d (1..%d), ld=%lld (>= n) or NULL data", k, h->m, (long long)ld);
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int c_after = (int)(h->count + k < h->m ? h->count + k : h->m);
+  const size_t elem_bytes = (size_t)h->elem;
+  const uint8_t* src = static_cast<const uint8_t*>(X);
+  if (!(h->dtype == SDMD_U8 && h->rebuild_tensor && c_after <= 127)) {
+    // k ordinary pushes (one Gram-row pass each)
+    for (int j = 0; j < k; ++j) {
+      const int rc = sdmd_push(h, src + (size_t)j * ld * elem_bytes, stream);
+      if (rc != SDMD_OK) return rc;
+    }
+    return SDMD_OK;
+  }
+  const int rc0 = ensure_gram_full_scratch(h);
+  if (rc0 != SDMD_OK) return rc0;
+  for (int j = 0; j < k; ++j) {        // ingest only
+    wait_ring_readers(h, st);
+    TraceScope ts(h, SDMD_K_INGEST, st);
+    CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, src + (size_t)j * ld * elem_bytes,
+                       (size_t)(h->n * h->elem), cudaMemcpyDefault, st));
+    h->head = (h->head + 1) % h->cap;
+    h->count += 1;
+  }
+  // rows and columns of the k new snapshots in one pass over the window
+  const int kt = k < c_after ? k : c_after;
+  GramFullArgs ga;
+  ga.ring = h->ring;
+  ga.slot_bytes = h->slot_bytes;
+  ga.n = h->n;
+  ga.m = h->cap;
+  ga.start = oldest_slot(h);
+  ga.c = c_after;
+  ga.k = kt;
+  ga.partials = h->gf_partials;
+  ga.sched = h->gf_sched;
+  ga.G = static_cast<long long*>(h->G);
+  ga.status = h->status;
+  TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+  CK(launch_gram_full_tc(ga, nullptr, st));
+  return SDMD_OK;
+}
+
 int sdmd_rebuild(sdmd_t h, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_rebuild: NULL handle");
   DeviceScope ds(h->device);
@@ -486,12 +547,8 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   const int first = oldest_slot(h);
   if (h->dtype == SDMD_U8 && h->rebuild_tensor && c >= 1 && c <= 127) {
     // one pass over the window on the tensor cores, exact int64
-    if (!h->gf_partials) {
-      cudaError_t e = cudaMalloc(&h->gf_partials, (size_t)kGramFullMaxCtas * 128 * 128 * sizeof(long long));
-      if (e == cudaSuccess) e = cudaMalloc(&h->gf_sched, sizeof(unsigned));
-      if (e == cudaSuccess) e = cudaMemset(h->gf_sched, 0, sizeof(unsigned));
-      if (e != cudaSuccess) return fail(SDMD_ERR_OOM, "sdmd_rebuild: %s", cudaGetErrorString(e));
-    }
+    const int rc0 = ensure_gram_full_scratch(h);
+    if (rc0 != SDMD_OK) return rc0;
     GramFullArgs ga;
     ga.ring = h->ring;
     ga.slot_bytes = h->slot_bytes;
@@ -499,6 +556,7 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
     ga.m = h->cap;
     ga.start = first;
     ga.c = c;
+    ga.k = c;
     ga.partials = h->gf_partials;
     ga.sched = h->gf_sched;
     ga.G = static_cast<long long*>(h->G);

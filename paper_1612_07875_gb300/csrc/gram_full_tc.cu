@@ -12,9 +12,13 @@
 //   G_ij = G'_ij + 128 (s_i + s_j) + 128^2 n        (exact int64).
 //
 // GEMM. The c snapshots (c <= 127) plus the ones row are the rows of one
-// K-major fp16 tile T (128 rows x 256 positions, zero rows beyond c + 1);
-// D[128 x N] += T T^T uses the same shared-memory descriptor for A and B
-// (N = c + 1 rounded up to 16). Core matrix (rg, kg) = rows 8 rg .. 8 rg + 7
+// K-major fp16 tile T (128 rows x 256 positions, zero rows beyond c + 1):
+// first the k target snapshots (the k newest; k = c for a full rebuild), then
+// the ones row, then the older ones. D[128 x N] += T T_B^T, where T_B is the
+// first N = k + 1 (rounded up to 16) rows of the same tile, so A and B share
+// one shared-memory descriptor and D holds every <x_i, x_j> with x_j a target
+// (the k new rows and columns of G: a multi-column catch-up reads the window
+// once for all k). Core matrix (rg, kg) = rows 8 rg .. 8 rg + 7
 // x positions 8 kg .. 8 kg + 7 at (kg * 16 + rg) * 128 bytes: LBO 2048 B
 // between K neighbours, SBO 128 B between row groups.
 //
@@ -60,7 +64,7 @@ constexpr int kStages = 2;           // staging ring (u8)
 constexpr int kTiles = 2;            // fp16 tile ring
 constexpr int kPitch = 272;          // staging row pitch, bytes
 constexpr int kTileBytes = kRowsM * kKst * 2;              // 65536
-constexpr int kStageBytes = (kRowsM - 1) * kPitch;         // 34544
+constexpr int kStageBytes = kRowsM * kPitch;               // 34816
 constexpr int kTmemCols = 256;       // two accumulators of <= 128 columns
 
 struct FullShared {
@@ -114,8 +118,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
   FullShared& sh = *reinterpret_cast<FullShared*>(smem + kTiles * kTileBytes + kStages * kStageBytes);
   volatile int* stop = &sh.stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c = a.c;                     // snapshots; row c is the ones row
-  const int npad = ((c + 1 + 15) / 16) * 16;
+  const int c = a.c;                     // snapshots (tile rows 0 .. c except the ones row)
+  const int kt = a.k;                    // targets: tile rows 0 .. kt - 1; row kt is the ones row
+  const int npad = ((kt + 1 + 15) / 16) * 16;
   const int64_t nchunks = (a.n + (int64_t)kKst * kStepsPerChunk - 1) / ((int64_t)kKst * kStepsPerChunk);
 
   if (tid == 0) {
@@ -133,7 +138,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == kMmaWarp) tmem_alloc(smem_u32(&sh.tmem_base), kTmemCols);
-  for (int i = tid; i < c; i += kThreads) sh.tab[i] = (int64_t)((a.start + i) % a.m) * a.slot_bytes;
+  for (int r = tid; r <= c; r += kThreads) {
+    if (r == kt) continue;
+    const int t = (r < kt) ? c - kt + r : r - kt - 1;      // window time index of tile row r
+    sh.tab[r] = (int64_t)((a.start + t) % a.m) * a.slot_bytes;
+  }
   // rows beyond the ones row stay zero in both tiles
   for (int idx = tid; idx < kTiles * kRowsM * (kKst / 8); idx += kThreads) {
     const int t = idx / (kRowsM * (kKst / 8)), rem = idx - t * (kRowsM * (kKst / 8));
@@ -178,13 +187,13 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
           }
           if (cbase < nchunks) {               // this chunk's first 8 K-steps (2 KiB per row) into L2
             const int64_t x0 = (int64_t)cbase * kStepsPerChunk * kKst;
-            for (int q = cw * 32 + lane; q < c; q += kConvWarps * 32)
-              bulk_prefetch_l2(a.ring + sh.tab[q] + x0, 8 * kKst);
+            for (int q = cw * 32 + lane; q <= c; q += kConvWarps * 32)
+              if (q != kt) bulk_prefetch_l2(a.ring + sh.tab[q] + x0, 8 * kKst);
           }
         } else if (o == 8 && cbase < nchunks) {  // the second half
           const int64_t x0 = ((int64_t)cbase * kStepsPerChunk + 8) * kKst;
-          for (int q = cw * 32 + lane; q < c; q += kConvWarps * 32)
-            bulk_prefetch_l2(a.ring + sh.tab[q] + x0, 8 * kKst);
+          for (int q = cw * 32 + lane; q <= c; q += kConvWarps * 32)
+            if (q != kt) bulk_prefetch_l2(a.ring + sh.tab[q] + x0, 8 * kKst);
         }
         if (cbase < nchunks) {
           p0 = ((int64_t)cbase * kStepsPerChunk + o) * kKst;
@@ -208,7 +217,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
             const int row = 8 * g + 2 * t + (lane >> 4), ch = lane & 15;
-            if (row < c) cp_async16(dst + (unsigned)(row * kPitch + 16 * ch), a.ring + sh.tab[row] + p0 + 16 * ch);
+            if (row <= c && row != kt)
+              cp_async16(dst + (unsigned)(row * kPitch + 16 * ch), a.ring + sh.tab[row] + p0 + 16 * ch);
           }
         }
       }
@@ -248,7 +258,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
           if (row > c) continue;
           const int64_t pos = p0 + 16 * ch;
           uint4 lo, hi;
-          if (row < c) {
+          if (row != kt) {
             const uint4 w = *reinterpret_cast<const uint4*>(sb + row * kPitch + 16 * ch);
             lo.x = f16x2_centred(w.x, 0x4140u);
             lo.y = f16x2_centred(w.x, 0x4342u);
@@ -390,7 +400,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int col = col0 + 8 * pc + i;
-        if (8 * pc < cols && row <= c && col <= c) P[(int64_t)row * kRowsM + col] = sum[pc][i];
+        if (8 * pc < cols && row <= c && col <= kt) P[(int64_t)row * kRowsM + col] = sum[pc][i];
       }
   }
   __syncthreads();
@@ -399,38 +409,44 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
   if (warp == kMmaWarp) tmem_dealloc(tbase, kTmemCols);
 }
 
-// G_ij = G'_ij + 128 (s_i + s_j) + 128^2 n from the per-CTA partials, written
-// to the physical slots (one block per row i, one thread per column j).
+// G_ij = G'_ij + 128 (s_i + s_j) + 128^2 n from the per-CTA partials, for
+// every tile row i (one block each) and target j (threads), written to both
+// G[i][j] and G[j][i] at the physical slots.
+__global__ void reset_sched_kernel(unsigned* sched) { sched[0] = 0u; }   // ready for the next launch
+
 __global__ void gram_full_finish_kernel(GramFullArgs a, int ctas) {
   __shared__ long long si_n[2];
-  const int i = blockIdx.x, c = a.c;
-  if (threadIdx.x < 2) {                 // s_i = G'_ic and n = G'_cc
-    const int col = c;
-    const int rw = (threadIdx.x == 0) ? i : c;
+  const int i = blockIdx.x, c = a.c, kt = a.k;
+  if (i == kt) return;                   // the ones row
+  if (threadIdx.x < 2) {                 // s_i = G'_i,kt and n = G'_kt,kt
+    const int rw = (threadIdx.x == 0) ? i : kt;
     long long s = 0;
-    for (int b = 0; b < ctas; ++b) s += a.partials[((int64_t)b * kRowsM + rw) * kRowsM + col];
+    for (int b = 0; b < ctas; ++b) s += a.partials[((int64_t)b * kRowsM + rw) * kRowsM + kt];
     si_n[threadIdx.x] = s;
   }
   __syncthreads();
   const long long si = si_n[0], n = si_n[1];
-  for (int j = threadIdx.x; j < c; j += blockDim.x) {
+  const int ti = (i < kt) ? c - kt + i : i - kt - 1;
+  const int pi = (a.start + ti) % a.m;
+  for (int j = threadIdx.x; j < kt; j += blockDim.x) {
     long long g = 0, sj = 0;
     for (int b = 0; b < ctas; ++b) {
       const long long* P = a.partials + (int64_t)b * kRowsM * kRowsM;
       g += P[(int64_t)i * kRowsM + j];
-      sj += P[(int64_t)j * kRowsM + c];
+      sj += P[(int64_t)j * kRowsM + kt];
     }
     const long long v = g + 128LL * (si + sj) + 16384LL * n;
-    const int pi = (a.start + i) % a.m, pj = (a.start + j) % a.m;
+    const int pj = (a.start + c - kt + j) % a.m;
     a.G[(int64_t)pi * a.m + pj] = v;
+    a.G[(int64_t)pj * a.m + pi] = v;
   }
-  if (i == 0 && threadIdx.x == 0) a.sched[0] = 0u;   // ready for the next launch
+  (void)c;
 }
 
 }  // namespace
 
 cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream_t st) {
-  if (a.c < 1 || a.c > kRowsM - 1) return cudaErrorNotSupported;
+  if (a.c < 1 || a.c > kRowsM - 1 || a.k < 1 || a.k > a.c) return cudaErrorNotSupported;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gram_full_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -445,7 +461,10 @@ cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream
   gram_full_tc_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  gram_full_finish_kernel<<<a.c, 128, 0, st>>>(a, ctas);
+  gram_full_finish_kernel<<<a.c + 1, 128, 0, st>>>(a, ctas);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  reset_sched_kernel<<<1, 1, 0, st>>>(a.sched);
   if (ctas_out) *ctas_out = ctas;
   return cudaGetLastError();
 }

@@ -38,7 +38,8 @@ struct GramRowArgs {
   int* status;           // device status word (kDevTimeout on an expired wait)
 };
 
-// Full-window Gram of uint8 snapshots on the tensor cores (c <= 127).
+// Gram rows/columns of the k newest uint8 snapshots against the window
+// (k = c: the full Gram) on the tensor cores, exact (c <= 127).
 struct GramFullArgs {
   const uint8_t* ring;
   int64_t slot_bytes;
@@ -46,6 +47,7 @@ struct GramFullArgs {
   int32_t m;             // ring modulus (G is m x m, physical slots)
   int32_t start;         // physical slot of the oldest resident snapshot
   int32_t c;             // resident snapshots
+  int32_t k;             // targets: the k newest (k = c: the whole Gram)
   long long* partials;   // [kGramFullMaxCtas][128][128] per-CTA sums
   unsigned* sched;       // chunk counter, zero between launches
   long long* G;

@@ -73,6 +73,7 @@ _SIGNATURES = {
     "sdmd_gram_row_static": [_I32, _VP, _I64, _I32, _VP, _I64, _VP, _VP],
     "sdmd_modes_phase_cycles": [_VP, ctypes.POINTER(_I64), _I32, _VP],
     "sdmd_amplitudes": [_VP, _VP, ctypes.POINTER(_I32), _VP],
+    "sdmd_push_batch": [_VP, _I32, _VP, _I64, _VP],
     "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
 }
 
@@ -194,6 +195,11 @@ def sdmd_modes(h, r, phi, lam, r_out=None, stream=None):
 
 def sdmd_svd(h, r, sigma, V, stream=None):
     _check(lib().sdmd_svd(h, int(r), ptr(sigma), ptr(V), stream_handle(stream)), "sdmd_svd")
+
+
+def sdmd_push_batch(h, k, X, ld, stream=None):
+    """Append k snapshots (snapshot j at X + j * ld elements)."""
+    _check(lib().sdmd_push_batch(h, int(k), ptr(X), int(ld), stream_handle(stream)), "sdmd_push_batch")
 
 
 def sdmd_amplitudes(h, b, stream=None, want_index=True):

@@ -264,3 +264,63 @@ def test_tensor_core_rebuild_exact(cuda_device, n, m, pushes, pattern):
         assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
+
+
+@pytest.mark.parametrize("n,m,pre,k,dtype,device_src", [
+    (40009, 9, 23, 4, "u8", True),          # wrapped window
+    (4096 * 3 + 17, 100, 120, 8, "u8", False),   # host source
+    (100003, 20, 5, 10, "u8", True),        # ramp-up: 5 resident, 10 new
+    (5000, 16, 3, 16, "u8", True),          # k = m: every resident snapshot is new
+    (6000, 127, 130, 127, "u8", True),      # the largest window on the tensor path
+    (5000, 128, 130, 3, "u8", True),        # beyond it: k ordinary pushes
+    (3001, 12, 15, 5, "f32", True),         # float: k ordinary pushes
+])
+def test_push_batch_equals_sequential_pushes(cuda_device, n, m, pre, k, dtype, device_src):
+    # SURVEY f2 multi-column catch-up: k new rows/columns of G in one pass
+    # over the window; the Gram must equal that of k single pushes (exactly
+    # for uint8, bit for bit for the float fallback) and the oracle's.
+    rng = np.random.default_rng(n + k)
+    dt = S.SDMD_U8 if dtype == "u8" else S.SDMD_F32
+    make = (lambda: rng.integers(0, 256, n, dtype=np.uint8)) if dtype == "u8" else \
+        (lambda: rng.standard_normal(n).astype(np.float32))
+    first = [make() for _ in range(pre)]
+    batch = np.stack([make() for _ in range(k)])          # k x n, snapshot j in row j
+    h1 = S.sdmd_create(n, m, dt)
+    h2 = S.sdmd_create(n, m, dt)
+    so = oracle.StreamOracle(n, m, dtype)
+    try:
+        for x in first:
+            S.sdmd_push(h1, torch.from_numpy(x).to(cuda_device))
+            S.sdmd_push(h2, torch.from_numpy(x).to(cuda_device))
+            so.push(x)
+        src = torch.from_numpy(batch).to(cuda_device) if device_src else batch
+        S.sdmd_push_batch(h1, k, src, n)
+        for j in range(k):
+            S.sdmd_push(h2, torch.from_numpy(batch[j]).to(cuda_device))
+            so.push(batch[j])
+        c = min(pre + k, m)
+        words = torch.int64 if dtype == "u8" else torch.float64
+        G1 = torch.empty(c, c, dtype=words, device=cuda_device)
+        G2 = torch.empty(c, c, dtype=words, device=cuda_device)
+        S.sdmd_gram(h1, G1)
+        S.sdmd_gram(h2, G2)
+        torch.cuda.synchronize()
+        assert torch.equal(G1, G2)
+        if dtype == "u8":
+            assert np.array_equal(G1.cpu().numpy(), so.gram())
+        assert S.sdmd_status(h1) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h1)
+        S.sdmd_destroy(h2)
+
+
+def test_push_batch_argument_errors(cuda_device):
+    h = S.sdmd_create(100, 4, S.SDMD_U8)
+    x = torch.zeros(5, 100, dtype=torch.uint8, device=cuda_device)
+    try:
+        for k, ld in ((0, 100), (5, 100), (2, 99)):
+            with pytest.raises(S.SdmdError) as ei:
+                S.sdmd_push_batch(h, k, x, ld)
+            assert ei.value.code == S.SDMD_ERR_ARG
+    finally:
+        S.sdmd_destroy(h)
