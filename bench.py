@@ -289,6 +289,37 @@ def measure_rebuild(S, h, stream, n, reps=3):
     return out
 
 
+def measure_catchup(S, h, frames, t0, stream, n, k=8, reps=3):
+    """Multi-column catch-up: k frames appended with one sdmd_push_batch (one
+    tensor-core pass over the window) vs k sdmd_push calls (k Gram-row passes)."""
+    import torch
+    sh = stream.cuda_stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    S.sdmd_sync(h, sh)
+    out = {}
+    for name in ("push_batch", "single_pushes"):
+        times = []
+        for r in range(reps + 1):
+            i0 = (t0 + r * k) % (frames.shape[0] - k)
+            block = frames[i0:i0 + k]
+            with torch.cuda.stream(stream):
+                e0.record(stream)
+                if name == "push_batch":
+                    S.sdmd_push_batch(h, k, block, n, sh)
+                else:
+                    for j in range(k):
+                        S.sdmd_push(h, block[j], sh)
+                e1.record(stream)
+            stream.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        out[name] = {"ms": ms, "frames_per_s": k / (ms * 1e-3)}
+    out["k"] = k
+    out["note"] = "push_batch: ingest + one exact tensor-core pass for the k new rows/columns"
+    return out
+
+
 def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
     """Per-push time of the Fourier-sparse Gram row (scatter + row kernels)."""
     import torch
@@ -452,10 +483,11 @@ def run_ours(args):
         ems = e0.elapsed_time(e1)
         e2e = {"value": world * Ke / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n,
                "d2h_bytes_per_step": 2 * R_MODES * 8 + 4, "steps": Ke}
-    # ---- a9: full-window rebuild of G (one Gram-row pass per resident slot)
-    rebuild = sparse = None
+    # ---- a9: full-window rebuild of G; f2: multi-column catch-up of 8 frames
+    rebuild = sparse = catchup = None
     if not args.no_secondary:
         rebuild = measure_rebuild(S, h, stream, n)
+        catchup = measure_catchup(S, h, frames, 0, stream, n)
     S.sdmd_destroy(h)
     band_frames = frames[:, :n // 64].cpu().numpy()     # CPU oracle sample (generated above)
     del frames
@@ -500,6 +532,7 @@ def run_ours(args):
         "pipeline_depth": D,
         "gpu_launches": 4 * K,
         "rebuild": rebuild,
+        "catch_up": catchup,
         "sparse_row": sparse,
         "e2e": e2e,
         "cpu_baseline": cpu,

@@ -173,6 +173,51 @@ SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
  */
 SDMD_API int sdmd_push_batch(sdmd_t h, int32_t k, const void *X, int64_t ld, void *stream);
 
+/*
+ * sdmd_push_many -- append one snapshot to each of `count` distinct handles
+ * (1 <= count <= SDMD_MAX_BATCH; dense handles of any n, window and element
+ * type, one device) with all their Gram rows in one kernel launch: the
+ * batching of many streams. xs[i] is handle hs[i]'s snapshot (host or device
+ * memory). Each handle's G equals, bit for bit, what sdmd_push gives (same
+ * chunking, per-lane sums and reduction order). All handles must be used on
+ * `stream`.
+ */
+#define SDMD_MAX_BATCH 64
+SDMD_API int sdmd_push_many(const sdmd_t *hs, const void *const *xs, int32_t count, void *stream);
+
+/*
+ * Serving many streams on one GPU (the library's request loop). A server
+ * admits streams by device-memory footprint (ring, G, workspaces and a queue
+ * of 4 frames): sdmd_server_open admits a stream at once if it fits within
+ * the budget after every stream waiting before it, else it waits in arrival
+ * order and is admitted when sdmd_server_close frees memory. sdmd_server_submit
+ * queues a frame (copied, host or device source; SDMD_ERR_NOT_READY when the
+ * stream is not active or its queue is full). sdmd_server_tick pushes the
+ * oldest queued frame of every active stream with one sdmd_push_many launch
+ * per 64 streams, waits for it, and records each frame's latency (tick
+ * completion minus arrival: the host clock at submit, or `arrival_ms` when
+ * >= 0, in the same steady millisecond clock). Every stream's G is bit-identical
+ * to pushing its frames alone. One host thread drives a server; its GPU work
+ * runs on its own stream (sdmd_server_stream), which the caller uses for
+ * sdmd_modes and the other calls on served handles (sdmd_server_handle).
+ */
+typedef struct sdmd_server_s *sdmd_server_t;
+enum { SDMD_STREAM_WAITING = 0, SDMD_STREAM_ACTIVE = 1, SDMD_STREAM_CLOSED = 2 };
+SDMD_API int sdmd_server_create(int64_t hbm_budget, sdmd_server_t *out);
+SDMD_API int sdmd_server_destroy(sdmd_server_t s);
+SDMD_API int sdmd_server_stream(sdmd_server_t s, void **stream);
+/* SDMD_ERR_ARG if the stream alone exceeds the budget or a size is invalid */
+SDMD_API int sdmd_server_open(sdmd_server_t s, int64_t n, int32_t m, int32_t dtype, int32_t *sid);
+/* SDMD_STREAM_* of stream `sid` */
+SDMD_API int sdmd_server_state(sdmd_server_t s, int32_t sid);
+SDMD_API int sdmd_server_handle(sdmd_server_t s, int32_t sid, sdmd_t *h);
+SDMD_API int sdmd_server_submit(sdmd_server_t s, int32_t sid, const void *x, double arrival_ms);
+SDMD_API int sdmd_server_tick(sdmd_server_t s, int32_t *frames_done);
+SDMD_API int sdmd_server_close(sdmd_server_t s, int32_t sid);
+SDMD_API int sdmd_server_stats(sdmd_server_t s, double *p50_ms, double *p99_ms, int64_t *frames);
+/* device bytes held by active streams (-1 for a NULL server) */
+SDMD_API int64_t sdmd_server_used_bytes(sdmd_server_t s);
+
 /* sdmd_count -- number of snapshots pushed so far (host pointer). Host-side
  * bookkeeping only; does not touch the device. */
 SDMD_API int sdmd_count(sdmd_t h, int64_t *count);

@@ -255,6 +255,20 @@ int sdmd::set_last_error(int code, const char* msg) {
   return code;
 }
 
+// Device bytes a depth-1 dense handle allocates (as sdmd_create does), for
+// admission by footprint; the tensor-core scratch of a first rebuild or
+// catch-up is not included.
+int64_t sdmd::handle_device_bytes(int64_t n, int32_t m, int32_t dtype, int num_sms) {
+  const int64_t elem = (dtype == SDMD_U8) ? 1 : (dtype == SDMD_C64 ? 8 : 4);
+  const int64_t gsz = (dtype == SDMD_C64) ? 16 : 8;
+  const int64_t slot = ((n * elem + kSlotAlign - 1) / kSlotAlign) * kSlotAlign;
+  int64_t chunk = 0;
+  int32_t nblk = 0;
+  gram_row_schedule(slot, num_sms, &chunk, &nblk);
+  return (int64_t)m * slot + 2 * (int64_t)m * m * gsz + (int64_t)m * nblk * gsz + 16 +
+         modes_ws_doubles(m) * (int64_t)sizeof(double) + 8 + kPhiSchedWords * 4;
+}
+
 extern "C" {
 
 const char* sdmd_last_error(void) { return g_err.c_str(); }
@@ -290,7 +304,7 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
   if (e == cudaSuccess) e = cudaMalloc(&h->G, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * h->gsz);
-  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
@@ -298,7 +312,7 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
   if (e == cudaSuccess) e = cudaMemset(h->phi_sched, 0, kPhiSchedWords * sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->ring, 0, ring_bytes);
   if (e == cudaSuccess) e = cudaMemset(h->G, 0, gbytes);
-  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->ws, 0, ws_bytes);
   if (depth > 1) {
     h->ctx.resize(depth);
@@ -356,13 +370,13 @@ int sdmd_create_sparse(int64_t n, int32_t m, int32_t nnz_max, sdmd_t* out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->G, (size_t)m * m * 16);
   if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, (size_t)m * m * 16);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)h->nblk * 16);
-  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->r_dev, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(h->tag, 0xff, (size_t)n * sizeof(int));   // tag -1: no stamp
   if (e == cudaSuccess) e = cudaMemset(h->G, 0, (size_t)m * m * 16);
-  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, 2 * sizeof(unsigned int));
+  if (e == cudaSuccess) e = cudaMemset(h->ticket, 0, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
@@ -536,6 +550,57 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   ga.status = h->status;
   TraceScope ts(h, SDMD_K_GRAM_ROW, st);
   CK(launch_gram_full_tc(ga, nullptr, st));
+  return SDMD_OK;
+}
+
+int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void* stream) {
+  if (!hs || !xs || count < 1 || count > kMaxBatchJobs)
+    return fail(SDMD_ERR_ARG, "sdmd_push_many: count=%d not in [1, %d] or NULL arrays", count, kMaxBatchJobs);
+  for (int i = 0; i < count; ++i) {
+    if (!hs[i] || !xs[i]) return fail(SDMD_ERR_ARG, "sdmd_push_many: NULL handle or snapshot %d", i);
+    if (hs[i]->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_push_many: sparse handle %d", i);
+    if (hs[i]->device != hs[0]->device) return fail(SDMD_ERR_ARG, "sdmd_push_many: handles on different devices");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) return fail(SDMD_ERR_ARG, "sdmd_push_many: handle %d appears twice", i);
+  }
+  DeviceScope ds(hs[0]->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchArgs ba;
+  ba.njobs = count;
+  ba.nitems = 0;
+  ba.grab = hs[0]->ticket + 2;
+  ba.status = hs[0]->status;
+  for (int i = 0; i < count; ++i) {
+    sdmd_s* h = hs[i];
+    wait_ring_readers(h, st);
+    const int32_t s_new = h->head;
+    {
+      TraceScope ts(h, SDMD_K_INGEST, st);
+      CK(cudaMemcpyAsync(h->ring + (int64_t)s_new * h->slot_bytes, xs[i], (size_t)(h->n * h->elem), cudaMemcpyDefault,
+                         st));
+    }
+    RowJob& J = ba.job[i];
+    J.ring = h->ring;
+    J.slot_bytes = h->slot_bytes;
+    J.chunk = h->chunk;
+    J.partials = h->partials;
+    J.ticket = h->ticket;
+    J.G = h->G;
+    J.nblk = h->nblk;
+    J.c = (int32_t)(h->count + 1 < h->m ? h->count + 1 : h->m);
+    J.s_first = (int32_t)((h->count + 1 - J.c) % h->cap);
+    J.s_new = s_new;
+    J.m = h->cap;
+    J.mode = (h->dtype == SDMD_U8) ? 0 : (h->dtype == SDMD_F32 ? 1 : 2);
+    J.item0 = ba.nitems;
+    ba.nitems += h->nblk;
+    h->head = (s_new + 1) % h->cap;
+    h->count += 1;
+  }
+  {
+    TraceScope ts(hs[0], SDMD_K_GRAM_ROW, st);
+    CK(launch_gram_rows_batched(ba, st));
+  }
   return SDMD_OK;
 }
 

@@ -367,6 +367,246 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
   }
 }
 
+// ---------------------------------------------------------------------------
+// Batched rows: one new snapshot of each of up to kMaxBatchJobs handles (mixed
+// n, window and element type) in one launch. Work items are (job, chunk)
+// pairs over the concatenated chunk lists, taken from a counter by
+// persistent CTAs. Each item is computed exactly as the single-handle kernel
+// computes that chunk (same warp-to-slot assignment, piece order and per-lane
+// sums), its partials go to the job's [slot][chunk] array, and the CTA that
+// completes a job's last chunk reduces the job's row in the same fixed order,
+// so every row is bit-identical to the handle's own sdmd_push.
+
+struct BatchSmem {
+  uint8_t stage[kGrWarps][kStages][kPiece];
+  uint8_t xs[kXSub];
+  unsigned long long bar[kGrWarps][kStages];
+  unsigned long long xbar;
+  int item, job, ch, fail, last;
+  long long acc_i[SDMD_MAX_M];
+  double acc_d[SDMD_MAX_M];
+  double acc_im[SDMD_MAX_M];
+};
+
+template <int kMode>
+__device__ __forceinline__ void piece_sums(const uint8_t* piece, const uint8_t* xq, int lane, unsigned& su, double& sd,
+                                           double& si) {
+  if constexpr (kMode == kModeU8) {
+#pragma unroll
+    for (int u = 0; u < kPiece / 512; ++u) {
+      const uint4 v = *reinterpret_cast<const uint4*>(piece + 16 * lane + 512 * u);
+      const uint4 w = *reinterpret_cast<const uint4*>(xq + 16 * lane + 512 * u);
+      su = __dp4a(v.x, w.x, su);
+      su = __dp4a(v.y, w.y, su);
+      su = __dp4a(v.z, w.z, su);
+      su = __dp4a(v.w, w.w, su);
+    }
+  } else if constexpr (kMode == kModeF32) {
+    float f0 = 0.f, f1 = 0.f, f2 = 0.f, f3 = 0.f;
+#pragma unroll
+    for (int u = 0; u < kPiece / 512; ++u) {
+      const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+      const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+      f0 = fmaf(v.x, w.x, f0);
+      f1 = fmaf(v.y, w.y, f1);
+      f2 = fmaf(v.z, w.z, f2);
+      f3 = fmaf(v.w, w.w, f3);
+    }
+    sd += (double)((f0 + f1) + (f2 + f3));
+  } else {
+    float r0 = 0.f, r1 = 0.f, i0 = 0.f, i1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < kPiece / 512; ++u) {
+      const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+      const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+      r0 = fmaf(v.x, w.x, fmaf(v.y, w.y, r0));
+      r1 = fmaf(v.z, w.z, fmaf(v.w, w.w, r1));
+      i0 = fmaf(v.x, w.y, fmaf(-v.y, w.x, i0));
+      i1 = fmaf(v.z, w.w, fmaf(-v.w, w.z, i1));
+    }
+    sd += (double)(r0 + r1);
+    si += (double)(i0 + i1);
+  }
+}
+
+// One item: chunk `ch` of job `J`; returns false if a wait expired.
+template <int kMode>
+__device__ bool batch_item(const RowJob& J, int ch, BatchSmem& sm, unsigned& g, int item_no) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t beg = (int64_t)ch * J.chunk;
+  const int len = (int)min(J.chunk, J.slot_bytes - beg);
+  const int np = len / kPiece;
+  const int nmine = (J.c > warp) ? (J.c - warp + kGrWarps - 1) / kGrWarps : 0;
+  const int nitems = nmine * np;
+  const uint8_t* xnew = J.ring + (int64_t)J.s_new * J.slot_bytes;
+  if (threadIdx.x == 0) {
+    const unsigned xb = smem_u32(&sm.xbar);
+    mbar_expect_tx(xb, (unsigned)len);
+    bulk_g2s(smem_u32(sm.xs), xnew + beg, (unsigned)len, xb);
+  }
+  auto issue = [&](int it) {
+    const unsigned s = (g + it) % kStages;
+    const int j = (J.s_first + warp + kGrWarps * (it / np)) % J.m;
+    const unsigned b = smem_u32(&sm.bar[warp][s]);
+    mbar_expect_tx(b, kPiece);
+    bulk_g2s(smem_u32(sm.stage[warp][s]), J.ring + (int64_t)j * J.slot_bytes + beg + (int64_t)kPiece * (it % np), kPiece,
+             b);
+  };
+  if (lane == 0)
+    for (int it = 0; it < kStages && it < nitems; ++it) issue(it);
+  bool failed = !mbar_wait(smem_u32(&sm.xbar), (unsigned)(item_no & 1));
+  failed = __any_sync(0xffffffffu, failed);
+  int consumed = 0;
+  unsigned su = 0;
+  double sd = 0.0, si = 0.0;
+  for (int it = 0; it < nitems && !failed; ++it) {
+    const unsigned gi = g + it, s = gi % kStages, par = (gi / kStages) & 1;
+    const int q = it % np;
+    const bool bad = !mbar_wait(smem_u32(&sm.bar[warp][s]), par);
+    if (__any_sync(0xffffffffu, bad)) {
+      failed = true;
+      break;
+    }
+    piece_sums<kMode>(sm.stage[warp][s], sm.xs + kPiece * q, lane, su, sd, si);
+    __syncwarp();
+    ++consumed;
+    if (lane == 0 && it + kStages < nitems) issue(it + kStages);
+    if (q == np - 1) {
+      const int jj = warp + kGrWarps * (it / np);
+      if constexpr (kMode == kModeU8) {
+        const long long t = warp_sum((long long)su);
+        if (lane == 0) sm.acc_i[jj] += t;
+        su = 0;
+      } else {
+        const double t = warp_sum(sd);
+        if (lane == 0) sm.acc_d[jj] += t;
+        sd = 0.0;
+        if constexpr (kMode == kModeC64) {
+          const double ti = warp_sum(si);
+          if (lane == 0) sm.acc_im[jj] += ti;
+          si = 0.0;
+        }
+      }
+    }
+  }
+  if (failed && lane == 0) {           // copies in flight land before the memory is reused
+    const int issued = nitems < consumed + kStages ? nitems : consumed + kStages;
+    for (int it = consumed; it < issued; ++it) mbar_wait(smem_u32(&sm.bar[warp][(g + it) % kStages]), ((g + it) / kStages) & 1);
+    mbar_wait(smem_u32(&sm.xbar), (unsigned)(item_no & 1));
+  }
+  g += nitems;
+  return !failed;
+}
+
+template <typename Acc>
+__device__ void batch_finish(const RowJob& J) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Acc* P = static_cast<const Acc*>(J.partials);
+  Acc* G = static_cast<Acc*>(J.G);
+  for (int jj = warp; jj < J.c; jj += kGrWarps) {
+    Acc s = 0;
+    for (int b = lane; b < J.nblk; b += 32) s += __ldcg(P + (int64_t)jj * J.nblk + b);
+    s = warp_sum(s);
+    if (lane == 0) {
+      const int j = (J.s_first + jj) % J.m;
+      G[(int64_t)J.s_new * J.m + j] = s;
+      G[(int64_t)j * J.m + J.s_new] = s;
+    }
+  }
+}
+
+__device__ void batch_finish_c64(const RowJob& J) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const double2* P = static_cast<const double2*>(J.partials);
+  double2* G = static_cast<double2*>(J.G);
+  for (int jj = warp; jj < J.c; jj += kGrWarps) {
+    double sr = 0.0, si = 0.0;
+    for (int b = lane; b < J.nblk; b += 32) {
+      const double2 v = __ldcg(P + (int64_t)jj * J.nblk + b);
+      sr += v.x;
+      si += v.y;
+    }
+    sr = warp_sum(sr);
+    si = warp_sum(si);
+    if (lane == 0) {
+      const int j = (J.s_first + jj) % J.m;
+      if (j == J.s_new) si = 0.0;
+      G[(int64_t)j * J.m + J.s_new] = make_double2(sr, si);
+      G[(int64_t)J.s_new * J.m + j] = make_double2(sr, -si);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kGrThreads, 1) gram_rows_batched_kernel(const __grid_constant__ BatchArgs a) {
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  BatchSmem& sm = *reinterpret_cast<BatchSmem*>(smem_raw);
+  for (int j = threadIdx.x; j < SDMD_MAX_M; j += blockDim.x) {
+    sm.acc_i[j] = 0;
+    sm.acc_d[j] = 0.0;
+    sm.acc_im[j] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < kGrWarps; ++w)
+      for (int s = 0; s < kStages; ++s) mbar_init(smem_u32(&sm.bar[w][s]), 1);
+    mbar_init(smem_u32(&sm.xbar), 1);
+    sm.fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  unsigned g = 0;                      // this warp's pieces so far (ring position)
+  for (int item_no = 0;; ++item_no) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int it = sm.fail ? a.nitems : (int)atomicAdd(a.grab, 1u);
+      int jb = 0;
+      if (it < a.nitems)
+        while (jb + 1 < a.njobs && a.job[jb + 1].item0 <= it) ++jb;
+      sm.item = it;
+      sm.job = jb;
+      sm.ch = it - a.job[jb].item0;
+    }
+    __syncthreads();
+    if (sm.item >= a.nitems) break;
+    const RowJob& J = a.job[sm.job];
+    const int ch = sm.ch;
+    bool ok;
+    if (J.mode == kModeU8) ok = batch_item<kModeU8>(J, ch, sm, g, item_no);
+    else if (J.mode == kModeF32) ok = batch_item<kModeF32>(J, ch, sm, g, item_no);
+    else ok = batch_item<kModeC64>(J, ch, sm, g, item_no);
+    if (!ok && (threadIdx.x & 31) == 0) {
+      atomicOr(a.status, kDevTimeout);
+      sm.fail = 1;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < J.c; j += blockDim.x) {
+      if (J.mode == kModeU8) static_cast<long long*>(J.partials)[(int64_t)j * J.nblk + ch] = sm.acc_i[j];
+      else if (J.mode == kModeF32) static_cast<double*>(J.partials)[(int64_t)j * J.nblk + ch] = sm.acc_d[j];
+      else static_cast<double2*>(J.partials)[(int64_t)j * J.nblk + ch] = make_double2(sm.acc_d[j], sm.acc_im[j]);
+      sm.acc_i[j] = 0;
+      sm.acc_d[j] = 0.0;
+      sm.acc_im[j] = 0.0;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sm.last = (atomicAdd(J.ticket, 1u) == (unsigned)J.nblk - 1u);
+    __syncthreads();
+    if (sm.last) {                     // this job's chunks are all in: reduce its row
+      __threadfence();
+      if (J.mode == kModeU8) batch_finish<long long>(J);
+      else if (J.mode == kModeF32) batch_finish<double>(J);
+      else batch_finish_c64(J);
+      if (threadIdx.x == 0) J.ticket[0] = 0u;
+    }
+  }
+  // the last CTA out zeroes the batch counters for the next launch
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.grab + 1, 1u) == gridDim.x - 1u) {
+      a.grab[0] = 0u;
+      a.grab[1] = 0u;
+    }
+  }
+}
+
 }  // namespace
 
 // Two chunks per SM: persistent CTAs take chunks as they free
@@ -407,6 +647,23 @@ cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
     gram_row_bulk_kernel<kModeC64><<<ctas, kGrThreads, smem, st>>>(a);
   else
     gram_row_bulk_kernel<kModeF32><<<ctas, kGrThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st) {
+  static bool attr = false;
+  const size_t smem = sizeof(BatchSmem);
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gram_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = a.nitems < sms ? a.nitems : (sms > 0 ? sms : 1);
+  gram_rows_batched_kernel<<<ctas, kGrThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

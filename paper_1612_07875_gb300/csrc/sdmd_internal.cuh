@@ -57,6 +57,31 @@ constexpr int kGramFullMaxCtas = 160;
 // Launches the two kernels on `st`; cudaErrorNotSupported outside c <= 127.
 cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream_t st);
 
+// One snapshot's Gram row inside a batched launch (fields as in GramRowArgs).
+struct RowJob {
+  const uint8_t* ring;
+  int64_t slot_bytes;
+  int64_t chunk;
+  void* partials;
+  unsigned int* ticket;  // chunks finished (word 0), zero between launches
+  void* G;
+  int32_t nblk, c, s_first, s_new, m;
+  int32_t mode;          // 0 uint8, 1 float32, 2 complex64
+  int32_t item0;         // first work item of this job in the batch
+};
+constexpr int kMaxBatchJobs = 64;
+struct BatchArgs {
+  RowJob job[kMaxBatchJobs];
+  int32_t njobs;
+  int32_t nitems;        // sum of the jobs' chunk counts
+  unsigned int* grab;    // two words, zero between launches: items taken, CTAs finished
+  int* status;           // status word of the first handle
+};
+cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st);
+
+// Device bytes of a depth-1 dense handle (admission by footprint).
+int64_t handle_device_bytes(int64_t n, int32_t m, int32_t dtype, int num_sms);
+
 // Gram row for one pushed snapshot; launches one kernel on `st`.
 cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st);
 

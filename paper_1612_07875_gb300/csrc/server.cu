@@ -1,0 +1,239 @@
+// Serving many streams on one GPU: admission by device-memory footprint,
+// per-stream frame queues on the device, and ticks that take the oldest
+// queued frame of every active stream and push them all with one batched
+// Gram-row launch (sdmd_push_many). Streams that do not fit wait in arrival
+// order and are admitted as memory is released (sdmd_server_close). Each
+// stream's G is bit-identical to pushing its frames alone (the batched
+// kernel keeps every handle's chunking and reduction order). Latency of a
+// frame = completion of its tick minus its arrival (host clock, or the time
+// given at submit); p50 / p99 over all completed frames.
+//
+// A server is driven by one host thread; all its GPU work runs on its own
+// stream (sdmd_server_stream).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <deque>
+#include <new>
+#include <vector>
+
+#include "sdmd.h"
+#include "sdmd_internal.cuh"
+
+namespace {
+
+constexpr int kQueue = 4;            // frames queued per stream
+
+struct ServedStream {
+  int state = 0;                     // SDMD_STREAM_*
+  int64_t n = 0;
+  int32_t m = 0, dtype = 0;
+  int64_t footprint = 0;
+  sdmd_t h = nullptr;
+  uint8_t* fifo = nullptr;           // kQueue frames
+  int64_t frame_bytes = 0;
+  int head = 0, len = 0;
+  double arrival[kQueue] = {};
+};
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+int err(int code, const char* msg) { return sdmd::set_last_error(code, msg); }
+
+}  // namespace
+
+struct sdmd_server_s {
+  int device = 0;
+  int num_sms = 1;
+  int64_t budget = 0, used = 0;
+  cudaStream_t st = nullptr;
+  std::vector<ServedStream> streams;
+  std::deque<int32_t> waiting;
+  std::vector<double> lat;
+  int64_t frames = 0;
+};
+
+namespace {
+
+int activate(sdmd_server_s* s, int32_t sid) {
+  ServedStream& q = s->streams[sid];
+  int rc = sdmd_create(q.n, q.m, q.dtype, &q.h);
+  if (rc != SDMD_OK) return rc;
+  q.frame_bytes = q.n * ((q.dtype == SDMD_U8) ? 1 : (q.dtype == SDMD_C64 ? 8 : 4));
+  if (cudaMalloc(&q.fifo, (size_t)kQueue * (size_t)q.frame_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    sdmd_destroy(q.h);
+    q.h = nullptr;
+    return err(SDMD_ERR_OOM, "sdmd_server: frame queue allocation failed");
+  }
+  q.state = SDMD_STREAM_ACTIVE;
+  s->used += q.footprint;
+  return SDMD_OK;
+}
+
+// Admit waiting streams, in arrival order, while the head of the line fits.
+int admit_waiting(sdmd_server_s* s) {
+  while (!s->waiting.empty()) {
+    const int32_t sid = s->waiting.front();
+    if (s->used + s->streams[sid].footprint > s->budget) break;
+    s->waiting.pop_front();
+    const int rc = activate(s, sid);
+    if (rc != SDMD_OK) return rc;
+  }
+  return SDMD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sdmd_server_create(int64_t hbm_budget, sdmd_server_t* out) {
+  if (!out || hbm_budget <= 0) return err(SDMD_ERR_ARG, "sdmd_server_create: bad argument");
+  sdmd_server_s* s = new (std::nothrow) sdmd_server_s();
+  if (!s) return err(SDMD_ERR_OOM, "sdmd_server_create: host allocation failed");
+  cudaGetDevice(&s->device);
+  cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device);
+  s->budget = hbm_budget;
+  if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete s;
+    return err(SDMD_ERR_CUDA, "sdmd_server_create: stream creation failed");
+  }
+  *out = s;
+  return SDMD_OK;
+}
+
+int sdmd_server_destroy(sdmd_server_t s) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_destroy: NULL server");
+  cudaStreamSynchronize(s->st);
+  for (ServedStream& q : s->streams) {
+    if (q.h) sdmd_destroy(q.h);
+    cudaFree(q.fifo);
+  }
+  cudaStreamDestroy(s->st);
+  delete s;
+  return SDMD_OK;
+}
+
+int sdmd_server_stream(sdmd_server_t s, void** stream) {
+  if (!s || !stream) return err(SDMD_ERR_ARG, "sdmd_server_stream: bad argument");
+  *stream = s->st;
+  return SDMD_OK;
+}
+
+int sdmd_server_open(sdmd_server_t s, int64_t n, int32_t m, int32_t dtype, int32_t* sid) {
+  if (!s || !sid) return err(SDMD_ERR_ARG, "sdmd_server_open: bad argument");
+  if (dtype != SDMD_U8 && dtype != SDMD_F32 && dtype != SDMD_C64)
+    return err(SDMD_ERR_ARG, "sdmd_server_open: dense dtypes only");
+  if (n < 1 || m < 2 || m > SDMD_MAX_M) return err(SDMD_ERR_ARG, "sdmd_server_open: n or m out of range");
+  ServedStream q;
+  q.n = n;
+  q.m = m;
+  q.dtype = dtype;
+  const int64_t elem = (dtype == SDMD_U8) ? 1 : (dtype == SDMD_C64 ? 8 : 4);
+  q.footprint = sdmd::handle_device_bytes(n, m, dtype, s->num_sms) + kQueue * n * elem;
+  if (q.footprint > s->budget) return err(SDMD_ERR_ARG, "sdmd_server_open: the stream alone exceeds the budget");
+  s->streams.push_back(q);
+  *sid = (int32_t)s->streams.size() - 1;
+  s->waiting.push_back(*sid);
+  return admit_waiting(s);
+}
+
+int sdmd_server_state(sdmd_server_t s, int32_t sid) {
+  if (!s || sid < 0 || sid >= (int32_t)s->streams.size()) return err(SDMD_ERR_ARG, "sdmd_server_state: bad stream");
+  return s->streams[sid].state;
+}
+
+int sdmd_server_handle(sdmd_server_t s, int32_t sid, sdmd_t* h) {
+  if (!s || !h || sid < 0 || sid >= (int32_t)s->streams.size()) return err(SDMD_ERR_ARG, "sdmd_server_handle: bad stream");
+  if (s->streams[sid].state != SDMD_STREAM_ACTIVE) return err(SDMD_ERR_NOT_READY, "sdmd_server_handle: stream not active");
+  *h = s->streams[sid].h;
+  return SDMD_OK;
+}
+
+int sdmd_server_submit(sdmd_server_t s, int32_t sid, const void* x, double arrival_ms) {
+  if (!s || !x || sid < 0 || sid >= (int32_t)s->streams.size()) return err(SDMD_ERR_ARG, "sdmd_server_submit: bad argument");
+  ServedStream& q = s->streams[sid];
+  if (q.state != SDMD_STREAM_ACTIVE) return err(SDMD_ERR_NOT_READY, "sdmd_server_submit: stream not active");
+  if (q.len == kQueue) return err(SDMD_ERR_NOT_READY, "sdmd_server_submit: frame queue full");
+  const int slot = (q.head + q.len) % kQueue;
+  if (cudaMemcpyAsync(q.fifo + (int64_t)slot * q.frame_bytes, x, (size_t)q.frame_bytes, cudaMemcpyDefault, s->st) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return err(SDMD_ERR_CUDA, "sdmd_server_submit: copy failed");
+  }
+  q.arrival[slot] = arrival_ms >= 0.0 ? arrival_ms : now_ms();
+  q.len += 1;
+  return SDMD_OK;
+}
+
+int sdmd_server_tick(sdmd_server_t s, int32_t* frames_done) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_tick: NULL server");
+  std::vector<int32_t> ids;
+  for (int32_t i = 0; i < (int32_t)s->streams.size(); ++i)
+    if (s->streams[i].state == SDMD_STREAM_ACTIVE && s->streams[i].len > 0) ids.push_back(i);
+  for (size_t b = 0; b < ids.size(); b += SDMD_MAX_BATCH) {
+    const size_t e = std::min(ids.size(), b + (size_t)SDMD_MAX_BATCH);
+    std::vector<sdmd_t> hs;
+    std::vector<const void*> xs;
+    for (size_t i = b; i < e; ++i) {
+      ServedStream& q = s->streams[ids[i]];
+      hs.push_back(q.h);
+      xs.push_back(q.fifo + (int64_t)q.head * q.frame_bytes);
+    }
+    const int rc = sdmd_push_many(hs.data(), xs.data(), (int32_t)hs.size(), s->st);
+    if (rc != SDMD_OK) return rc;
+  }
+  if (cudaStreamSynchronize(s->st) != cudaSuccess) {
+    cudaGetLastError();
+    return err(SDMD_ERR_CUDA, "sdmd_server_tick: stream synchronisation failed");
+  }
+  const double t = now_ms();
+  for (int32_t sid : ids) {
+    ServedStream& q = s->streams[sid];
+    s->lat.push_back(t - q.arrival[q.head]);
+    q.head = (q.head + 1) % kQueue;
+    q.len -= 1;
+  }
+  s->frames += (int64_t)ids.size();
+  if (frames_done) *frames_done = (int32_t)ids.size();
+  return SDMD_OK;
+}
+
+int sdmd_server_close(sdmd_server_t s, int32_t sid) {
+  if (!s || sid < 0 || sid >= (int32_t)s->streams.size()) return err(SDMD_ERR_ARG, "sdmd_server_close: bad stream");
+  ServedStream& q = s->streams[sid];
+  if (q.state == SDMD_STREAM_WAITING) {
+    s->waiting.erase(std::find(s->waiting.begin(), s->waiting.end(), sid));
+  } else if (q.state == SDMD_STREAM_ACTIVE) {
+    cudaStreamSynchronize(s->st);
+    sdmd_destroy(q.h);
+    q.h = nullptr;
+    cudaFree(q.fifo);
+    q.fifo = nullptr;
+    s->used -= q.footprint;
+  }
+  q.state = SDMD_STREAM_CLOSED;
+  return admit_waiting(s);
+}
+
+int sdmd_server_stats(sdmd_server_t s, double* p50_ms, double* p99_ms, int64_t* frames) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_stats: NULL server");
+  std::vector<double> v = s->lat;
+  std::sort(v.begin(), v.end());
+  auto pct = [&](double p) { return v.empty() ? 0.0 : v[(size_t)std::min<double>(v.size() - 1, p * (v.size() - 1) + 0.5)]; };
+  if (p50_ms) *p50_ms = pct(0.50);
+  if (p99_ms) *p99_ms = pct(0.99);
+  if (frames) *frames = s->frames;
+  return SDMD_OK;
+}
+
+int64_t sdmd_server_used_bytes(sdmd_server_t s) { return s ? s->used : -1; }
+
+}  // extern "C"

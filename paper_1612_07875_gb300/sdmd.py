@@ -74,6 +74,18 @@ _SIGNATURES = {
     "sdmd_modes_phase_cycles": [_VP, ctypes.POINTER(_I64), _I32, _VP],
     "sdmd_amplitudes": [_VP, _VP, ctypes.POINTER(_I32), _VP],
     "sdmd_push_batch": [_VP, _I32, _VP, _I64, _VP],
+    "sdmd_push_many": [ctypes.POINTER(_VP), ctypes.POINTER(_VP), _I32, _VP],
+    "sdmd_server_create": [_I64, ctypes.POINTER(_VP)],
+    "sdmd_server_destroy": [_VP],
+    "sdmd_server_stream": [_VP, ctypes.POINTER(_VP)],
+    "sdmd_server_open": [_VP, _I64, _I32, _I32, ctypes.POINTER(_I32)],
+    "sdmd_server_state": [_VP, _I32],
+    "sdmd_server_handle": [_VP, _I32, ctypes.POINTER(_VP)],
+    "sdmd_server_submit": [_VP, _I32, _VP, ctypes.c_double],
+    "sdmd_server_tick": [_VP, ctypes.POINTER(_I32)],
+    "sdmd_server_close": [_VP, _I32],
+    "sdmd_server_stats": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
+    "sdmd_server_used_bytes": [_VP],
     "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
 }
 
@@ -99,6 +111,7 @@ def lib():
                 fn.restype = ctypes.c_int
             L.sdmd_last_error.argtypes = []
             L.sdmd_last_error.restype = ctypes.c_char_p
+            L.sdmd_server_used_bytes.restype = ctypes.c_int64
             _lib = L
     return _lib
 
@@ -200,6 +213,82 @@ def sdmd_svd(h, r, sigma, V, stream=None):
 def sdmd_push_batch(h, k, X, ld, stream=None):
     """Append k snapshots (snapshot j at X + j * ld elements)."""
     _check(lib().sdmd_push_batch(h, int(k), ptr(X), int(ld), stream_handle(stream)), "sdmd_push_batch")
+
+
+SDMD_MAX_BATCH = 64
+
+
+def sdmd_push_many(hs, xs, stream=None):
+    """One snapshot per handle, all Gram rows in one launch."""
+    k = len(hs)
+    harr = (_VP * k)(*hs)
+    xarr = (_VP * k)(*[ptr(x) for x in xs])
+    _check(lib().sdmd_push_many(harr, xarr, k, stream_handle(stream)), "sdmd_push_many")
+
+
+SDMD_STREAM_WAITING = 0
+SDMD_STREAM_ACTIVE = 1
+SDMD_STREAM_CLOSED = 2
+
+
+def sdmd_server_create(hbm_budget):
+    s = _VP()
+    _check(lib().sdmd_server_create(int(hbm_budget), ctypes.byref(s)), "sdmd_server_create")
+    return s.value
+
+
+def sdmd_server_destroy(s):
+    _check(lib().sdmd_server_destroy(s), "sdmd_server_destroy")
+
+
+def sdmd_server_stream(s):
+    st = _VP()
+    _check(lib().sdmd_server_stream(s, ctypes.byref(st)), "sdmd_server_stream")
+    return st.value
+
+
+def sdmd_server_open(s, n, m, dtype):
+    sid = _I32()
+    _check(lib().sdmd_server_open(s, int(n), int(m), int(dtype), ctypes.byref(sid)), "sdmd_server_open")
+    return sid.value
+
+
+def sdmd_server_state(s, sid):
+    rc = lib().sdmd_server_state(s, int(sid))
+    if rc < 0:
+        _check(rc, "sdmd_server_state")
+    return rc
+
+
+def sdmd_server_handle(s, sid):
+    h = _VP()
+    _check(lib().sdmd_server_handle(s, int(sid), ctypes.byref(h)), "sdmd_server_handle")
+    return h.value
+
+
+def sdmd_server_submit(s, sid, x, arrival_ms=-1.0):
+    _check(lib().sdmd_server_submit(s, int(sid), ptr(x), float(arrival_ms)), "sdmd_server_submit")
+
+
+def sdmd_server_tick(s):
+    n = _I32()
+    _check(lib().sdmd_server_tick(s, ctypes.byref(n)), "sdmd_server_tick")
+    return n.value
+
+
+def sdmd_server_close(s, sid):
+    _check(lib().sdmd_server_close(s, int(sid)), "sdmd_server_close")
+
+
+def sdmd_server_stats(s):
+    """(p50_ms, p99_ms, frames)"""
+    p50, p99, fr = ctypes.c_double(), ctypes.c_double(), _I64()
+    _check(lib().sdmd_server_stats(s, ctypes.byref(p50), ctypes.byref(p99), ctypes.byref(fr)), "sdmd_server_stats")
+    return p50.value, p99.value, fr.value
+
+
+def sdmd_server_used_bytes(s):
+    return lib().sdmd_server_used_bytes(s)
 
 
 def sdmd_amplitudes(h, b, stream=None, want_index=True):

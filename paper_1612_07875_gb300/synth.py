@@ -240,6 +240,14 @@ class ConditionedStream:
             x += a[k] * self._basis(k, lo, hi)
         return (x * np.sqrt(self.n)).astype(np.float32)
 
+    def snapshots(self, ts):
+        """Snapshots for the times `ts` as a len(ts) x n float32 array: the
+        same construction as `snapshot`, with the K basis fields built once
+        and combined by one matrix product (faster for many snapshots)."""
+        B = np.stack([self._basis(k, 0, self.n) for k in range(self.K)])     # K x n
+        A = np.stack([self.coeffs(t) * self.s for t in ts])                  # T x K
+        return ((A @ B) * np.sqrt(self.n)).astype(np.float32)
+
 
 def random_dense(n, seed, dtype=np.float32):
     """i.i.d. test vector: N(0,1) floats or uniform 0..255 bytes."""
