@@ -13,6 +13,13 @@ per-frame latency percentiles, an end-to-end figure through the C ABI with
 pinned host buffers, the CPU oracle timed on a bounded sample, and the SM
 clocks sampled during the timed region.
 
+Secondary measurements in the same line: each kernel launched alone, the
+full-window rebuild (tensor cores vs row passes), the 8-frame catch-up, the
+Fourier-sparse Gram row, and batched serving of 64 mixed FP32/uint8 streams
+with Poisson arrivals (aggregate snapshots/s, p50/p99 frame latency, and the
+closed-loop capacity of one batched launch per tick against one push per
+stream).
+
 `--impl reference` times the CPU oracle alone (the reference arm).
 Multi-GPU (torchrun): every rank streams its own independent video (weak
 scaling, no data-path collective).
@@ -50,6 +57,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the rebuild and Fourier-sparse measurements")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the served Poisson-arrival run (0 skips the serving measurement)")
     return ap.parse_args()
 
 
@@ -84,8 +93,10 @@ def oracle_rate(band_frames, n_total, seconds):
         so.push(band_frames[t])
     steps = 0
     t0 = time.perf_counter()
-    for t in range(M_WIN, T):
-        so.push(band_frames[t])
+    # the frames after the first window are streamed in a loop until the
+    # sample's time is up (the oracle's cost does not depend on the values)
+    while True:
+        so.push(band_frames[M_WIN + steps % (T - M_WIN)])
         so.modes(R_MODES)
         steps += 1
         if time.perf_counter() - t0 >= seconds:
@@ -356,6 +367,146 @@ def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
             "bound": "latency / L2 (lookup table 12 MB and window 8 MB are L2-resident)"}
 
 
+def measure_serving(S, synth, dev, seconds, capacity_ticks=12):
+    """Batched serving of 64 concurrent streams (FP32 and uint8 mixed, n
+    log-uniform in [2^16, 2^22], m in {16..256}, Poisson arrivals at 10-120 Hz
+    each): windows filled first (untimed), then `seconds` of real-time
+    arrivals submitted from pinned host memory as they fall due; each tick
+    pushes every stream's oldest queued frame in one batched launch. Latency
+    of a frame = its tick's completion minus its scheduled arrival. Then the
+    closed-loop capacity: every stream pushes one device-resident frame per
+    tick, batched (sdmd_push_many) against the same frames pushed one handle
+    at a time (sdmd_push), both timed with CUDA events."""
+    import torch
+    from collections import deque
+    mix = synth.ServingMix()
+    specs = mix.specs
+    DT = {"u8": S.SDMD_U8, "f32": S.SDMD_F32}
+    EL = {"u8": 1, "f32": 4}
+    pu8, pf32 = mix.pools()
+    host = {"u8": torch.from_numpy(pu8).pin_memory(), "f32": torch.from_numpy(pf32).pin_memory()}
+    devp = {k: v.to(dev) for k, v in host.items()}
+    hbase = {k: v.data_ptr() for k, v in host.items()}
+    dbase = {k: v.data_ptr() for k, v in devp.items()}
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.8)
+    srv = S.sdmd_server_create(budget)
+    st = S.sdmd_server_stream(srv)
+    ns = len(specs)
+    try:
+        sids = [S.sdmd_server_open(srv, n, m, DT[k]) for k, n, m, _ in specs]
+        active = sum(S.sdmd_server_state(srv, s) == S.SDMD_STREAM_ACTIVE for s in sids)
+        fcount = [0] * ns
+
+        def haddr(i):
+            k, n, _, _ = specs[i]
+            a = hbase[k] + EL[k] * mix.offset(i, fcount[i])
+            fcount[i] += 1
+            return a
+
+        # warm-up: every window filled
+        for j in range(max(s[2] for s in specs)):
+            for i in range(ns):
+                if j < specs[i][2]:
+                    S.sdmd_server_submit(srv, sids[i], haddr(i))
+            S.sdmd_server_tick(srv)
+        arr = mix.arrivals(seconds)
+        ev_t = np.concatenate(arr) * 1e3
+        ev_s = np.concatenate([np.full(len(a), i) for i, a in enumerate(arr)])
+        order = np.argsort(ev_t, kind="stable")
+        ev_t, ev_s = ev_t[order].tolist(), ev_s[order].tolist()
+        backlog = [deque() for _ in range(ns)]
+        qlen = [0] * ns
+        gram_bytes = 0
+        ticks = 0
+        nxt, nev = 0, len(ev_t)
+        clocks = ClockSampler(torch.cuda.current_device())
+        clocks.start()
+        time.sleep(0.2)
+        S.sdmd_server_reset_stats(srv)
+        T0 = S.sdmd_server_clock_ms()
+        while True:
+            now = S.sdmd_server_clock_ms() - T0
+            while nxt < nev and ev_t[nxt] <= now:
+                backlog[ev_s[nxt]].append(ev_t[nxt] + T0)
+                nxt += 1
+            queued = False
+            for i in range(ns):
+                b = backlog[i]
+                while b and qlen[i] < 4:
+                    S.sdmd_server_submit(srv, sids[i], haddr(i), b.popleft())
+                    qlen[i] += 1
+                if qlen[i]:
+                    queued = True
+            if queued:
+                S.sdmd_server_tick(srv)
+                ticks += 1
+                for i in range(ns):
+                    if qlen[i]:
+                        qlen[i] -= 1
+                        k, n, m, _ = specs[i]
+                        gram_bytes += m * n * EL[k]
+            elif nxt >= nev:
+                break
+            else:
+                wait = (ev_t[nxt] - now) * 1e-3
+                if wait > 0.0005:
+                    time.sleep(wait - 0.0003)
+        wall = (S.sdmd_server_clock_ms() - T0) * 1e-3
+        clk = clocks.stop()
+        p50, p99, frames = S.sdmd_server_stats(srv)
+        served = {"streams": ns, "active": active, "seconds": seconds, "offered_hz": sum(s[3] for s in specs),
+                  "frames": frames, "snapshots_per_s": frames / wall, "ticks": ticks,
+                  "frames_per_tick": frames / max(ticks, 1),
+                  "gram_GB/s": gram_bytes / wall / 1e9,
+                  "latency_ms": {"p50": p50, "p99": p99,
+                                 "definition": "tick completion (host) minus the frame's scheduled arrival"},
+                  "hbm_footprint_GB": S.sdmd_server_used_bytes(srv) / 1e9, "budget_GB": budget / 1e9,
+                  "clocks": clk}
+
+        # closed-loop capacity, device-resident frames
+        hs = [S.sdmd_server_handle(srv, s) for s in sids]
+
+        def daddr(i):
+            k, n, _, _ = specs[i]
+            a = dbase[k] + EL[k] * mix.offset(i, fcount[i])
+            fcount[i] += 1
+            return a
+        tick_bytes = sum(m * n * EL[k] for k, n, m, _ in specs)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sobj = torch.cuda.ExternalStream(st)
+        out = {}
+        for mode in ("single", "batched", "single", "batched"):
+            for rep in range(2):                      # untimed pass, then timed
+                xs = [[daddr(i) for i in range(ns)] for _ in range(capacity_ticks)]
+                torch.cuda.synchronize()
+                e0.record(sobj)
+                for t in range(capacity_ticks):
+                    if mode == "batched":
+                        S.sdmd_push_many(hs, xs[t], st)
+                    else:
+                        for i in range(ns):
+                            S.sdmd_push(hs[i], xs[t][i], st)
+                e1.record(sobj)
+                torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            out[mode] = max(out.get(mode, 0.0), ns * capacity_ticks / (ms * 1e-3))
+        for h in hs:
+            if S.sdmd_status(h, st) != S.SDMD_OK:
+                raise RuntimeError("served stream status: " + S.sdmd_last_error())
+        served["capacity"] = {"batched_snapshots_per_s": out["batched"], "single_snapshots_per_s": out["single"],
+                              "batched_gram_GB/s": out["batched"] / ns * tick_bytes / 1e9,
+                              "ticks": capacity_ticks,
+                              "note": "every stream pushes one frame per tick, windows full; batched = one "
+                                      "sdmd_push_many launch per tick, single = one sdmd_push per stream"}
+        return served
+    finally:
+        S.sdmd_server_destroy(srv)
+        del devp
+        torch.cuda.empty_cache()
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -496,6 +647,11 @@ def run_ours(args):
     if not args.no_secondary:
         sparse = measure_sparse(S, synth, dev, stream)
 
+    # ---- batched serving of 64 mixed streams (Poisson arrivals)
+    serving = None
+    if not args.no_secondary and args.serve_seconds > 0:
+        serving = measure_serving(S, synth, dev, args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, info = oracle_rate(band_frames, n, args.cpu_sample_seconds)
@@ -534,6 +690,7 @@ def run_ours(args):
         "rebuild": rebuild,
         "catch_up": catchup,
         "sparse_row": sparse,
+        "serving": serving,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,

@@ -217,6 +217,11 @@ SDMD_API int sdmd_server_close(sdmd_server_t s, int32_t sid);
 SDMD_API int sdmd_server_stats(sdmd_server_t s, double *p50_ms, double *p99_ms, int64_t *frames);
 /* device bytes held by active streams (-1 for a NULL server) */
 SDMD_API int64_t sdmd_server_used_bytes(sdmd_server_t s);
+/* forget the latencies and frame count gathered so far (e.g. after warm-up) */
+SDMD_API int sdmd_server_reset_stats(sdmd_server_t s);
+/* the clock that arrival_ms and the latencies use: milliseconds of a
+ * monotonic host clock (arbitrary origin, shared by all servers) */
+SDMD_API double sdmd_server_clock_ms(void);
 
 /* sdmd_count -- number of snapshots pushed so far (host pointer). Host-side
  * bookkeeping only; does not touch the device. */

@@ -236,4 +236,13 @@ int sdmd_server_stats(sdmd_server_t s, double* p50_ms, double* p99_ms, int64_t* 
 
 int64_t sdmd_server_used_bytes(sdmd_server_t s) { return s ? s->used : -1; }
 
+int sdmd_server_reset_stats(sdmd_server_t s) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_reset_stats: NULL server");
+  s->lat.clear();
+  s->frames = 0;
+  return SDMD_OK;
+}
+
+double sdmd_server_clock_ms(void) { return now_ms(); }
+
 }  // extern "C"

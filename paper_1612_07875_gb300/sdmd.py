@@ -86,6 +86,8 @@ _SIGNATURES = {
     "sdmd_server_close": [_VP, _I32],
     "sdmd_server_stats": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
     "sdmd_server_used_bytes": [_VP],
+    "sdmd_server_reset_stats": [_VP],
+    "sdmd_server_clock_ms": [],
     "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
 }
 
@@ -112,6 +114,7 @@ def lib():
             L.sdmd_last_error.argtypes = []
             L.sdmd_last_error.restype = ctypes.c_char_p
             L.sdmd_server_used_bytes.restype = ctypes.c_int64
+            L.sdmd_server_clock_ms.restype = ctypes.c_double
             _lib = L
     return _lib
 
@@ -289,6 +292,14 @@ def sdmd_server_stats(s):
 
 def sdmd_server_used_bytes(s):
     return lib().sdmd_server_used_bytes(s)
+
+
+def sdmd_server_reset_stats(s):
+    _check(lib().sdmd_server_reset_stats(s), "sdmd_server_reset_stats")
+
+
+def sdmd_server_clock_ms():
+    return lib().sdmd_server_clock_ms()
 
 
 def sdmd_amplitudes(h, b, stream=None, want_index=True):

@@ -255,3 +255,45 @@ def random_dense(n, seed, dtype=np.float32):
     if dtype == np.uint8:
         return rng.integers(0, 256, n, dtype=np.uint8)
     return rng.standard_normal(n).astype(dtype)
+
+
+class ServingMix:
+    """Many concurrent streams for serving: per stream an element type (FP32
+    or uint8, equally likely), n log-uniform in [2^lo, 2^hi], a window m drawn
+    from `windows`, and Poisson frame arrivals at a rate uniform in
+    [hz_lo, hz_hi]. Frame contents are windows of one seeded random pool per
+    element type (the Gram row's cost does not depend on them)."""
+
+    def __init__(self, streams=64, lo=16, hi=22, windows=(16, 32, 64, 128, 256), hz_lo=10.0, hz_hi=120.0,
+                 seed=config_seed(5)):
+        rng = np.random.default_rng(seed)
+        self.seed = seed
+        self.specs = []
+        for _ in range(streams):
+            kind = "u8" if rng.random() < 0.5 else "f32"
+            n = int(round(2.0 ** rng.uniform(lo, hi)))
+            m = int(rng.choice(windows))
+            hz = float(rng.uniform(hz_lo, hz_hi))
+            self.specs.append((kind, n, m, hz))
+        self.pool_len = (1 << hi) + (1 << 16)
+
+    def arrivals(self, seconds):
+        """Per stream, sorted arrival times in seconds within [0, seconds)."""
+        rng = np.random.default_rng(self.seed + 1)
+        out = []
+        for _, _, _, hz in self.specs:
+            k = int(hz * seconds * 1.5) + 16
+            t = np.cumsum(rng.exponential(1.0 / hz, k))
+            out.append(t[t < seconds])
+        return out
+
+    def pools(self):
+        """(uint8 pool, float32 pool), each pool_len long."""
+        rng = np.random.default_rng(self.seed + 2)
+        return (rng.integers(0, 256, self.pool_len, dtype=np.uint8),
+                rng.standard_normal(self.pool_len, dtype=np.float32))
+
+    def offset(self, i, j):
+        """Start of stream i's j-th frame inside its pool."""
+        n = self.specs[i][1]
+        return (j * 4099 + i * 131) % (self.pool_len - n + 1)

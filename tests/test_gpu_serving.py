@@ -154,6 +154,15 @@ def test_server_admission_and_continuous_batching(cuda_device):
         p50, p99, frames = S.sdmd_server_stats(srv)
         assert frames == sum(pushed)
         assert 0.0 < p50 <= p99
+        # latencies against given arrival times on the server's clock
+        S.sdmd_server_reset_stats(srv)
+        assert S.sdmd_server_stats(srv)[2] == 0
+        t_arr = S.sdmd_server_clock_ms() - 50.0
+        x = _frame("f32", specs[1][1], rng)
+        S.sdmd_server_submit(srv, sids[1], x, t_arr)
+        assert S.sdmd_server_tick(srv) == 1
+        p50, p99, frames = S.sdmd_server_stats(srv)
+        assert frames == 1 and 50.0 <= p50 == p99 < S.sdmd_server_clock_ms() - t_arr
     finally:
         S.sdmd_server_destroy(srv)
         for h in alone:
