@@ -155,9 +155,12 @@ SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const v
  * e.g. to resynchronise G after the ring was modified outside the library.
  * uint8 windows of at most 127 snapshots (with SDMD_OPT_REBUILD_TENSOR, the
  * default): one pass over the window on the tensor cores, exact int64, so
- * equal to the streamed G. Otherwise one Gram-row pass per resident snapshot,
- * in time order, so every entry is computed with the same reduction as when
- * it was streamed: the result equals the streamed G bit for bit (c passes).
+ * equal to the streamed G. FP32 windows with SDMD_OPT_F32_BF16X3 = 1: the
+ * tensor cores in BF16x3 split precision, one pass per block of 64 target
+ * columns (|G_ij - <x_i, x_j>| <= 1e-6 sum_p |x_ip x_jp|). Otherwise one
+ * Gram-row pass per resident snapshot, in time order, so every entry is
+ * computed with the same reduction as when it was streamed: the result
+ * equals the streamed G bit for bit (c passes).
  */
 SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
 
@@ -168,8 +171,12 @@ SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
  * until the stream reaches the call. The resulting G equals that of k
  * sdmd_push calls. uint8 windows of at most 127 snapshots (with
  * SDMD_OPT_REBUILD_TENSOR): the k new rows and columns of G in one pass over
- * the window on the tensor cores (exact int64) instead of k passes; other
- * handles: k sdmd_push calls. SDMD_ERR_ARG for a bad k, ld or pointer.
+ * the window on the tensor cores (exact int64) instead of k passes; FP32
+ * windows with SDMD_OPT_F32_BF16X3 = 1 and k >= 2: the k new rows and columns
+ * in BF16x3 on the tensor cores, one pass over the window per 64 new
+ * snapshots (equal to k pushes within the BF16x3 bound given at
+ * sdmd_rebuild); other handles: k sdmd_push calls. SDMD_ERR_ARG for a bad k,
+ * ld or pointer.
  */
 SDMD_API int sdmd_push_batch(sdmd_t h, int32_t k, const void *X, int64_t ld, void *stream);
 
@@ -348,6 +355,14 @@ enum {
                                    fp16 pixels, exact int64 G); 0: one
                                    Gram-row pass per snapshot (bit-identical
                                    to streaming for every dtype) */
+    ,
+    SDMD_OPT_F32_BF16X3 = 3 /* 0 (default): FP32 windows keep FP32 products
+                               with FP64 sums everywhere; 1: sdmd_rebuild and
+                               sdmd_push_batch (k >= 2) of FP32 windows on the
+                               tensor cores in BF16x3 split precision (each
+                               value as three bf16 terms, the six products
+                               b_i c_j with i + j <= 2, FP32 accumulation per
+                               64 positions, compensated sums) */
 };
 
 /* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */

@@ -5,7 +5,7 @@ Eqs. 5-9), Sec. 3.3 (amplitudes from POD coefficients, Eq. 14a-e) and
 Algorithms 1-3, in FP64 / complex128 with LAPACK (numpy) doing the
 eigendecompositions.
 
-Readings where the paper is silent or ambiguous (all listed in the design doc):
+Readings where the paper is silent or ambiguous:
 
 * window: the c resident snapshots W = [x_1 .. x_c]; X = W[:, :-1] and
   X' = W[:, 1:], so at most c-1 DMD eigenvalues (Algorithm 2 passes a window

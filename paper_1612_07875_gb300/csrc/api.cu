@@ -60,6 +60,7 @@ struct sdmd_s {
   int64_t gsz = 8;            // bytes per G entry (16 for complex handles)
   int32_t phi_tensor = 1;     // SDMD_OPT_PHI_TENSOR
   int32_t rebuild_tensor = 1; // SDMD_OPT_REBUILD_TENSOR
+  int32_t f32_bf16x3 = 0;     // SDMD_OPT_F32_BF16X3
   long long* gf_partials = nullptr;  // tensor-core rebuild: per-CTA sums (allocated on first use)
   unsigned* gf_sched = nullptr;      // tensor-core rebuild: chunk counter
   // sparse handles
@@ -504,6 +505,26 @@ int ensure_gram_full_scratch(sdmd_s* h) {
   return SDMD_OK;
 }
 
+// The k newest of the c resident FP32 snapshots against the window, BF16x3
+// on the tensor cores (k = c: the whole Gram).
+int gram_f32_tensor(sdmd_s* h, int c, int k, cudaStream_t st) {
+  const int rc0 = ensure_gram_full_scratch(h);
+  if (rc0 != SDMD_OK) return rc0;
+  GramF32Args ga;
+  ga.ring = h->ring;
+  ga.slot_bytes = h->slot_bytes;
+  ga.n = h->n;
+  ga.m = h->cap;
+  ga.start = oldest_slot(h);
+  ga.t_tgt = ga.k = ga.t_old = ga.nold = 0;
+  ga.partials = reinterpret_cast<float2*>(h->gf_partials);
+  ga.G = static_cast<double*>(h->G);
+  ga.status = h->status;
+  TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+  CK(launch_gram_f32_tc(ga, c, k, h->num_sms, nullptr, st));
+  return SDMD_OK;
+}
+
 }  // namespace
 
 int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream) {
@@ -516,7 +537,9 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   const int c_after = (int)(h->count + k < h->m ? h->count + k : h->m);
   const size_t elem_bytes = (size_t)h->elem;
   const uint8_t* src = static_cast<const uint8_t*>(X);
-  if (!(h->dtype == SDMD_U8 && h->rebuild_tensor && c_after <= 127)) {
+  const bool u8_tc = h->dtype == SDMD_U8 && h->rebuild_tensor && c_after <= 127;
+  const bool f32_tc = h->dtype == SDMD_F32 && h->f32_bf16x3 && k >= 2;
+  if (!u8_tc && !f32_tc) {
     // k ordinary pushes (one Gram-row pass each)
     for (int j = 0; j < k; ++j) {
       const int rc = sdmd_push(h, src + (size_t)j * ld * elem_bytes, stream);
@@ -536,6 +559,7 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   }
   // rows and columns of the k new snapshots in one pass over the window
   const int kt = k < c_after ? k : c_after;
+  if (f32_tc) return gram_f32_tensor(h, c_after, kt, st);
   GramFullArgs ga;
   ga.ring = h->ring;
   ga.slot_bytes = h->slot_bytes;
@@ -610,6 +634,7 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int c = resident(h);
   const int first = oldest_slot(h);
+  if (h->dtype == SDMD_F32 && h->f32_bf16x3 && c >= 1) return gram_f32_tensor(h, c, c, st);
   if (h->dtype == SDMD_U8 && h->rebuild_tensor && c >= 1 && c <= 127) {
     // one pass over the window on the tensor cores, exact int64
     const int rc0 = ensure_gram_full_scratch(h);
@@ -882,6 +907,9 @@ int sdmd_set_option(sdmd_t h, int32_t option, int64_t value) {
       return SDMD_OK;
     case SDMD_OPT_REBUILD_TENSOR:
       h->rebuild_tensor = value ? 1 : 0;
+      return SDMD_OK;
+    case SDMD_OPT_F32_BF16X3:
+      h->f32_bf16x3 = value ? 1 : 0;
       return SDMD_OK;
     default:
       return fail(SDMD_ERR_ARG, "sdmd_set_option: unknown option %d", option);

@@ -57,6 +57,28 @@ constexpr int kGramFullMaxCtas = 160;
 // Launches the two kernels on `st`; cudaErrorNotSupported outside c <= 127.
 cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream_t st);
 
+// Gram rows/columns of FP32 snapshots on the tensor cores in BF16x3 split
+// precision: one launch pairs k <= 64 target snapshots (window time indices
+// t_tgt ..) with themselves and with nold older ones (t_old ..), k + nold <= 128.
+struct GramF32Args {
+  const uint8_t* ring;
+  int64_t slot_bytes;
+  int64_t n;
+  int32_t m;             // ring modulus (G is m x m doubles, physical slots)
+  int32_t start;         // physical slot of window time index 0 (the oldest)
+  int32_t t_tgt, k;      // target rows
+  int32_t t_old, nold;   // older rows
+  float2* partials;      // [kGramF32MaxCtas][128][64] per-CTA (hi, lo) sums
+  double* G;
+  int* status;
+};
+constexpr int kGramF32MaxCtas = 160;
+constexpr int kGramF32MaxTargets = 64;
+// All launches for the k newest of c resident snapshots (k = c: the whole
+// Gram) on `st`; `launches` receives the number of main-kernel launches.
+cudaError_t launch_gram_f32_tc(const GramF32Args& base, int c, int k, int num_sms, int* launches, cudaStream_t st);
+int gram_f32_tc_ctas(int64_t n, int num_sms);
+
 // One snapshot's Gram row inside a batched launch (fields as in GramRowArgs).
 struct RowJob {
   const uint8_t* ring;

@@ -276,7 +276,7 @@ def test_tensor_core_rebuild_exact(cuda_device, n, m, pushes, pattern):
     (3001, 12, 15, 5, "f32", True),         # float: k ordinary pushes
 ])
 def test_push_batch_equals_sequential_pushes(cuda_device, n, m, pre, k, dtype, device_src):
-    # SURVEY f2 multi-column catch-up: k new rows/columns of G in one pass
+    # multi-column catch-up: k new rows/columns of G in one pass
     # over the window; the Gram must equal that of k single pushes (exactly
     # for uint8, bit for bit for the float fallback) and the oracle's.
     rng = np.random.default_rng(n + k)
