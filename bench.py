@@ -15,7 +15,8 @@ clocks sampled during the timed region.
 
 Secondary measurements in the same line: each kernel launched alone, the
 full-window rebuild (tensor cores vs row passes), the 8-frame catch-up, the
-Fourier-sparse Gram row, and batched serving of 64 mixed FP32/uint8 streams
+Fourier-sparse Gram row, the BF16x3 tensor-core catch-up and rebuild of an
+FP32 window (n = 2^22, m = 256), and batched serving of 64 mixed FP32/uint8 streams
 with Poisson arrivals (aggregate snapshots/s, p50/p99 frame latency, and the
 closed-loop capacity of one batched launch per tick against one push per
 stream).
@@ -329,6 +330,90 @@ def measure_catchup(S, h, frames, t0, stream, n, k=8, reps=3):
     out["k"] = k
     out["note"] = "push_batch: ingest + one exact tensor-core pass for the k new rows/columns"
     return out
+
+
+def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
+    """FP32 window shaped like the precision-sweep workload (n = 2^22, m = 256):
+    k frames appended with one BF16x3 tensor-core sdmd_push_batch against k
+    FP32 sdmd_push calls, the BF16x3 rebuild against the FP32 row passes, and
+    the BF16x3 error of the k new rows on sampled entries against FP64 dot
+    products of the same FP32 frames."""
+    import torch
+    sh = stream.cuda_stream
+    g = torch.Generator(device=dev)
+    g.manual_seed(1612)
+    kmax = max(ks)
+    frames = torch.randn(m + kmax * (reps + 1), n, device=dev, generator=g)
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"n": n, "m": m}
+    try:
+        with torch.cuda.stream(stream):
+            for t in range(m):
+                S.sdmd_push(h, frames[t], sh)
+        nxt = m
+
+        def timed(fn, r=reps):
+            ts = []
+            for i in range(r + 1):
+                with torch.cuda.stream(stream):
+                    e0.record(stream)
+                    fn()
+                    e1.record(stream)
+                stream.synchronize()
+                if i:
+                    ts.append(e0.elapsed_time(e1))
+            return sum(ts) / len(ts)
+
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
+        src = [0]
+
+        def one_push():
+            j = m + src[0] % (kmax * reps)
+            src[0] += 1
+            S.sdmd_push(h, frames[j], sh)
+        ms1 = timed(one_push, r=8)
+        out["fp32_push"] = {"ms": ms1, "snapshots_per_s": 1e3 / ms1, "GB/s": m * n * 4 / (ms1 * 1e-3) / 1e9}
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
+        for k in ks:
+            def batch():
+                j = m + (src[0] * k) % (kmax * reps)
+                src[0] += 1
+                S.sdmd_push_batch(h, k, frames[j:j + k], n, sh)
+            msb = timed(batch)
+            out["bf16x3_push_batch_k%d" % k] = {"ms": msb, "snapshots_per_s": k / (msb * 1e-3),
+                                                 "window_GB/s": m * n * 4 / (msb * 1e-3) / 1e9,
+                                                 "vs_fp32_push": (k / msb) / (1.0 / ms1)}
+        # error of the newest k rows (last batch) on sampled entries
+        k = ks[-1]
+        stream.synchronize()
+        G = torch.empty(m, m, dtype=torch.float64, device=dev)
+        S.sdmd_gram(h, G, sh)
+        stream.synchronize()
+        j = m + ((src[0] - 1) * k) % (kmax * reps)       # the last batch: the k newest snapshots
+        W = frames[j:j + k][::4].double()
+        ref = W @ W.T
+        bound = W.abs() @ W.abs().T
+        sel = torch.arange(m - k, m, 4, device=dev)
+        err = ((G[sel][:, sel] - ref).abs() / bound).max().item()
+        out["bf16x3_sampled_error"] = {"max_abs_err_over_sum_abs_products": err, "entries": int(sel.numel() ** 2),
+                                       "bound": 1e-6,
+                                       "reference": "FP64 dot products of the same FP32 frames (torch, on the GPU)"}
+        msr = timed(lambda: S.sdmd_rebuild(h), r=2)
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
+        msr_rows = timed(lambda: S.sdmd_rebuild(h), r=1)
+        flops = 6 * 2.0 * n * m * m / 2
+        out["rebuild"] = {"bf16x3_ms": msr, "fp32_rows_ms": msr_rows, "speedup": msr_rows / msr,
+                          "bf16x3_TFLOP/s_useful": flops / (msr * 1e-3) / 1e12}
+        if S.sdmd_status(h, sh) != S.SDMD_OK:
+            raise RuntimeError("BF16x3 measurement status: " + S.sdmd_last_error())
+        out["note"] = ("random N(0,1) FP32 frames; window_GB/s = window bytes / batch time; the rebuild's "
+                       "useful flops count the six bf16 products of the lower triangle")
+        return out
+    finally:
+        S.sdmd_destroy(h)
+        del frames
+        torch.cuda.empty_cache()
 
 
 def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
@@ -647,6 +732,11 @@ def run_ours(args):
     if not args.no_secondary:
         sparse = measure_sparse(S, synth, dev, stream)
 
+    # ---- FP32 window n = 2^22, m = 256: BF16x3 tensor-core catch-up / rebuild
+    bf16x3 = None
+    if not args.no_secondary:
+        bf16x3 = measure_bf16x3(S, dev, stream)
+
     # ---- batched serving of 64 mixed streams (Poisson arrivals)
     serving = None
     if not args.no_secondary and args.serve_seconds > 0:
@@ -691,6 +781,7 @@ def run_ours(args):
         "catch_up": catchup,
         "sparse_row": sparse,
         "serving": serving,
+        "fp32_bf16x3": bf16x3,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "clocks": clk,
