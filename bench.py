@@ -399,9 +399,9 @@ def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
         out["bf16x3_sampled_error"] = {"max_abs_err_over_sum_abs_products": err, "entries": int(sel.numel() ** 2),
                                        "bound": 1e-6,
                                        "reference": "FP64 dot products of the same FP32 frames (torch, on the GPU)"}
-        msr = timed(lambda: S.sdmd_rebuild(h), r=2)
+        msr = timed(lambda: S.sdmd_rebuild(h, sh), r=2)
         S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
-        msr_rows = timed(lambda: S.sdmd_rebuild(h), r=1)
+        msr_rows = timed(lambda: S.sdmd_rebuild(h, sh), r=1)
         flops = 6 * 2.0 * n * m * m / 2
         out["rebuild"] = {"bf16x3_ms": msr, "fp32_rows_ms": msr_rows, "speedup": msr_rows / msr,
                           "bf16x3_TFLOP/s_useful": flops / (msr * 1e-3) / 1e12}

@@ -22,14 +22,16 @@
 // block of older snapshots. D[128 x N] += T_a T_b^T over the six term pairs,
 // with T_b the first N = k (rounded up to 16) rows of the same term tiles, so
 // D holds <x_i, x_j> for every tile row i and target j. Each term tile is
-// K-major bf16, 128 rows x 64 positions, no swizzle: core matrix (rg, kg) =
-// rows 8 rg .. 8 rg + 7 x positions 8 kg .. 8 kg + 7 at (kg * 16 + rg) * 128
-// bytes (LBO 2048 B along K, SBO 128 B along M/N).
+// K-major bf16, 128 rows x 64 positions in the 128-byte swizzle: row r is 128
+// bytes at r * 128 and its 16-byte chunk c (positions 8 c .. 8 c + 7) sits at
+// chunk c ^ (r & 7); eight rows form one 1024-byte atom (SBO 1024 B), and the
+// K-slice of positions 16 j .. 16 j + 15 starts 32 j bytes into the tile.
 //
 // Roles (544 threads):
 //   warps 9..16  load + split: warp-private row groups, cp.async 16-byte
 //                copies (a half warp = one row's 256 contiguous bytes) into a
-//                3-deep staging ring, bulk L2 prefetch of every row 2 KiB
+//                4-deep staging ring (16-byte chunk c of row r at chunk
+//                c ^ (r & 7): conflict-free reads), bulk L2 prefetch of every row 2 KiB
 //                ahead, then the three-term split into a 2-deep ring of term
 //                tiles;
 //   warp 8       lane 0 issues the 24 MMAs of a K-step into one of four TMEM
@@ -60,12 +62,12 @@ constexpr int kThreads = 32 * (kConvWarp0 + kConvWarps);   // 544
 constexpr int kRowsM = 128;          // MMA M
 constexpr int kKst = 64;             // positions per K-step (= accumulation period)
 constexpr int kStepsPerChunk = 16;   // scheduling unit: 1024 positions, 4 KiB per row
-constexpr int kStages = 3;           // staging ring (fp32)
+constexpr int kStages = 4;           // staging ring (fp32): three K-steps in flight
 constexpr int kTiles = 2;            // ring of term tiles
-constexpr int kPitch = kKst * 4 + 16;                      // staging row pitch: 272 B
+constexpr int kRowBytes = kKst * 4;                        // 256 B of a row per K-step
 constexpr int kTermBytes = kRowsM * kKst * 2;              // 16384
 constexpr int kTileBytes = 3 * kTermBytes;                 // 49152
-constexpr int kStageBytes = kRowsM * kPitch;               // 34816
+constexpr int kStageBytes = kRowsM * kRowBytes;            // 32768
 constexpr int kAcc = 4;              // TMEM accumulators
 constexpr int kAccCols = kGramF32MaxTargets;               // 64
 constexpr int kTmemCols = kAcc * kAccCols;                 // 256
@@ -154,10 +156,9 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
   // rows beyond `rows` stay zero in every term of both tiles
   for (int idx = tid; idx < kTiles * 3 * kRowsM * (kKst / 8); idx += kThreads) {
     const int tt = idx / (kRowsM * (kKst / 8)), rem = idx - tt * (kRowsM * (kKst / 8));
-    const int row = rem % kRowsM, kg = rem / kRowsM;
+    const int row = rem / (kKst / 8), c = rem % (kKst / 8);
     if (row >= rows)
-      *reinterpret_cast<uint4*>(tiles + tt * kTermBytes + (kg * 16 + (row >> 3)) * 128 + (row & 7) * 16) =
-          make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(tiles + tt * kTermBytes + row * 128 + c * 16) = make_uint4(0u, 0u, 0u, 0u);
   }
   fence_proxy_async();
   fence_before();
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
         const int row = 8 * g + 2 * t + (lane >> 4), ch = lane & 15;
         ld_ok[gi][t] = row < rows;
         src[gi][t] = a.ring + (row < rows ? sh.tab[row] : 0) + 16 * ch;
-        ld_dst[gi][t] = (unsigned)(row * kPitch + 16 * ch);
+        ld_dst[gi][t] = (unsigned)(row * kRowBytes + 16 * (ch ^ (row & 7)));
       }
     }
     const int rsub = lane & 7, kq = lane >> 3;
@@ -233,9 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
       for (int gi = 0; gi < kGroupsPerWarp; ++gi) {
         if (!grp_ok[gi]) continue;
         const int g = cw + gi * kConvWarps;
-        const uint8_t* rp = sb + (8 * g + rsub) * kPitch + 32 * kq;
-        float4 x[4] = {*reinterpret_cast<const float4*>(rp), *reinterpret_cast<const float4*>(rp + 16),
-                       *reinterpret_cast<const float4*>(rp + 128), *reinterpret_cast<const float4*>(rp + 144)};
+        const uint8_t* rp = sb + (8 * g + rsub) * kRowBytes;
+        float4 x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)            // chunks 2 kq, 2 kq + 1, 2 kq + 8, 2 kq + 9 (swizzled)
+          x[q] = *reinterpret_cast<const float4*>(rp + 16 * ((2 * kq + (q & 1) + 8 * (q >> 1)) ^ rsub));
         if (tail) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
             if (pos + 3 >= a.n) x[q].w = 0.f;
           }
         }
-        uint8_t* core = tile + (kq * 16 + g) * 128 + rsub * 16;
+        uint8_t* trow = tile + (8 * g + rsub) * 128;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {          // positions 8 kq .. (h = 0) and 8 kq + 32 .. (h = 1)
           uint4 t0, t1, t2;
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
           split3(x[2 * h].z, x[2 * h].w, t0.y, t1.y, t2.y);
           split3(x[2 * h + 1].x, x[2 * h + 1].y, t0.z, t1.z, t2.z);
           split3(x[2 * h + 1].z, x[2 * h + 1].w, t0.w, t1.w, t2.w);
-          uint8_t* cp = core + h * (4 * 16 * 128);
+          uint8_t* cp = trow + 16 * ((kq + 4 * h) ^ rsub);
           *reinterpret_cast<uint4*>(cp) = t0;
           *reinterpret_cast<uint4*>(cp + kTermBytes) = t1;
           *reinterpret_cast<uint4*>(cp + 2 * kTermBytes) = t2;
@@ -297,8 +300,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
         for (int pr = 0; pr < kPairs; ++pr) {
 #pragma unroll
           for (int ks = 0; ks < kKst / 16; ++ks) {
-            const uint64_t da = smem_desc(base + (unsigned)(pa[pr] * kTermBytes + ks * 4096), 2048u, 128u);
-            const uint64_t db = smem_desc(base + (unsigned)(pb[pr] * kTermBytes + ks * 4096), 2048u, 128u);
+            const uint64_t da = smem_desc_sw128(base + (unsigned)(pa[pr] * kTermBytes + ks * 32));
+            const uint64_t db = smem_desc_sw128(base + (unsigned)(pb[pr] * kTermBytes + ks * 32));
             mma_f16(dt, da, db, idesc, first ? 0u : 1u);
             first = 0;
           }

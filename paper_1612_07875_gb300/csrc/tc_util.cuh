@@ -79,6 +79,19 @@ __device__ __forceinline__ uint64_t smem_desc(unsigned saddr, unsigned lbo, unsi
   return d;
 }
 
+// K-major operand in the 128-byte swizzle: rows of 128 bytes, 8-row atoms
+// of 1024 bytes (SBO), atoms 1024-byte aligned; a K offset inside the atom is
+// added to the start address.
+__device__ __forceinline__ uint64_t smem_desc_sw128(unsigned saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;          // leading byte offset: unused for swizzled K-major
+  d |= (uint64_t)(1024u >> 4) << 32;
+  d |= (uint64_t)1 << 46;          // descriptor version of the tcgen05 family
+  d |= (uint64_t)2 << 61;          // layout: 128-byte swizzle
+  return d;
+}
+
 __device__ __forceinline__ void mma_f16(unsigned dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                         unsigned accumulate) {
   asm volatile(
