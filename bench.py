@@ -374,31 +374,39 @@ def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
             S.sdmd_push(h, frames[j], sh)
         ms1 = timed(one_push, r=8)
         out["fp32_push"] = {"ms": ms1, "snapshots_per_s": 1e3 / ms1, "GB/s": m * n * 4 / (ms1 * 1e-3) / 1e9}
-        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
-        for k in ks:
-            def batch():
-                j = m + (src[0] * k) % (kmax * reps)
-                src[0] += 1
-                S.sdmd_push_batch(h, k, frames[j:j + k], n, sh)
-            msb = timed(batch)
-            out["bf16x3_push_batch_k%d" % k] = {"ms": msb, "snapshots_per_s": k / (msb * 1e-3),
-                                                 "window_GB/s": m * n * 4 / (msb * 1e-3) / 1e9,
-                                                 "vs_fp32_push": (k / msb) / (1.0 / ms1)}
-        # error of the newest k rows (last batch) on sampled entries
-        k = ks[-1]
-        stream.synchronize()
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_FP64, 1)
+        ms64 = timed(one_push, r=3)
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_FP64, 0)
+        out["fp64_push"] = {"ms": ms64, "snapshots_per_s": 1e3 / ms64,
+                            "note": "FP64 products and sums (reference precision)"}
         G = torch.empty(m, m, dtype=torch.float64, device=dev)
-        S.sdmd_gram(h, G, sh)
-        stream.synchronize()
-        j = m + ((src[0] - 1) * k) % (kmax * reps)       # the last batch: the k newest snapshots
-        W = frames[j:j + k][::4].double()
-        ref = W @ W.T
-        bound = W.abs() @ W.abs().T
-        sel = torch.arange(m - k, m, 4, device=dev)
-        err = ((G[sel][:, sel] - ref).abs() / bound).max().item()
-        out["bf16x3_sampled_error"] = {"max_abs_err_over_sum_abs_products": err, "entries": int(sel.numel() ** 2),
-                                       "bound": 1e-6,
-                                       "reference": "FP64 dot products of the same FP32 frames (torch, on the GPU)"}
+        for split, name, bound in ((1, "bf16x3", 1e-6), (2, "bf16x2", 3e-5)):
+            S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, split)
+            for k in ks:
+                def batch():
+                    j = m + (src[0] * k) % (kmax * reps)
+                    src[0] += 1
+                    S.sdmd_push_batch(h, k, frames[j:j + k], n, sh)
+                msb = timed(batch)
+                out["%s_push_batch_k%d" % (name, k)] = {"ms": msb, "snapshots_per_s": k / (msb * 1e-3),
+                                                         "window_GB/s": m * n * 4 / (msb * 1e-3) / 1e9,
+                                                         "vs_fp32_push": (k / msb) / (1.0 / ms1)}
+            # error of the newest k rows (last batch) on sampled entries
+            k = ks[-1]
+            stream.synchronize()
+            S.sdmd_gram(h, G, sh)
+            stream.synchronize()
+            j = m + ((src[0] - 1) * k) % (kmax * reps)   # the last batch: the k newest snapshots
+            W = frames[j:j + k][::4].double()
+            ref = W @ W.T
+            bnd = W.abs() @ W.abs().T
+            sel = torch.arange(m - k, m, 4, device=dev)
+            err = ((G[sel][:, sel] - ref).abs() / bnd).max().item()
+            fro = (torch.linalg.norm(G[sel][:, sel] - ref) / torch.linalg.norm(ref)).item()
+            out["%s_sampled_error" % name] = {
+                "max_abs_err_over_sum_abs_products": err, "rel_frobenius": fro, "entries": int(sel.numel() ** 2),
+                "bound": bound, "reference": "FP64 dot products of the same FP32 frames (torch, on the GPU)"}
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
         msr = timed(lambda: S.sdmd_rebuild(h, sh), r=2)
         S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
         msr_rows = timed(lambda: S.sdmd_rebuild(h, sh), r=1)

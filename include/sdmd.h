@@ -362,7 +362,16 @@ enum {
                                tensor cores in BF16x3 split precision (each
                                value as three bf16 terms, the six products
                                b_i c_j with i + j <= 2, FP32 accumulation per
-                               64 positions, compensated sums) */
+                               64 positions, compensated sums; bound
+                               1e-6 sum_p |x_ip x_jp|); 2: the same with two
+                               bf16 terms and the three products with
+                               i + j <= 1 (about 2^-16 per product) */
+    ,
+    SDMD_OPT_F32_FP64 = 4   /* 0 (default): Gram rows of FP32 windows with FP32
+                               products and FP64 sums; 1: FP64 products (exact
+                               for FP32 inputs) and FP64 sums, the reference
+                               precision (GB300 runs FP64 at a small fraction
+                               of FP32: several times slower) */
 };
 
 /* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */

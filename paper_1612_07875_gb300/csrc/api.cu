@@ -60,7 +60,8 @@ struct sdmd_s {
   int64_t gsz = 8;            // bytes per G entry (16 for complex handles)
   int32_t phi_tensor = 1;     // SDMD_OPT_PHI_TENSOR
   int32_t rebuild_tensor = 1; // SDMD_OPT_REBUILD_TENSOR
-  int32_t f32_bf16x3 = 0;     // SDMD_OPT_F32_BF16X3
+  int32_t f32_bf16x3 = 0;     // SDMD_OPT_F32_BF16X3 (0 off, 1 three terms, 2 two terms)
+  int32_t f32_fp64 = 0;       // SDMD_OPT_F32_FP64
   long long* gf_partials = nullptr;  // tensor-core rebuild: per-CTA sums (allocated on first use)
   unsigned* gf_sched = nullptr;      // tensor-core rebuild: chunk counter
   // sparse handles
@@ -486,7 +487,7 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   a.status = h->status;
   {
     TraceScope ts(h, SDMD_K_GRAM_ROW, st);
-    CK(launch_gram_row(h->dtype, a, st));
+    CK(launch_gram_row(h->dtype, h->f32_fp64 != 0, a, st));
   }
   h->head = (s + 1) % h->cap;
   h->count += 1;
@@ -517,6 +518,7 @@ int gram_f32_tensor(sdmd_s* h, int c, int k, cudaStream_t st) {
   ga.m = h->cap;
   ga.start = oldest_slot(h);
   ga.t_tgt = ga.k = ga.t_old = ga.nold = 0;
+  ga.split = (h->f32_bf16x3 == 2) ? 2 : 3;
   ga.partials = reinterpret_cast<float2*>(h->gf_partials);
   ga.G = static_cast<double*>(h->G);
   ga.status = h->status;
@@ -615,7 +617,7 @@ int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void*
     J.s_first = (int32_t)((h->count + 1 - J.c) % h->cap);
     J.s_new = s_new;
     J.m = h->cap;
-    J.mode = (h->dtype == SDMD_U8) ? 0 : (h->dtype == SDMD_F32 ? 1 : 2);
+    J.mode = (h->dtype == SDMD_U8) ? 0 : (h->dtype == SDMD_F32 ? (h->f32_fp64 ? 3 : 1) : 2);
     J.item0 = ba.nitems;
     ba.nitems += h->nblk;
     h->head = (s_new + 1) % h->cap;
@@ -702,7 +704,7 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
       a.G = h->G;
       a.status = h->status;
       TraceScope ts(h, SDMD_K_GRAM_ROW, st);
-      CK(launch_gram_row(h->dtype, a, st));
+      CK(launch_gram_row(h->dtype, h->f32_fp64 != 0, a, st));
     }
   }
   return SDMD_OK;
@@ -909,7 +911,11 @@ int sdmd_set_option(sdmd_t h, int32_t option, int64_t value) {
       h->rebuild_tensor = value ? 1 : 0;
       return SDMD_OK;
     case SDMD_OPT_F32_BF16X3:
-      h->f32_bf16x3 = value ? 1 : 0;
+      if (value < 0 || value > 2) return fail(SDMD_ERR_ARG, "sdmd_set_option: SDMD_OPT_F32_BF16X3 value %lld not in 0..2", (long long)value);
+      h->f32_bf16x3 = (int32_t)value;
+      return SDMD_OK;
+    case SDMD_OPT_F32_FP64:
+      h->f32_fp64 = value ? 1 : 0;
       return SDMD_OK;
     default:
       return fail(SDMD_ERR_ARG, "sdmd_set_option: unknown option %d", option);

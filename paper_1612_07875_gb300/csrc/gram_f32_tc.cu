@@ -9,10 +9,14 @@
 // |r| <= 2^-24 |x|. A product x y is taken as the six products b_i c_j with
 // i + j <= 2; the dropped ones and the remainders are below 2^-22 |x y|.
 //
+// Two-term variant (split = 2): x = b0 + b1 + r2 with |r2| <= 2^-16 |x|, the
+// three products with i + j <= 1; the dropped b1 c1 and remainders are about
+// 2^-16 |x y| (the bf16x3 of three bf16 GEMMs).
+//
 // Accumulation. One accumulation period is one K-step of 64 positions: its
-// 20 cross-term MMAs (i + j >= 1) run first, from a zeroed accumulator, then
-// the 4 b0 c0 MMAs, so the FP32 tensor-memory accumulator rounds about 4
-// times at full magnitude per period. Every period is drained into
+// cross-term MMAs (i + j >= 1, smallest first) run first, from a zeroed
+// accumulator, then the 4 b0 c0 MMAs, so the FP32 tensor-memory accumulator
+// rounds about 4 times at full magnitude per period. Every period is drained into
 // compensated FP32 sums (hi + lo, error-free two-sum per value) per CTA, and
 // the per-CTA sums are added in FP64 in a fixed order. Chunks are assigned to
 // CTAs statically, so the result is the same on every run. Bound used by the
@@ -275,9 +279,12 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
       const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(npad >> 3) << 17) |
                              ((uint32_t)(kRowsM >> 4) << 24);
       // (A term, B term): the cross terms first, b0 c0 last
+      // (A term, B term), smallest first: three terms take all six pairs
+      // (i + j <= 2), two terms the last three (i + j <= 1); b0 c0 is last
       constexpr int kPairs = 6;
-      const int pa[kPairs] = {1, 0, 1, 2, 0, 0};
-      const int pb[kPairs] = {0, 1, 1, 0, 2, 0};
+      const int pa[kPairs] = {1, 2, 0, 1, 0, 0};
+      const int pb[kPairs] = {1, 0, 2, 0, 1, 0};
+      const int pr0 = (a.split == 2) ? 3 : 0;
       bool ok = true;
       int64_t s = 0;
       for (; s < nsteps; ++s) {
@@ -298,6 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
         int first = 1;
 #pragma unroll
         for (int pr = 0; pr < kPairs; ++pr) {
+          if (pr < pr0) continue;
 #pragma unroll
           for (int ks = 0; ks < kKst / 16; ++ks) {
             const uint64_t da = smem_desc_sw128(base + (unsigned)(pa[pr] * kTermBytes + ks * 32));

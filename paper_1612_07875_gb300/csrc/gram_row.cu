@@ -111,7 +111,9 @@ struct Smem {
 };
 
 // Element modes of the kernel.
-enum { kModeU8 = 0, kModeF32 = 1, kModeC64 = 2 };
+// kModeF64: FP32 snapshots with FP64 products and sums (the reference Gram;
+// a product of two FP32 values is exact in FP64).
+enum { kModeU8 = 0, kModeF32 = 1, kModeC64 = 2, kModeF64 = 3 };
 
 template <typename Acc>
 __device__ void finish_row(const GramRowArgs& a, Smem& sm) {
@@ -293,6 +295,18 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
           f3 = fmaf(v.w, w.w, f3);
         }
         sd += (double)((f0 + f1) + (f2 + f3));
+      } else if constexpr (kMode == kModeF64) {
+        double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+#pragma unroll
+        for (int u = 0; u < kPiece / 512; ++u) {
+          const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+          const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+          d0 = fma((double)v.x, (double)w.x, d0);
+          d1 = fma((double)v.y, (double)w.y, d1);
+          d2 = fma((double)v.z, (double)w.z, d2);
+          d3 = fma((double)v.w, (double)w.w, d3);
+        }
+        sd += (d0 + d1) + (d2 + d3);
       } else {
         // two complex64 values per 16 bytes: conj(v) * w
         float r0 = 0.f, r1 = 0.f, i0 = 0.f, i1 = 0.f;
@@ -340,7 +354,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
     for (int j = threadIdx.x; j < a.c; j += blockDim.x) {
       if constexpr (kU8) {
         static_cast<long long*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_i[j];
-      } else if constexpr (kMode == kModeF32) {
+      } else if constexpr (kMode == kModeF32 || kMode == kModeF64) {
         static_cast<double*>(a.partials)[(int64_t)j * a.nblk + ch] = sm.acc_d[j];
       } else {
         static_cast<double2*>(a.partials)[(int64_t)j * a.nblk + ch] = make_double2(sm.acc_d[j], sm.acc_im[j]);
@@ -360,7 +374,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_row_bulk_kernel(GramRowArg
   }
   if constexpr (kU8) {
     finish_row<long long>(a, sm);
-  } else if constexpr (kMode == kModeF32) {
+  } else if constexpr (kMode == kModeF32 || kMode == kModeF64) {
     finish_row<double>(a, sm);
   } else {
     finish_row_c64(a, sm);
@@ -413,6 +427,18 @@ __device__ __forceinline__ void piece_sums(const uint8_t* piece, const uint8_t* 
       f3 = fmaf(v.w, w.w, f3);
     }
     sd += (double)((f0 + f1) + (f2 + f3));
+  } else if constexpr (kMode == kModeF64) {
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+#pragma unroll
+    for (int u = 0; u < kPiece / 512; ++u) {
+      const float4 v = *reinterpret_cast<const float4*>(piece + 16 * lane + 512 * u);
+      const float4 w = *reinterpret_cast<const float4*>(xq + 16 * lane + 512 * u);
+      d0 = fma((double)v.x, (double)w.x, d0);
+      d1 = fma((double)v.y, (double)w.y, d1);
+      d2 = fma((double)v.z, (double)w.z, d2);
+      d3 = fma((double)v.w, (double)w.w, d3);
+    }
+    sd += (d0 + d1) + (d2 + d3);
   } else {
     float r0 = 0.f, r1 = 0.f, i0 = 0.f, i1 = 0.f;
 #pragma unroll
@@ -571,6 +597,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_rows_batched_kernel(const 
     bool ok;
     if (J.mode == kModeU8) ok = batch_item<kModeU8>(J, ch, sm, g, item_no);
     else if (J.mode == kModeF32) ok = batch_item<kModeF32>(J, ch, sm, g, item_no);
+    else if (J.mode == kModeF64) ok = batch_item<kModeF64>(J, ch, sm, g, item_no);
     else ok = batch_item<kModeC64>(J, ch, sm, g, item_no);
     if (!ok && (threadIdx.x & 31) == 0) {
       atomicOr(a.status, kDevTimeout);
@@ -579,7 +606,8 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_rows_batched_kernel(const 
     __syncthreads();
     for (int j = threadIdx.x; j < J.c; j += blockDim.x) {
       if (J.mode == kModeU8) static_cast<long long*>(J.partials)[(int64_t)j * J.nblk + ch] = sm.acc_i[j];
-      else if (J.mode == kModeF32) static_cast<double*>(J.partials)[(int64_t)j * J.nblk + ch] = sm.acc_d[j];
+      else if (J.mode == kModeF32 || J.mode == kModeF64)
+        static_cast<double*>(J.partials)[(int64_t)j * J.nblk + ch] = sm.acc_d[j];
       else static_cast<double2*>(J.partials)[(int64_t)j * J.nblk + ch] = make_double2(sm.acc_d[j], sm.acc_im[j]);
       sm.acc_i[j] = 0;
       sm.acc_d[j] = 0.0;
@@ -592,7 +620,7 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_rows_batched_kernel(const 
     if (sm.last) {                     // this job's chunks are all in: reduce its row
       __threadfence();
       if (J.mode == kModeU8) batch_finish<long long>(J);
-      else if (J.mode == kModeF32) batch_finish<double>(J);
+      else if (J.mode == kModeF32 || J.mode == kModeF64) batch_finish<double>(J);
       else batch_finish_c64(J);
       if (threadIdx.x == 0) J.ticket[0] = 0u;
     }
@@ -625,7 +653,7 @@ void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t*
   *nblk = (int32_t)((units + per - 1) / per);
 }
 
-cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
+cudaError_t launch_gram_row(int dtype, bool f64_ref, const GramRowArgs& a, cudaStream_t st) {
   static bool attr = false;
   const size_t smem = sizeof(Smem);
   if (!attr) {
@@ -634,6 +662,8 @@ cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
       e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeC64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = true;
   }
@@ -645,6 +675,8 @@ cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st) {
     gram_row_bulk_kernel<kModeU8><<<ctas, kGrThreads, smem, st>>>(a);
   else if (dtype == SDMD_C64)
     gram_row_bulk_kernel<kModeC64><<<ctas, kGrThreads, smem, st>>>(a);
+  else if (f64_ref)
+    gram_row_bulk_kernel<kModeF64><<<ctas, kGrThreads, smem, st>>>(a);
   else
     gram_row_bulk_kernel<kModeF32><<<ctas, kGrThreads, smem, st>>>(a);
   return cudaGetLastError();

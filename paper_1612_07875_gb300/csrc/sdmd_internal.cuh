@@ -68,6 +68,7 @@ struct GramF32Args {
   int32_t start;         // physical slot of window time index 0 (the oldest)
   int32_t t_tgt, k;      // target rows
   int32_t t_old, nold;   // older rows
+  int32_t split;         // 3: three bf16 terms, six products; 2: two terms, three products
   float2* partials;      // [kGramF32MaxCtas][128][64] per-CTA (hi, lo) sums
   double* G;
   int* status;
@@ -88,7 +89,7 @@ struct RowJob {
   unsigned int* ticket;  // chunks finished (word 0), zero between launches
   void* G;
   int32_t nblk, c, s_first, s_new, m;
-  int32_t mode;          // 0 uint8, 1 float32, 2 complex64
+  int32_t mode;          // 0 uint8, 1 float32, 2 complex64, 3 float32 with FP64 products
   int32_t item0;         // first work item of this job in the batch
 };
 constexpr int kMaxBatchJobs = 64;
@@ -105,7 +106,8 @@ cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st);
 int64_t handle_device_bytes(int64_t n, int32_t m, int32_t dtype, int num_sms);
 
 // Gram row for one pushed snapshot; launches one kernel on `st`.
-cudaError_t launch_gram_row(int dtype, const GramRowArgs& a, cudaStream_t st);
+// f64_ref: FP32 snapshots with FP64 products and sums (SDMD_OPT_F32_FP64).
+cudaError_t launch_gram_row(int dtype, bool f64_ref, const GramRowArgs& a, cudaStream_t st);
 
 // Schedule of the Gram-row kernel: a function of slot size and SM count only,
 // so that every entry of G sees the same summation order.

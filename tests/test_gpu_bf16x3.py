@@ -107,6 +107,58 @@ def test_push_batch_bf16x3_within_bound(cuda_device, n, m, pre, k):
         S.sdmd_destroy(h)
 
 
+@pytest.mark.parametrize("n,m,data", [(70001, 40, "normal"), ((1 << 18) + 1, 100, "offset")])
+def test_rebuild_two_term_split_within_its_bound(cuda_device, n, m, data):
+    # two bf16 terms, three products: dropped b1 c1 and remainders about
+    # 2^-16 |x y| per product; bound used: 3e-5 sum_p |x_ip x_jp|
+    X = _frames(n, m, seed=11 * n + m, kind=data)
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    try:
+        for t in range(m):
+            S.sdmd_push(h, torch.from_numpy(X[t]).to(cuda_device))
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 2)
+        S.sdmd_rebuild(h)
+        G = _gram(h, m, cuda_device)
+        Wd = X.astype(np.float64)
+        ref = Wd @ Wd.T
+        worst = float((np.abs(G - ref) / (np.abs(Wd) @ np.abs(Wd).T)).max())
+        print("two-term n=%d m=%d %s: worst %.2e, rel Frobenius %.2e" % (n, m, data, worst, rel_fro(G, ref)))
+        assert worst <= 3e-5
+        assert np.array_equal(G, G.T)
+        with pytest.raises(S.SdmdError):
+            S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 3)
+    finally:
+        S.sdmd_destroy(h)
+
+
+def test_fp64_reference_rows(cuda_device):
+    # FP64 products (exact for FP32 inputs) and FP64 sums: the oracle's Gram
+    # up to FP64 summation order; batched rows equal single pushes bit for bit
+    n, m = (1 << 17) + 9, 12
+    X = _frames(n, m + 4, seed=2)
+    ha = S.sdmd_create(n, m, S.SDMD_F32)
+    hb = S.sdmd_create(n, m, S.SDMD_F32)
+    hc = S.sdmd_create(777, 5, S.SDMD_U8)
+    so = oracle.StreamOracle(n, m, "f32")
+    try:
+        for h in (ha, hb):
+            S.sdmd_set_option(h, S.SDMD_OPT_F32_FP64, 1)
+        u8 = np.random.default_rng(3).integers(0, 256, (m + 4, 777), dtype=np.uint8)
+        for t in range(m + 4):
+            x = torch.from_numpy(X[t]).to(cuda_device)
+            S.sdmd_push(ha, x)
+            S.sdmd_push_many([hb, hc], [x, torch.from_numpy(u8[t]).to(cuda_device)])
+            so.push(X[t])
+        Ga, Gb = _gram(ha, m, cuda_device), _gram(hb, m, cuda_device)
+        assert np.array_equal(Ga, Gb)
+        ref = so.gram()
+        assert rel_fro(Ga, ref) <= 1e-14
+        assert np.abs(Ga - ref).max() <= 1e-13 * np.abs(ref).max()
+    finally:
+        for h in (ha, hb, hc):
+            S.sdmd_destroy(h)
+
+
 def test_bf16x3_option_off_keeps_fp32_rows(cuda_device):
     n, m, k = 20000, 12, 6
     X = _frames(n, m + k, seed=5)
