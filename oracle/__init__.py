@@ -33,12 +33,14 @@ from .gram import (gram_dense, cross_gram, gram_u8, gram_u8_cols, dot_u8, sparse
                    gram_sparse, densify_sparse)
 from .dmd import (RANK_RTOL_FACTOR, numerical_rank, mos_svd, exact_dmd, dmd_from_gram,
                   DMDResult, pod_amplitudes, lstsq_amplitudes,
-                  background_index, background_column, reconstruct, foreground_column)
+                  background_index, background_column, reconstruct, foreground_column,
+                  pod_modes, slow_modes, slow_background_column, slow_foreground_column)
 from .stream import StreamOracle
 
 __all__ = [
     "gram_dense", "cross_gram", "gram_u8", "gram_u8_cols", "dot_u8", "sparse_inner",
     "gram_sparse", "densify_sparse", "RANK_RTOL_FACTOR", "numerical_rank",
     "mos_svd", "exact_dmd", "dmd_from_gram", "DMDResult", "pod_amplitudes", "lstsq_amplitudes",
-    "background_index", "background_column", "reconstruct", "foreground_column", "StreamOracle",
+    "background_index", "background_column", "reconstruct", "foreground_column", "pod_modes",
+    "slow_modes", "slow_background_column", "slow_foreground_column", "StreamOracle",
 ]

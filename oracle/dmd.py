@@ -190,3 +190,37 @@ def foreground_column(W, res, b, t):
     """x_t minus its background (Eq. 11's sparse part, Algorithm 3), where
     W[:, t] is the window column at time index t (t = 0 is x_1)."""
     return np.asarray(W)[:, t].astype(np.float64) - background_column(res, b, t).real
+
+
+def pod_modes(W, r):
+    """POD (left singular) vectors of X = W[:, :-1]: U_r = X V_r Sigma_r^-1
+    (Eq. 4), with sigma and V from the method of snapshots (mos_svd of
+    X^H X, Algorithm 1); r is clamped to the numerical rank. Returns
+    (U, sigma) with U of shape n x r."""
+    W = np.asarray(W)
+    exact_u8 = W.dtype == np.uint8
+    X, _, GX, _ = _window_blocks(W, exact_u8)
+    _, sigma, V, rank = mos_svd(GX)
+    rr = int(min(max(r, 0), rank))
+    Xf = X.astype(np.complex128) if np.iscomplexobj(X) else X.astype(np.float64)
+    U = Xf @ (V[:, :rr] / sigma[None, :rr])
+    return U, sigma[:rr]
+
+
+def slow_modes(lam, tol):
+    """Indices of the slow modes: |log lambda_k| <= tol with the principal
+    log (several background modes instead of the single argmin, Algorithm 3's
+    criterion widened to a threshold)."""
+    return np.nonzero(np.abs(np.log(np.asarray(lam, dtype=np.complex128))) <= tol)[0]
+
+
+def slow_background_column(res, b, t, tol):
+    """sum over the slow modes of b_k phi_k lambda_k^t (Eq. 11 with the
+    low-rank part spanned by every slow mode); t = 0 is x_1."""
+    idx = slow_modes(res.lam, tol)
+    return res.Phi[:, idx] @ (b[idx] * res.lam[idx] ** t)
+
+
+def slow_foreground_column(W, res, b, t, tol):
+    """x_t minus its slow-mode background (real part)."""
+    return np.asarray(W)[:, t].astype(np.float64) - slow_background_column(res, b, t, tol).real

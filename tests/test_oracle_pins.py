@@ -381,6 +381,43 @@ def test_background_and_foreground_of_planted_static_scene():
         assert np.allclose(oracle.foreground_column(W, res, b, t), W[:, t] - B, atol=1e-9)
 
 
+def test_slow_modes_background_is_the_planted_slow_part():
+    # Planted scene: static B (lambda = 1), a rotation (|log lambda| = 0.4)
+    # and a decay (lambda = 0.97, |log lambda| = 0.030). Slow modes with
+    # tol = 0.1 are the static and the decaying ones: their background is
+    # B + the decaying component, known in closed form; tol below 0.03 leaves
+    # the single background mode, tol above 0.4 every mode (the window).
+    W, B = _planted_rotation_window(10, static=3.0, seed=51)
+    rng = np.random.default_rng(51)
+    Q, _ = np.linalg.qr(rng.standard_normal((40, 4)))
+    res = oracle.exact_dmd(W, r=4)
+    b = oracle.pod_amplitudes(res)
+    assert sorted(oracle.slow_modes(res.lam, 0.1).tolist()) == sorted(
+        [int(np.argmin(np.abs(res.lam - 1.0))), int(np.argmin(np.abs(res.lam - 0.97)))])
+    for t in (0, 3, 9):
+        decay = Q[:, 2] * 2.0 * 0.97 ** t
+        assert np.allclose(oracle.slow_background_column(res, b, t, 0.1).real, B + decay, atol=1e-9)
+        assert np.allclose(oracle.slow_foreground_column(W, res, b, t, 0.1), W[:, t] - B - decay, atol=1e-9)
+        assert np.allclose(oracle.slow_background_column(res, b, t, 0.01), oracle.background_column(res, b, t),
+                           atol=1e-12)
+        assert np.allclose(oracle.slow_background_column(res, b, t, 0.5).real, W[:, t], atol=1e-9)
+
+
+def test_pod_modes_are_the_left_singular_vectors():
+    # U = X V Sigma^-1 (Eq. 4) against numpy's SVD of X: same sigma, columns
+    # equal up to sign, orthonormal; X (not X') is the operand.
+    rng = np.random.default_rng(70)
+    W = rng.standard_normal((30, 8)) * np.array([5, 4, 3, 2.5, 2, 1.5, 1, 0.5])[None, :]
+    U, sigma = oracle.pod_modes(W, 5)
+    Us, ss, _ = np.linalg.svd(W[:, :-1], full_matrices=False)
+    assert np.allclose(sigma, ss[:5], rtol=1e-12)
+    for k in range(5):
+        assert abs(abs(U[:, k] @ Us[:, k]) - 1.0) < 1e-10
+    assert np.allclose(U.T @ U, np.eye(5), atol=1e-10)
+    Uu, _ = oracle.pod_modes(rng.integers(0, 256, (50, 6), dtype=np.uint8), 3)   # exact-u8 Gram route
+    assert np.allclose(Uu.T @ Uu, np.eye(3), atol=1e-9)
+
+
 def test_background_index_principal_log():
     lam = np.array([0.5, 1.0001 * cmath.exp(0.001j), 0.9 * cmath.exp(2j), -1.0])
     # |log(-1)| = pi: a unit-modulus but fast mode is not background
