@@ -316,7 +316,10 @@ SDMD_API int sdmd_amplitudes(sdmd_t h, void *b, int32_t *bg_index, void *stream)
 enum {
     SDMD_RECON_MODES = 0,       /* sum_k b_k phi_k lambda_k^t over the kept modes */
     SDMD_RECON_BACKGROUND = 1,  /* b_i phi_i lambda_i^t, i = background mode (Algorithm 3) */
-    SDMD_RECON_FOREGROUND = 2   /* x_t minus its background (Eq. 11's sparse part) */
+    SDMD_RECON_FOREGROUND = 2,  /* x_t minus its background (Eq. 11's sparse part) */
+    SDMD_RECON_BACKGROUND_SLOW = 3, /* sum over the slow modes, |log lambda_k| <= tol
+                                       (several background modes; sdmd_reconstruct_ex) */
+    SDMD_RECON_FOREGROUND_SLOW = 4  /* x_t minus the slow-mode background */
 };
 
 /*
@@ -332,6 +335,27 @@ enum {
  * pointer.
  */
 SDMD_API int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float *out, void *stream);
+
+/*
+ * sdmd_reconstruct_ex -- sdmd_reconstruct with a tolerance for the slow-mode
+ * variants: SDMD_RECON_BACKGROUND_SLOW sums b_k phi_k lambda_k^t over every
+ * kept mode with |log lambda_k| <= tol (principal log; the background of
+ * Eq. 11 spanned by several slow modes instead of Algorithm 3's single
+ * argmin), SDMD_RECON_FOREGROUND_SLOW is x_t minus that sum. tol >= 0; it is
+ * ignored by the other variants. Errors as sdmd_reconstruct.
+ */
+SDMD_API int sdmd_reconstruct_ex(sdmd_t h, int64_t t, int32_t what, double tol, float *out, void *stream);
+
+/*
+ * sdmd_pod_modes -- the POD (left singular) vectors of X from the last
+ * sdmd_modes call: U = X V Sigma^-1 (Sec. 2.1, Eq. 4), the SVD-only output of
+ * the method of snapshots, formed in one pass over X (the oldest c-1
+ * resident snapshots). U receives n x r float32, column-major (vector k at
+ * U + k*n), device memory, 4-byte aligned; columns beyond the kept rank are
+ * zero. r must equal the r of that sdmd_modes call. Real dense handles;
+ * SDMD_ERR_NOT_READY if no sdmd_modes call has run since the last push.
+ */
+SDMD_API int sdmd_pod_modes(sdmd_t h, int32_t r, float *U, void *stream);
 
 /*
  * sdmd_status -- waits for `stream`, then reports the device-side status

@@ -986,15 +986,55 @@ int sdmd_amplitudes(sdmd_t h, void* b, int32_t* bg_index, void* stream) {
 }
 
 int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float* out, void* stream) {
+  if (what == SDMD_RECON_BACKGROUND_SLOW || what == SDMD_RECON_FOREGROUND_SLOW)
+    return fail(SDMD_ERR_ARG, "sdmd_reconstruct: the slow-mode variants take a tolerance (sdmd_reconstruct_ex)");
+  return sdmd_reconstruct_ex(h, t, what, 0.0, out, stream);
+}
+
+int sdmd_pod_modes(sdmd_t h, int32_t r, float* U, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_pod_modes: NULL handle");
+  if (h->dtype != SDMD_U8 && h->dtype != SDMD_F32)
+    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_pod_modes: real dense handles only");
+  if (h->modes_count != h->count || h->last_r < 1)
+    return fail(SDMD_ERR_NOT_READY, "sdmd_pod_modes: no sdmd_modes call since the last push");
+  if (r != h->last_r) return fail(SDMD_ERR_ARG, "sdmd_pod_modes: r=%d differs from the last sdmd_modes r=%d", r, h->last_r);
+  if (!U || ptr_kind(U) != kDevice || (reinterpret_cast<uintptr_t>(U) & 3u) != 0)
+    return fail(SDMD_ERR_ARG, "sdmd_pod_modes: U must be device memory (n x r floats)");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const ModesLayout L = modes_layout(h->m);
+  PhiArgs pa;
+  pa.ring = h->ring;
+  pa.slot_bytes = h->slot_bytes;
+  pa.n = h->n;
+  pa.dtype = h->dtype;
+  pa.m = h->cap;
+  pa.start = oldest_slot(h);
+  pa.p = h->last_p;
+  pa.r = r;
+  pa.Mf = nullptr;
+  pa.r_dev = h->r_dev;
+  pa.phi = U;
+  pa.status = h->status;
+  pa.tensor = 0;
+  pa.sched = h->phi_sched;
+  TraceScope ts(h, SDMD_K_PHI, st);
+  CK(launch_pod_modes(pa, h->ws + L.V, h->ws + L.sig, reinterpret_cast<float*>(h->ws + L.Mu), st));
+  return SDMD_OK;
+}
+
+int sdmd_reconstruct_ex(sdmd_t h, int64_t t, int32_t what, double tol, float* out, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_reconstruct: NULL handle");
   if (h->dtype != SDMD_U8 && h->dtype != SDMD_F32)
     return fail(SDMD_ERR_UNSUPPORTED, "sdmd_reconstruct: real dense handles only");
   if (h->modes_count != h->count || h->last_r < 1)
     return fail(SDMD_ERR_NOT_READY, "sdmd_reconstruct: no sdmd_modes call since the last push");
-  if (what != SDMD_RECON_MODES && what != SDMD_RECON_BACKGROUND && what != SDMD_RECON_FOREGROUND)
+  if (what < SDMD_RECON_MODES || what > SDMD_RECON_FOREGROUND_SLOW)
     return fail(SDMD_ERR_ARG, "sdmd_reconstruct: what=%d", what);
+  const bool fg = (what == SDMD_RECON_FOREGROUND || what == SDMD_RECON_FOREGROUND_SLOW);
+  if (!(tol >= 0.0)) return fail(SDMD_ERR_ARG, "sdmd_reconstruct: tol must be >= 0");
   const int c = h->last_p + 1;
-  if (t < 0 || (what == SDMD_RECON_FOREGROUND && t > c - 1))
+  if (t < 0 || (fg && t > c - 1))
     return fail(SDMD_ERR_ARG, "sdmd_reconstruct: t=%lld out of range", (long long)t);
   if (!out || ptr_kind(out) != kDevice || (reinterpret_cast<uintptr_t>(out) & 15u) != 0)
     return fail(SDMD_ERR_ARG, "sdmd_reconstruct: out must be 16-byte aligned device memory (n floats)");
@@ -1020,7 +1060,8 @@ int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float* out, void* stream
   ra.what = what;
   ra.urec = reinterpret_cast<float*>(h->ws + L.urec);
   ra.out = out;
-  ra.xt_slot = (what == SDMD_RECON_FOREGROUND) ? (int32_t)((ra.start + t) % h->cap) : -1;
+  ra.xt_slot = fg ? (int32_t)((ra.start + t) % h->cap) : -1;
+  ra.slow_tol = tol;
   CK(launch_reconstruct(ra, st));
   return SDMD_OK;
 }

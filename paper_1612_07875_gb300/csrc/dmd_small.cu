@@ -56,6 +56,7 @@ constexpr int kMsRounds = 8;                     // FP32 multisection rounds (33
 constexpr int kJacobiSweeps = 12;                // Rayleigh-Ritz Jacobi sweep cap
 constexpr int kSmemMaxP = 144;                   // G_X kept in shared memory up to this p
 constexpr int kRRMax = 32;                       // Rayleigh-Ritz matrices in smem up to this r
+constexpr int kClusterExt = 8;                   // eigenvalues added to close a cluster at the boundary
 constexpr int kEigMaxR = 48;                     // FP32 eig workspace in smem up to this r
 
 // ------------------------------------------------------------ helpers ----
@@ -306,10 +307,28 @@ __device__ void tri_solve_dd(int p, const dd* u0inv, const dd* u1, const dd* u2,
 
 // Orthonormalise vectors Z[i*p ..], i < rw, in order (classical Gram-Schmidt,
 // `passes` times), vectors over warps and rows over threads.
+// A vector that lies (to working precision) in the span of the earlier ones
+// -- inverse iteration with shifts inside a cluster closer than the shifts'
+// resolution -- is replaced by a fixed pseudo-random vector and
+// orthogonalised again, so the set stays a basis of the cluster's subspace.
+__device__ dd norm2_dd(const dd* z, int p, dd* red) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  dd nn = {0.f, 0.f};
+  for (int q = tid; q < p; q += kThreads) nn = dd_fma(z[q], z[q], nn);
+  nn = warp_sum_dd(nn);
+  if (lane == 0) red[warp] = nn;
+  __syncthreads();
+  dd t = red[0];
+  for (int w = 1; w < kWarps; ++w) t = dd_add(t, red[w]);
+  __syncthreads();
+  return t;
+}
+
 __device__ void cgs_dd(dd* Z, int rw, int p, int passes, dd* coef, dd* red, dd* sc) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = 0; i < rw; ++i) {
     dd* zi = Z + (int64_t)i * p;
+    const dd t0 = norm2_dd(zi, p, red);
     for (int pass = 0; pass < passes && i > 0; ++pass) {
       for (int j = warp; j < i; j += kWarps) {
         const dd* zj = Z + (int64_t)j * p;
@@ -326,16 +345,32 @@ __device__ void cgs_dd(dd* Z, int rw, int p, int passes, dd* coef, dd* red, dd* 
       }
       __syncthreads();
     }
-    dd nn = {0.f, 0.f};
-    for (int q = tid; q < p; q += kThreads) nn = dd_fma(zi[q], zi[q], nn);
-    nn = warp_sum_dd(nn);
-    if (lane == 0) red[warp] = nn;
-    __syncthreads();
-    if (tid == 0) {
-      dd t = red[0];
-      for (int w = 1; w < kWarps; ++w) t = dd_add(t, red[w]);
-      sc[3] = (t.hi > 0.f) ? dd_div(dd_make(1.f), dd_sqrt(t)) : dd{0.f, 0.f};
+    dd t = norm2_dd(zi, p, red);
+    if (i > 0 && !(t.hi > 1e-20f * t0.hi)) {   // collapsed: reseed and orthogonalise twice
+      for (int q = tid; q < p; q += kThreads) {
+        const unsigned hsh = (unsigned)(q + 1) * 2654435761u ^ (unsigned)(i + 1) * 40503u;
+        zi[q] = dd_make((float)((hsh >> 8) & 0xFFFFu) / 65536.f - 0.5f);
+      }
+      __syncthreads();
+      for (int pass = 0; pass < 2; ++pass) {
+        for (int j = warp; j < i; j += kWarps) {
+          const dd* zj = Z + (int64_t)j * p;
+          dd s = {0.f, 0.f};
+          for (int q = lane; q < p; q += 32) s = dd_fma(zj[q], zi[q], s);
+          s = warp_sum_dd(s);
+          if (lane == 0) coef[j] = s;
+        }
+        __syncthreads();
+        for (int q = tid; q < p; q += kThreads) {
+          dd s = zi[q];
+          for (int j = 0; j < i; ++j) s = dd_sub(s, dd_mul(coef[j], Z[(int64_t)j * p + q]));
+          zi[q] = s;
+        }
+        __syncthreads();
+      }
+      t = norm2_dd(zi, p, red);
     }
+    if (tid == 0) sc[3] = (t.hi > 0.f) ? dd_div(dd_make(1.f), dd_sqrt(t)) : dd{0.f, 0.f};
     __syncthreads();
     const dd inv = sc[3];
     for (int q = tid; q < p; q += kThreads) zi[q] = dd_mul(zi[q], inv);
@@ -666,6 +701,7 @@ struct SmemPlan {
   int a_in_smem;
   int rr_in_smem;
   int eig_in_smem;
+  int rr_dim;            // Rayleigh-Ritz size limit: r plus the cluster extension
   int64_t P, vec_units, rr_units, big_units;
 };
 
@@ -674,8 +710,9 @@ __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   s.P = (p + 3) & ~3;
   // d, e, vs, pv, wv, lam (df64) + part (256 df64) + d32, e2_32 (float) + 32 df64 scalars
   s.vec_units = 6 * s.P + 256 + s.P + 32;
-  s.rr_in_smem = (r <= kRRMax);
-  s.rr_units = s.rr_in_smem ? 2 * (int64_t)r * r : 0;
+  s.rr_dim = (r + kClusterExt < p) ? r + kClusterExt : p;
+  s.rr_in_smem = (s.rr_dim <= kRRMax);
+  s.rr_units = s.rr_in_smem ? 2 * (int64_t)s.rr_dim * s.rr_dim : 0;
   s.a_in_smem = (p <= kSmemMaxP);
   s.eig_in_smem = (r <= kEigMaxR);
   const int64_t a = s.a_in_smem ? (int64_t)p * p : 0;
@@ -711,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   float* e2_32 = d32 + P;
   dd* sc = reinterpret_cast<dd*>(e2_32 + P);
   dd* rrH = plan.rr_in_smem ? base + plan.vec_units : w.Y;
-  dd* rrR = rrH + (int64_t)a.r_req * a.r_req;
+  dd* rrR = rrH + (int64_t)plan.rr_dim * plan.rr_dim;
   dd* big = base + plan.vec_units + plan.rr_units;
   dd* A = plan.a_in_smem ? big : w.Ad;
   if (tid == 0) w.clk[0] = clock64();
@@ -783,7 +820,8 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   }
   __syncthreads();
   const float tnorm = sh_f[2];
-  for (int i = warp; i < rw; i += kWarps) {
+  // eigenvalue number i (descending) of T to FP32 resolution, one warp
+  auto multisect = [&](int i) -> float {
     const int target = p - 1 - i;
     float lo = sh_f[0], hi = sh_f[1];
     for (int round = 0; round < kMsRounds; ++round) {
@@ -797,9 +835,35 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
       if (f < 32) hi = xf;
       lo = (f == 0) ? lo : xp;
     }
-    if (lane == 0) lam[i] = dd_make(0.5f * (lo + hi));
+    return 0.5f * (lo + hi);
+  };
+  for (int i = warp; i < rw; i += kWarps) {
+    const float v = multisect(i);
+    if (lane == 0) lam[i] = dd_make(v);
   }
   __syncthreads();
+  // A cluster that the FP32 values cannot resolve and that straddles the last
+  // requested eigenvalue is taken in whole (up to kClusterExt more), so the
+  // df64 inverse iteration and Rayleigh-Ritz below see its whole subspace;
+  // only the rw largest Ritz pairs are kept. Eigenvalues under the rank
+  // floor are dropped later anyway and do not extend the set.
+  if (warp == 0) {
+    int rwe = rw;
+    const int cap = (rw + kClusterExt < p) ? rw + kClusterExt : p;
+    const float floor_v = lam[0].hi * (float)(kRankRtol * (double)p * kEps);
+    while (rwe < cap) {
+      const float last = lam[rwe - 1].hi;
+      if (!(last > floor_v)) break;
+      const float v = multisect(rwe);
+      if (fabsf(v - last) > 8.f * kEps32 * tnorm) break;
+      if (lane == 0) lam[rwe] = dd_make(v);
+      __syncwarp();
+      ++rwe;
+    }
+    if (lane == 0) sh_int[2] = rwe;
+  }
+  __syncthreads();
+  const int rwe = (rw > 0) ? sh_int[2] : 0;
   if (tid == 0) w.clk[3] = clock64();
 
   // ---- 3. df64 inverse iteration + Gram-Schmidt + Rayleigh-Ritz, twice:
@@ -809,7 +873,7 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   const float tiny = fmaxf(1e-13f * tnorm, FLT_MIN);
   for (int round = 0; round < 2; ++round) {
     const float sep = (round == 0) ? 2.f * kEps32 * tnorm : 1e-12f * tnorm;
-    for (int i = tid; i < rw; i += kThreads) {
+    for (int i = tid; i < rwe; i += kThreads) {
       dd* u0 = w.lu + (int64_t)i * 5 * p;
       dd shift = lam[i];
       for (int q = 0; q < i; ++q)    // (numerically) equal shifts: separate them slightly
@@ -823,14 +887,14 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
     }
     __syncthreads();
     for (int it = 0; it < kInvIters; ++it) {
-      for (int i = tid; i < rw; i += kThreads) {
+      for (int i = tid; i < rwe; i += kThreads) {
         dd* u0 = w.lu + (int64_t)i * 5 * p;
         tri_solve_dd(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, w.Z + (int64_t)i * p);
       }
       __syncthreads();
-      cgs_dd(w.Z, rw, p, (it + 1 == kInvIters) ? 2 : 1, coef, red, sc);
+      cgs_dd(w.Z, rwe, p, (it + 1 == kInvIters) ? 2 : 1, coef, red, sc);
     }
-    rayleigh_ritz(w.Z, rw, p, d, e, rrH, rrR, w.lu + (int64_t)rw * 5 * p, lam, sc, ord);
+    rayleigh_ritz(w.Z, rwe, p, d, e, rrH, rrR, w.lu + (int64_t)rwe * 5 * p, lam, sc, ord);
   }
   if (tid == 0) w.clk[4] = clock64();
 
@@ -1068,6 +1132,7 @@ ModesLayout modes_layout(int m) {
   L.clk = take(16);
   L.bamp = take(2 * p + 2);  // b (re, im) per mode, then [2p] = background index
   L.urec = take(p);          // 2p floats
+  L.Mu = take((p2 + 1) / 2);  // p x r floats (r <= p)
   L.total = o;
   return L;
 }

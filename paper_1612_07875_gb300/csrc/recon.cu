@@ -30,9 +30,16 @@ __global__ void __launch_bounds__(kThreads) recon_weights_kernel(ReconArgs a) {
   const int bg = (int)*a.bgi;
   for (int k = threadIdx.x; k < a.R; k += kThreads) {
     double cr = 0.0, ci = 0.0;
-    const bool use = k < re && (a.what == SDMD_RECON_MODES || k == bg);
+    const double lr = a.lamout[2 * k], li = a.lamout[2 * k + 1];
+    bool use = k < re;
+    if (a.what == SDMD_RECON_BACKGROUND || a.what == SDMD_RECON_FOREGROUND) {
+      use = use && k == bg;
+    } else if (a.what == SDMD_RECON_BACKGROUND_SLOW || a.what == SDMD_RECON_FOREGROUND_SLOW) {
+      const double m2 = lr * lr + li * li;    // |log lambda| with the principal log
+      const double lg = (m2 > 0.0) ? 0.5 * log(m2) : -INFINITY;
+      use = use && m2 > 0.0 && sqrt(lg * lg + atan2(li, lr) * atan2(li, lr)) <= a.slow_tol;
+    }
     if (use) {
-      const double lr = a.lamout[2 * k], li = a.lamout[2 * k + 1];
       double pr = 1.0, pi = 0.0;            // lambda^t (lambda^0 = 1)
       if (a.t != 0) {
         const double m2 = lr * lr + li * li;

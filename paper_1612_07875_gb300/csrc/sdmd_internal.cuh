@@ -134,6 +134,7 @@ struct ModesLayout {
   int64_t A, GXY, HV, d, e, lam, Z, V, Y, At, Hc, Qc, Wc, M, Mf, sig, lamout, tmp, lu, clk;
   int64_t bamp;   // r complex128 mode amplitudes b (Sec. 3.3), then the background index (as double)
   int64_t urec;   // p x 2 floats: reconstruction weights (hi, lo) of X' columns
+  int64_t Mu;     // p x r floats: V Sigma^-1 for the POD modes
   int64_t total;
 };
 ModesLayout modes_layout(int m);
@@ -155,11 +156,16 @@ struct PhiArgs {
   int* status;          // device status word
   int32_t tensor;       // 1: use the tensor-core kernel where it applies
   unsigned* sched;      // kPhiSchedWords zeroed words: per-pass tile counters, CTA-done counter
+  int32_t xoff = 1;     // first window column read: 1 = X' (Phi), 0 = X (POD modes)
+  int32_t real_out = 0; // 1: Mf is p x r real, phi is n x r FP32 (CUDA-core kernel)
 };
 constexpr int kPhiSchedPasses = 16;                 // mode passes of 16 (r <= 256)
 constexpr int kPhiSchedWords = kPhiSchedPasses + 1;
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
+// Mu[j][k] = V[k][j] / sigma_k (zero beyond the kept rank), then
+// U = X Mu with the real CUDA-core Phi kernel (xoff = 0, real_out = 1).
+cudaError_t launch_pod_modes(const PhiArgs& a, const double* V, const double* sig, float* Mu, cudaStream_t st);
 
 struct ReconArgs {
   const uint8_t* ring;
@@ -180,6 +186,7 @@ struct ReconArgs {
   float* urec;          // workspace: p x 2 floats
   float* out;           // n floats, 16-byte aligned
   int32_t xt_slot;      // physical slot of x_t (foreground), -1 otherwise
+  double slow_tol;      // SDMD_RECON_*_SLOW: modes with |log lambda| <= slow_tol
 };
 cudaError_t launch_reconstruct(const ReconArgs& a, cudaStream_t st);
 // tcgen05 kernel for uint8 windows; cudaErrorNotSupported outside its shapes

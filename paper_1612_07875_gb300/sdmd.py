@@ -35,6 +35,8 @@ SDMD_OPT_F32_FP64 = 4
 SDMD_RECON_MODES = 0
 SDMD_RECON_BACKGROUND = 1
 SDMD_RECON_FOREGROUND = 2
+SDMD_RECON_BACKGROUND_SLOW = 3
+SDMD_RECON_FOREGROUND_SLOW = 4
 
 SDMD_K_INGEST = 0
 SDMD_K_GRAM_ROW = 1
@@ -91,6 +93,8 @@ _SIGNATURES = {
     "sdmd_server_reset_stats": [_VP],
     "sdmd_server_clock_ms": [],
     "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
+    "sdmd_reconstruct_ex": [_VP, _I64, _I32, ctypes.c_double, _VP, _VP],
+    "sdmd_pod_modes": [_VP, _I32, _VP, _VP],
 }
 
 
@@ -315,6 +319,16 @@ def sdmd_amplitudes(h, b, stream=None, want_index=True):
 
 def sdmd_reconstruct(h, t, what, out, stream=None):
     _check(lib().sdmd_reconstruct(h, int(t), int(what), ptr(out), stream_handle(stream)), "sdmd_reconstruct")
+
+
+def sdmd_reconstruct_ex(h, t, what, tol, out, stream=None):
+    _check(lib().sdmd_reconstruct_ex(h, int(t), int(what), float(tol), ptr(out), stream_handle(stream)),
+           "sdmd_reconstruct_ex")
+
+
+def sdmd_pod_modes(h, r, U, stream=None):
+    """U = X V Sigma^-1 (n x r float32, column-major) of the last sdmd_modes."""
+    _check(lib().sdmd_pod_modes(h, int(r), ptr(U), stream_handle(stream)), "sdmd_pod_modes")
 
 
 def sdmd_status(h, stream=None):

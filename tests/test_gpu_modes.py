@@ -148,6 +148,32 @@ def test_rank_clamped_to_numerical_rank(cuda_device):
         S.sdmd_destroy(h)
 
 
+def test_cluster_at_the_requested_boundary(cuda_device):
+    # Five planted modes plus noise: the three noise eigenvalues of G_X lie
+    # closer together than FP32 resolves, so requesting 6, 7 or all 8 of them
+    # cuts a cluster; every requested eigenvalue and the kept rank must still
+    # match the FP64 eigenvalues of the same G (same-input parity).
+    ps = synth.PlantedStream(side=32, noise_var=1e-6, seed=synth.config_seed(1) + 9)
+    n, m = ps.n, 9
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    try:
+        for t in range(m + 3):
+            S.sdmd_push(h, torch.from_numpy(ps.snapshot(t)).to(cuda_device))
+        G = _gram(h, m, cuda_device, False)
+        ev = np.sort(np.linalg.eigvalsh(G[:-1, :-1]))[::-1]
+        for r in range(4, m):
+            rout = np.zeros(1, dtype=np.int32)
+            S.sdmd_modes(h, r, None, None, rout)
+            sig = np.zeros(r)
+            S.sdmd_svd(h, r, sig, None)
+            torch.cuda.synchronize()
+            assert int(rout[0]) == r
+            assert np.abs(sig ** 2 - ev[:r]).max() <= 1e-9 * ev[0], r
+            assert S.sdmd_status(h) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h)
+
+
 def test_rank_fp32_matches_oracle_on_same_gram(cuda_device):
     # FP32 data from a 3-dimensional subspace: G carries FP32 accumulation
     # rounding, which the rank rule (FP64 floor) does not remove; the kept
