@@ -34,7 +34,8 @@ from .gram import (gram_dense, cross_gram, gram_u8, gram_u8_cols, dot_u8, sparse
 from .dmd import (RANK_RTOL_FACTOR, numerical_rank, mos_svd, exact_dmd, dmd_from_gram,
                   DMDResult, pod_amplitudes, lstsq_amplitudes,
                   background_index, background_column, reconstruct, foreground_column,
-                  pod_modes, slow_modes, slow_background_column, slow_foreground_column)
+                  pod_modes, slow_modes, slow_background_column, slow_foreground_column,
+                  fourier_dmd, fourier_support, fourier_phi_rows)
 from .stream import StreamOracle
 
 __all__ = [
@@ -42,5 +43,6 @@ __all__ = [
     "gram_sparse", "densify_sparse", "RANK_RTOL_FACTOR", "numerical_rank",
     "mos_svd", "exact_dmd", "dmd_from_gram", "DMDResult", "pod_amplitudes", "lstsq_amplitudes",
     "background_index", "background_column", "reconstruct", "foreground_column", "pod_modes",
-    "slow_modes", "slow_background_column", "slow_foreground_column", "StreamOracle",
+    "slow_modes", "slow_background_column", "slow_foreground_column", "fourier_dmd",
+    "fourier_support", "fourier_phi_rows", "StreamOracle",
 ]

@@ -224,3 +224,34 @@ def slow_background_column(res, b, t, tol):
 def slow_foreground_column(W, res, b, t, tol):
     """x_t minus its slow-mode background (real part)."""
     return np.asarray(W)[:, t].astype(np.float64) - slow_background_column(res, b, t, tol).real
+
+
+def fourier_dmd(snaps, r):
+    """Exact DMD of a window of sparse Fourier-coefficient snapshots
+    [(idx, val), ...] (oldest first) without leaving coefficient space
+    (Sec. 3.5): G from sparse inner products (Parseval), then the small-matrix
+    part of Algorithms 1-2 (dmd_from_gram). Phi is not formed here; its rows
+    come from fourier_phi_rows."""
+    from .gram import gram_sparse
+    G = gram_sparse(snaps)
+    return dmd_from_gram(G[:-1, :-1], G[:-1, 1:], r)
+
+
+def fourier_support(snaps):
+    """Sorted union of the supports of X' (snapshots 1 .. c-1): the only
+    coefficients where Phi-hat = X'-hat M can be nonzero."""
+    return np.unique(np.concatenate([np.asarray(s[0], dtype=np.int64) for s in snaps[1:]]))
+
+
+def fourier_phi_rows(snaps, M, ks):
+    """Rows ks of Phi-hat = X'-hat M (Eq. 9 in coefficient space): row k is
+    sum_j xhat_{j+1}[k] M[j, :] over the X' snapshots holding coefficient k."""
+    ks = np.asarray(ks, dtype=np.int64)
+    out = np.zeros((ks.size, M.shape[1]), dtype=np.complex128)
+    for j, (idx, val) in enumerate(snaps[1:]):
+        idx = np.asarray(idx, dtype=np.int64)
+        pos = np.searchsorted(idx, ks)
+        pos = np.minimum(pos, idx.size - 1)
+        hit = idx[pos] == ks
+        out[hit] += np.asarray(val)[pos[hit]].astype(np.complex128)[:, None] * M[j][None, :]
+    return out

@@ -418,6 +418,32 @@ def test_pod_modes_are_the_left_singular_vectors():
     assert np.allclose(Uu.T @ Uu, np.eye(3), atol=1e-9)
 
 
+def test_fourier_domain_dmd_equals_physical_dmd():
+    # DMD in coefficient space (Sec. 3.5): the orthonormal transform leaves G,
+    # and so lambda and M, unchanged (Parseval), and Phi-hat maps to the
+    # physical-space modes by the inverse transform: Phi = ifft2(Phi-hat).
+    fs = synth.FourierSparseStream(side=16, nnz=40, churn=0.1, seed=5)
+    c, r = 9, 5
+    snaps = [fs.snapshot(t) for t in range(c)]
+    res_f = oracle.fourier_dmd(snaps, r)
+    Wp = np.stack([fs.physical(t) for t in range(c)], axis=1)
+    res_p = oracle.exact_dmd(Wp, r)
+    assert res_f.r == res_p.r == r
+    assert np.abs(res_f.lam - res_p.lam).max() < 1e-10
+    sup = oracle.fourier_support(snaps)
+    rows = oracle.fourier_phi_rows(snaps, res_f.M, sup)
+    Phi_hat = np.zeros((fs.N, r), dtype=np.complex128)
+    Phi_hat[sup] = rows
+    dense_hat = np.stack([fs.dense_coeffs(t) for t in range(1, c)], axis=1) @ res_f.M
+    assert np.allclose(Phi_hat, dense_hat, atol=1e-12)               # zero off the support
+    Phi_phys = np.stack([np.fft.ifft2(Phi_hat[:, k].reshape(16, 16), norm="ortho").reshape(-1)
+                         for k in range(r)], axis=1)
+    for k in range(r):                                                # same columns up to phase
+        a, b = Phi_phys[:, k], res_p.Phi[:, k]
+        ph = np.vdot(a, b) / abs(np.vdot(a, b))
+        assert np.linalg.norm(a * ph - b) <= 1e-8 * np.linalg.norm(b)
+
+
 def test_background_index_principal_log():
     lam = np.array([0.5, 1.0001 * cmath.exp(0.001j), 0.9 * cmath.exp(2j), -1.0])
     # |log(-1)| = pi: a unit-modulus but fast mode is not background
