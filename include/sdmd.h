@@ -262,9 +262,12 @@ SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
  *           |lambda| then by angle; entries beyond the kept rank are zero.
  *   r_out   receives the kept rank (int32), or NULL.
  * phi must be device memory (SDMD_ERR_ARG otherwise); lambda and r_out may
- * be device or host memory. Complex handles (SDMD_C64, SDMD_C64_SPARSE)
- * return SDMD_ERR_UNSUPPORTED: they provide the streaming Gram only. Needs c >= 3 snapshots (else
- * SDMD_ERR_NOT_READY). The eigensolvers have iteration caps; if one is
+ * be device or host memory. Complex handles (SDMD_C64, SDMD_C64_SPARSE):
+ * the same small algebra with complex V (FP64 Jacobi for the Hermitian G_X,
+ * A~ = vsi^H G_XY vsi), lambda / sigma / amplitudes as above; phi must be
+ * NULL (SDMD_ERR_UNSUPPORTED otherwise) -- Fourier-sparse handles form their
+ * modes in coefficient space with sdmd_fourier_modes. Needs c >= 3
+ * snapshots (else SDMD_ERR_NOT_READY). The eigensolvers have iteration caps; if one is
  * reached the call still completes and sdmd_status reports SDMD_ERR_RANK.
  */
 SDMD_API int sdmd_modes(sdmd_t h, int32_t r, void *phi, void *lambda, int32_t *r_out, void *stream);
@@ -294,8 +297,9 @@ SDMD_API int sdmd_sync(sdmd_t h, void *stream);
  * sdmd_svd -- singular values and right singular vectors of X from the last
  * sdmd_modes call (Sec. 2.1, Eqs. 3-4; Algorithm 1). sigma receives r doubles
  * (descending; zero beyond the kept rank), V receives (c-1) x r doubles,
- * column-major (vector k at V + k*(c-1)); either may be NULL. r must equal the
- * r of that sdmd_modes call.
+ * column-major (vector k at V + k*(c-1)); complex handles: (c-1) x r
+ * complex128 (interleaved re, im; vector k at V + 2*k*(c-1)). Either may be
+ * NULL. r must equal the r of that sdmd_modes call.
  */
 SDMD_API int sdmd_svd(sdmd_t h, int32_t r, double *sigma, double *V, void *stream);
 
@@ -345,6 +349,24 @@ SDMD_API int sdmd_reconstruct(sdmd_t h, int64_t t, int32_t what, float *out, voi
  * ignored by the other variants. Errors as sdmd_reconstruct.
  */
 SDMD_API int sdmd_reconstruct_ex(sdmd_t h, int64_t t, int32_t what, double tol, float *out, void *stream);
+
+/*
+ * sdmd_fourier_modes -- DMD modes of a Fourier-sparse window without leaving
+ * coefficient space (Sec. 3.5; Eq. 9 with X' in Fourier coefficients):
+ * Phi-hat = X'-hat M from the last sdmd_modes call, which is nonzero only on
+ * the union of the supports of X' (the c-1 newest resident snapshots). The
+ * compressed result: idx receives the union's coefficient indices in
+ * increasing order (int32), phi the matching rows of Phi-hat, complex64
+ * column-major with leading dimension cap (mode k at phi + 2*k*cap floats).
+ * *count (host) receives the union size. cap = 0 (idx and phi may be NULL)
+ * only counts; if the union exceeds cap the outputs are incomplete and the
+ * call returns SDMD_ERR_ARG with *count set. idx and phi are device memory.
+ * Waits for the stream. Fourier-sparse handles only (SDMD_ERR_UNSUPPORTED);
+ * SDMD_ERR_NOT_READY if no sdmd_modes call has run since the last push; r
+ * must equal that call's r.
+ */
+SDMD_API int sdmd_fourier_modes(sdmd_t h, int32_t r, int32_t *idx, void *phi, int64_t cap, int64_t *count,
+                                void *stream);
 
 /*
  * sdmd_pod_modes -- the POD (left singular) vectors of X from the last

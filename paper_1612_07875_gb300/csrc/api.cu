@@ -69,6 +69,8 @@ struct sdmd_s {
   int* idx_ring = nullptr;    // m x nnz_max indices
   float2* val_ring = nullptr; // m x nnz_max complex64 values
   int* tag = nullptr;         // n lookup tags
+  unsigned* fbits = nullptr;  // Fourier modes: support bitmap (allocated on first use)
+  unsigned long long* fprefix = nullptr;  // its popcount prefix, then the union size
   float2* tval = nullptr;     // n lookup values
   int stamp = 0;
   std::vector<int> nnz;       // entries per physical slot
@@ -200,6 +202,8 @@ void free_sparse(sdmd_s* h) {
   cudaFree(h->idx_ring);
   cudaFree(h->val_ring);
   cudaFree(h->tag);
+  cudaFree(h->fbits);
+  cudaFree(h->fprefix);
   cudaFree(h->tval);
 }
 
@@ -363,7 +367,7 @@ int sdmd_create_sparse(int64_t n, int32_t m, int32_t nnz_max, sdmd_t* out) {
   h->nnz_max = nnz_max;
   h->nnz.assign(m, 0);
   h->nblk = m * sparse_chunks(nnz_max);
-  const size_t ws_bytes = (size_t)modes_ws_doubles(2) * sizeof(double);
+  const size_t ws_bytes = (size_t)modes_ws_doubles(m) * sizeof(double);
   cudaError_t e = cudaSuccess;
   if (e == cudaSuccess) e = cudaMalloc(&h->idx_ring, (size_t)m * nnz_max * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&h->val_ring, (size_t)m * nnz_max * sizeof(float2));
@@ -733,8 +737,10 @@ int sdmd_gram(sdmd_t h, void* G, void* stream) {
 
 int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_modes: NULL handle");
-  if (h->dtype == SDMD_C64 || h->dtype == SDMD_C64_SPARSE)
-    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes: complex handles provide the streaming Gram only");
+  const bool cplx = (h->dtype == SDMD_C64 || h->dtype == SDMD_C64_SPARSE);
+  if (cplx && phi)
+    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes: complex handles return no dense Phi (Fourier-sparse handles: "
+                                      "sdmd_fourier_modes after this call)");
   const int c = resident(h);
   if (c < 3) return fail(SDMD_ERR_NOT_READY, "sdmd_modes: %d snapshots resident, need >= 3", c);
   if (r < 1 || r > h->m - 1) return fail(SDMD_ERR_ARG, "sdmd_modes: r=%d not in [1, %d]", r, h->m - 1);
@@ -755,7 +761,11 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
   a.r_dev = h->r_dev;
   {
     TraceScope ts(h, SDMD_K_MODES, st);
-    CK(launch_modes_small(a, st));
+    if (cplx) {
+      CK(launch_modes_complex(a, st));
+    } else {
+      CK(launch_modes_small(a, st));
+    }
   }
   const ModesLayout L = modes_layout(h->m);
   if (phi) {
@@ -895,7 +905,11 @@ int sdmd_svd(sdmd_t h, int32_t r, double* sigma, double* V, void* stream) {
     if (rc != SDMD_OK) return rc;
   }
   if (V) {
-    const int rc = copy_out(V, h->ws + L.V, (size_t)r * h->last_p * sizeof(double), st);
+    const bool cplx = (h->dtype == SDMD_C64 || h->dtype == SDMD_C64_SPARSE);
+    const int64_t p2 = (int64_t)(h->m - 1 > 1 ? h->m - 1 : 1) * (h->m - 1 > 1 ? h->m - 1 : 1);
+    // complex windows: V is complex (interleaved), the sixth array of the cx region
+    const double* src = cplx ? h->ws + L.cx + 10 * p2 : h->ws + L.V;
+    const int rc = copy_out(V, src, (size_t)r * h->last_p * sizeof(double) * (cplx ? 2 : 1), st);
     if (rc != SDMD_OK) return rc;
   }
   return SDMD_OK;
@@ -982,6 +996,59 @@ int sdmd_amplitudes(sdmd_t h, void* b, int32_t* bg_index, void* stream) {
     CK(cudaStreamSynchronize(st));
     *bg_index = (int32_t)v;
   }
+  return SDMD_OK;
+}
+
+int sdmd_fourier_modes(sdmd_t h, int32_t r, int32_t* idx, void* phi, int64_t cap, int64_t* count, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_fourier_modes: NULL handle");
+  if (h->dtype != SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_fourier_modes: Fourier-sparse handles only");
+  if (h->modes_count != h->count || h->last_r < 1)
+    return fail(SDMD_ERR_NOT_READY, "sdmd_fourier_modes: no sdmd_modes call since the last push");
+  if (r != h->last_r) return fail(SDMD_ERR_ARG, "sdmd_fourier_modes: r=%d differs from the last sdmd_modes r=%d", r, h->last_r);
+  if (!count || cap < 0) return fail(SDMD_ERR_ARG, "sdmd_fourier_modes: NULL count or negative cap");
+  if (cap > 0 && (!idx || !phi || ptr_kind(idx) != kDevice || ptr_kind(phi) != kDevice))
+    return fail(SDMD_ERR_ARG, "sdmd_fourier_modes: idx and phi must be device memory when cap > 0");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t nw = (h->n + 31) / 32;
+  if (!h->fbits) {
+    cudaError_t e = cudaMalloc(&h->fbits, (size_t)nw * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&h->fprefix, (size_t)nw * sizeof(unsigned long long) + 8);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SDMD_ERR_OOM, "sdmd_fourier_modes: bitmap allocation failed");
+    }
+  }
+  const ModesLayout L = modes_layout(h->m);
+  FourierPhiArgs fa;
+  fa.idx_ring = h->idx_ring;
+  fa.val_ring = h->val_ring;
+  fa.nnz_max = h->nnz_max;
+  for (int j = 0; j < SDMD_MAX_M; ++j) fa.nnz[j] = (j < h->m) ? h->nnz[j] : 0;
+  fa.m = h->cap;
+  fa.start = oldest_slot(h);
+  fa.p = h->last_p;
+  fa.r = r;
+  fa.R = h->last_r;
+  fa.Mf = reinterpret_cast<const float*>(h->ws + L.Mf);
+  fa.n = h->n;
+  fa.bitmap = h->fbits;
+  fa.prefix = h->fprefix;
+  fa.count = h->fprefix + nw;
+  fa.idx_out = idx;
+  fa.phi_out = static_cast<float2*>(phi);
+  fa.cap = cap;
+  {
+    TraceScope ts(h, SDMD_K_PHI, st);
+    CK(launch_fourier_phi(fa, cap > 0, st));
+  }
+  unsigned long long total = 0;
+  CK(cudaMemcpyAsync(&total, fa.count, sizeof(total), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *count = (int64_t)total;
+  if (cap > 0 && (int64_t)total > cap)
+    return fail(SDMD_ERR_ARG, "sdmd_fourier_modes: %lld coefficients in the support, cap %lld", (long long)total,
+                (long long)cap);
   return SDMD_OK;
 }
 

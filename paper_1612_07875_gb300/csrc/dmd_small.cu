@@ -1098,6 +1098,348 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   }
 }
 
+
+// ------------------------------------------------------- complex windows --
+// The small-matrix part of exact DMD for complex snapshots (dense complex64
+// or Fourier-sparse handles: G is Hermitian complex128), Algorithms 1-2 with
+// complex V: FP64 cyclic Jacobi for G_X (parallel round-robin rotations, a
+// bounded number of sweeps), rank rule, sigma, vsi = V Sigma^-1, A~ = vsi^H
+// G_XY vsi (FP64), eig(A~) by the FP32 complex Schur of phase 7 refined by
+// FP64 two-sided Rayleigh quotients, M = vsi W, amplitudes and the
+// background index as for real windows. Outputs go to the same workspace
+// arrays (sig, lamout, Mf, bamp, r_dev); V (complex) to the cx region.
+constexpr int kCThreads = 512;
+constexpr int kCWarps = kCThreads / 32;
+constexpr int kJacobiMaxSweeps = 40;
+
+struct C64d {
+  double re, im;
+};
+__device__ __forceinline__ C64d zmul(C64d a, C64d b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ C64d zcmul(C64d a, C64d b) {   // conj(a) b
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+
+__device__ double block_sum_c(double v, double* red) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kCWarps; ++w) t += red[w];
+  __syncthreads();
+  return t;
+}
+
+__global__ void __launch_bounds__(kCThreads, 1) modes_complex_kernel(ModesArgs a, ModesLayout L) {
+  __shared__ double red[kCWarps];
+  __shared__ double rc[SDMD_MAX_M / 2], rs[SDMD_MAX_M / 2], rpr[SDMD_MAX_M / 2], rpi[SDMD_MAX_M / 2];
+  __shared__ int ri[SDMD_MAX_M / 2], rj[SDMD_MAX_M / 2];
+  __shared__ int ord[SDMD_MAX_M];
+  __shared__ double lam_s[SDMD_MAX_M];
+  __shared__ float cs[SDMD_MAX_M];
+  __shared__ CF sn[SDMD_MAX_M];
+  __shared__ int sh_int[4];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m = a.m, p = a.c - 1;
+  const int R = a.r_req;
+  double* ws = a.ws;
+  C64d* Ac = reinterpret_cast<C64d*>(ws + L.cx);   // p x p, row-major (later G_XY vsi)
+  C64d* Vc = Ac + (int64_t)p * p;                  // p x p: V[i][k], column k = eigenvector k
+  C64d* Bc = Vc + (int64_t)p * p;                  // G_XY
+  C64d* At = Bc + (int64_t)p * p;                  // re x re
+  C64d* vsi = At + (int64_t)p * p;                 // p x R
+  C64d* Vo = vsi + (int64_t)p * p;                 // R vectors of length p (sorted V)
+  const double2* G = static_cast<const double2*>(a.G);
+
+  // ---- 0. scale by a power of two (largest diagonal), gather G_X, G_XY
+  if (warp == 0) {
+    int ex = -1000;
+    for (int i = lane; i < p; i += 32) {
+      const int si = (a.start + i) % m;
+      const double g = G[(int64_t)si * m + si].x;
+      const int bits = (__double2hiint(g) >> 20) & 0x7ff;
+      ex = max(ex, (g > 0.0 && bits > 0) ? bits - 1023 : -1000);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+    if (lane == 0) sh_int[0] = (ex == -1000) ? 0 : ex + 1;
+  }
+  __syncthreads();
+  const int s_exp = sh_int[0];
+  for (int idx = tid; idx < p * p; idx += kCThreads) {
+    const int i = idx / p, j = idx - i * p;
+    const int si = (a.start + i) % m, sj = (a.start + j) % m, sj1 = (a.start + j + 1) % m;
+    const double2 gx = G[(int64_t)si * m + sj], gxy = G[(int64_t)si * m + sj1];
+    Ac[idx] = {ldexp(gx.x, -s_exp), (i == j) ? 0.0 : ldexp(gx.y, -s_exp)};
+    Bc[idx] = {ldexp(gxy.x, -s_exp), ldexp(gxy.y, -s_exp)};
+    Vc[idx] = {(i == j) ? 1.0 : 0.0, 0.0};
+  }
+  __syncthreads();
+
+  // ---- 1. cyclic Jacobi: A <- J^H A J, V <- V J, J = diag(1, e^{-i phi}) R
+  //         with R the real rotation that zeroes |a_ij| (round-robin pairs,
+  //         all disjoint pairs of a step at once)
+  const int P2 = p + (p & 1);
+  const int npairs = P2 / 2;
+  for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int idx = tid; idx < p * p; idx += kCThreads) {
+      const C64d v = Ac[idx];
+      const double q = v.re * v.re + v.im * v.im;
+      tot += q;
+      if (idx / p != idx % p) off += q;
+    }
+    off = block_sum_c(off, red);
+    tot = block_sum_c(tot, red);
+    if (!(off > 1e-30 * tot)) break;
+    for (int step = 0; step < P2 - 1; ++step) {
+      if (tid < npairs) {
+        int u = (tid == 0) ? P2 - 1 : (step + tid) % (P2 - 1);
+        int v = (step - tid + (P2 - 1)) % (P2 - 1);
+        if (tid == 0) v = step;
+        const int i = min(u, v), j = max(u, v);
+        double c = 1.0, sv = 0.0, pr = 1.0, pim = 0.0;
+        if (j < p) {
+          const C64d b = Ac[(int64_t)i * p + j];
+          const double ab = hypot(b.re, b.im);
+          if (ab > 0.0) {
+            const double al = Ac[(int64_t)i * p + i].re, de = Ac[(int64_t)j * p + j].re;
+            const double tau = (de - al) / (2.0 * ab);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sv = t * c;
+            pr = b.re / ab;                   // e^{i phi}
+            pim = b.im / ab;
+          }
+        }
+        ri[tid] = i;
+        rj[tid] = (j < p) ? j : -1;
+        rc[tid] = c;
+        rs[tid] = sv;
+        rpr[tid] = pr;
+        rpi[tid] = pim;
+      }
+      __syncthreads();
+      // columns: (a_ki, a_kj) <- (a_ki c - a_kj s e^{-i phi}, a_ki s + a_kj c e^{-i phi}); also V
+      for (int w = tid; w < 2 * npairs * p; w += kCThreads) {
+        const int which = w / (npairs * p);
+        const int rem = w - which * npairs * p;
+        const int q = rem / p, k = rem - q * p;
+        const int j = rj[q];
+        if (j < 0) continue;
+        const int i = ri[q];
+        C64d* X = which ? Vc : Ac;
+        const C64d xi = X[(int64_t)k * p + i], xj = X[(int64_t)k * p + j];
+        const C64d em = {rpr[q], -rpi[q]};
+        const C64d xje = zmul(xj, em);
+        const double c = rc[q], sv = rs[q];
+        X[(int64_t)k * p + i] = {c * xi.re - sv * xje.re, c * xi.im - sv * xje.im};
+        X[(int64_t)k * p + j] = {sv * xi.re + c * xje.re, sv * xi.im + c * xje.im};
+      }
+      __syncthreads();
+      // rows: (a_ik, a_jk) <- (c a_ik - s e^{i phi} a_jk, s a_ik + c e^{i phi} a_jk)
+      for (int w = tid; w < npairs * p; w += kCThreads) {
+        const int q = w / p, k = w - q * p;
+        const int j = rj[q];
+        if (j < 0) continue;
+        const int i = ri[q];
+        const C64d xi = Ac[(int64_t)i * p + k], xj = Ac[(int64_t)j * p + k];
+        const C64d ep = {rpr[q], rpi[q]};
+        const C64d xje = zmul(ep, xj);
+        const double c = rc[q], sv = rs[q];
+        Ac[(int64_t)i * p + k] = {c * xi.re - sv * xje.re, c * xi.im - sv * xje.im};
+        Ac[(int64_t)j * p + k] = {sv * xi.re + c * xje.re, sv * xi.im + c * xje.im};
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- 2. eigenvalues (real diagonal) sorted descending, rank, sigma, V, vsi
+  for (int i = tid; i < p; i += kCThreads) lam_s[i] = Ac[(int64_t)i * p + i].re;
+  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < p; ++i) ord[i] = i;
+    for (int i = 0; i < p; ++i) {
+      int best = i;
+      for (int q = i + 1; q < p; ++q)
+        if (lam_s[ord[q]] > lam_s[ord[best]]) best = q;
+      const int t = ord[i];
+      ord[i] = ord[best];
+      ord[best] = t;
+    }
+    const int rw = min(R, p);
+    int k = 0;
+    const double l0 = lam_s[ord[0]];
+    if (l0 > 0.0) {
+      const double thr = l0 * kRankRtol * (double)p * kEps;
+      while (k < rw && lam_s[ord[k]] > thr) ++k;
+    }
+    sh_int[1] = k;
+  }
+  __syncthreads();
+  const int re = sh_int[1];
+  for (int k = tid; k < R; k += kCThreads)
+    ws[L.sig + k] = (k < re) ? sqrt(ldexp(lam_s[ord[k]], s_exp)) : 0.0;
+  for (int idx = tid; idx < R * p; idx += kCThreads) {
+    const int k = idx / p, i = idx - k * p;
+    const C64d v = (k < re) ? Vc[(int64_t)i * p + ord[k]] : C64d{0.0, 0.0};
+    Vo[idx] = v;
+    const double inv = (k < re) ? 1.0 / sqrt(lam_s[ord[k]]) : 0.0;
+    vsi[(int64_t)i * R + k] = {v.re * inv, v.im * inv};
+  }
+  __syncthreads();
+
+  // ---- 3. A~ = vsi^H (G_XY vsi)
+  for (int idx = tid; idx < p * re; idx += kCThreads) {
+    const int i = idx / re, k = idx - i * re;
+    C64d s = {0.0, 0.0};
+    for (int j = 0; j < p; ++j) {
+      const C64d t = zmul(Bc[(int64_t)i * p + j], vsi[(int64_t)j * R + k]);
+      s.re += t.re;
+      s.im += t.im;
+    }
+    Ac[(int64_t)i * R + k] = s;                  // Y = G_XY vsi, p x re (stride R)
+  }
+  __syncthreads();
+  CF* Hc = reinterpret_cast<CF*>(ws + L.lu);
+  CF* Qc = Hc + re * re;
+  CF* Wc = Qc + re * re;
+  CF* Uc = Wc + re * re;
+  CF* yc = Uc + re * re;
+  for (int idx = tid; idx < re * re; idx += kCThreads) {
+    const int k = idx / re, l = idx - k * re;
+    C64d s = {0.0, 0.0};
+    for (int i = 0; i < p; ++i) {
+      const C64d t = zcmul(vsi[(int64_t)i * R + k], Ac[(int64_t)i * R + l]);
+      s.re += t.re;
+      s.im += t.im;
+    }
+    At[idx] = s;
+    Hc[idx] = {(float)s.re, (float)s.im};
+  }
+  __syncthreads();
+
+  // ---- 4. eig(A~): FP32 complex Schur, then FP64 two-sided Rayleigh quotients
+  if (warp == 0 && re > 0) {
+    const bool ok = warp_eig32(Hc, Qc, Wc, Uc, yc, re, cs, sn);
+    if (!ok && lane == 0) atomicOr(a.status, kDevRank);
+  }
+  __syncthreads();
+  double* lam_tmp = ws + L.Y;
+  for (int k = tid; k < re; k += kCThreads) {
+    C64d num = {0.0, 0.0}, den = {0.0, 0.0};
+    for (int i = 0; i < re; ++i) {
+      C64d aw = {0.0, 0.0};
+      for (int j = 0; j < re; ++j) {
+        const CF wj = Wc[j * re + k];
+        const C64d t = zmul(At[i * re + j], C64d{wj.re, wj.im});
+        aw.re += t.re;
+        aw.im += t.im;
+      }
+      const CF ui = Uc[i * re + k], wi = Wc[i * re + k];
+      const C64d un = zcmul(C64d{ui.re, ui.im}, aw);
+      const C64d ud = zcmul(C64d{ui.re, ui.im}, C64d{wi.re, wi.im});
+      num.re += un.re;
+      num.im += un.im;
+      den.re += ud.re;
+      den.im += ud.im;
+    }
+    const double q = den.re * den.re + den.im * den.im;
+    lam_tmp[2 * k] = (q > 0.0) ? (num.re * den.re + num.im * den.im) / q : 0.0;
+    lam_tmp[2 * k + 1] = (q > 0.0) ? (num.im * den.re - num.re * den.im) / q : 0.0;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int k = 0; k < re; ++k) ord[k] = k;
+    for (int k = 0; k < re; ++k) {
+      int best = k;
+      for (int q = k + 1; q < re; ++q) {
+        const double br = lam_tmp[2 * ord[best]], bi = lam_tmp[2 * ord[best] + 1];
+        const double qr = lam_tmp[2 * ord[q]], qi = lam_tmp[2 * ord[q] + 1];
+        const double mb = br * br + bi * bi, mq = qr * qr + qi * qi;
+        if (mq > mb || (mq == mb && atan2(qi, qr) < atan2(bi, br))) best = q;
+      }
+      const int t = ord[k];
+      ord[k] = ord[best];
+      ord[best] = t;
+    }
+  }
+  __syncthreads();
+  for (int k = tid; k < R; k += kCThreads) {
+    ws[L.lamout + 2 * k] = (k < re) ? lam_tmp[2 * ord[k]] : 0.0;
+    ws[L.lamout + 2 * k + 1] = (k < re) ? lam_tmp[2 * ord[k] + 1] : 0.0;
+  }
+  __syncthreads();
+
+  // ---- 5. M = vsi W, FP32 out in true units (vsi carries 2^{s/2})
+  float* Mf = reinterpret_cast<float*>(ws + L.Mf);
+  const double unscale = exp2(-0.5 * s_exp);
+  for (int idx = tid; idx < p * R; idx += kCThreads) {
+    const int row = idx / R, k = idx - row * R;
+    C64d s = {0.0, 0.0};
+    if (k < re) {
+      const int kk = ord[k];
+      for (int l = 0; l < re; ++l) {
+        const CF wv = Wc[l * re + kk];
+        const C64d t = zmul(vsi[(int64_t)row * R + l], C64d{wv.re, wv.im});
+        s.re += t.re;
+        s.im += t.im;
+      }
+    }
+    Mf[2 * idx] = (float)(s.re * unscale);
+    Mf[2 * idx + 1] = (float)(s.im * unscale);
+  }
+
+  // ---- 6. amplitudes b_k = u_k^H alpha_1 / (lambda_k u_k^H w_k), alpha_1[i] =
+  //         sigma_i conj(V[0][i]); background index argmin |log lambda|
+  for (int k = tid; k < R; k += kCThreads) {
+    double br = 0.0, bi = 0.0;
+    if (k < re) {
+      const int kk = ord[k];
+      C64d nu = {0.0, 0.0}, de = {0.0, 0.0};
+      for (int i = 0; i < re; ++i) {
+        const CF u = Uc[i * re + kk], wv = Wc[i * re + kk];
+        const double sg = ws[L.sig + i];
+        const C64d a1 = {sg * Vo[(int64_t)i * p].re, -sg * Vo[(int64_t)i * p].im};
+        const C64d t1 = zcmul(C64d{u.re, u.im}, a1), t2 = zcmul(C64d{u.re, u.im}, C64d{wv.re, wv.im});
+        nu.re += t1.re;
+        nu.im += t1.im;
+        de.re += t2.re;
+        de.im += t2.im;
+      }
+      const double lr = ws[L.lamout + 2 * k], li = ws[L.lamout + 2 * k + 1];
+      const C64d e = zmul(C64d{lr, li}, de);
+      const double q = e.re * e.re + e.im * e.im;
+      if (q > 0.0) {
+        br = (nu.re * e.re + nu.im * e.im) / q;
+        bi = (nu.im * e.re - nu.re * e.im) / q;
+      } else {
+        atomicOr(a.status, kDevRank);
+      }
+    }
+    ws[L.bamp + 2 * k] = br;
+    ws[L.bamp + 2 * k + 1] = bi;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int best = -1;
+    double bv = 0.0;
+    for (int k = 0; k < re; ++k) {
+      const double lr = ws[L.lamout + 2 * k], li = ws[L.lamout + 2 * k + 1];
+      const double lm = 0.5 * log(lr * lr + li * li), th = atan2(li, lr);
+      const double v = lm * lm + th * th;
+      if (best < 0 || v < bv) {
+        best = k;
+        bv = v;
+      }
+    }
+    ws[L.bamp + 2 * (a.ws_m - 1 > 1 ? a.ws_m - 1 : 1)] = (double)best;
+    *a.r_dev = re;
+  }
+}
+
 }  // namespace
 
 ModesLayout modes_layout(int m) {
@@ -1133,6 +1475,7 @@ ModesLayout modes_layout(int m) {
   L.bamp = take(2 * p + 2);  // b (re, im) per mode, then [2p] = background index
   L.urec = take(p);          // 2p floats
   L.Mu = take((p2 + 1) / 2);  // p x r floats (r <= p)
+  L.cx = take(12 * p2 + 64);  // complex windows: G_X, V, G_XY, A~, vsi, sorted V (complex128, p x p each)
   L.total = o;
   return L;
 }
@@ -1150,6 +1493,12 @@ cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
     attr_bytes = bytes;
   }
   modes_small_kernel<<<1, kThreads, bytes, st>>>(a, modes_layout(a.ws_m));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_modes_complex(const ModesArgs& a, cudaStream_t st) {
+  if (a.c - 1 > SDMD_MAX_M - 1) return cudaErrorNotSupported;
+  modes_complex_kernel<<<1, kCThreads, 0, st>>>(a, modes_layout(a.ws_m));
   return cudaGetLastError();
 }
 

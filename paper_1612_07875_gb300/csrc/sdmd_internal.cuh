@@ -135,11 +135,15 @@ struct ModesLayout {
   int64_t bamp;   // r complex128 mode amplitudes b (Sec. 3.3), then the background index (as double)
   int64_t urec;   // p x 2 floats: reconstruction weights (hi, lo) of X' columns
   int64_t Mu;     // p x r floats: V Sigma^-1 for the POD modes
+  int64_t cx;     // complex windows: six p x p complex128 arrays (V of sdmd_svd at the sixth)
   int64_t total;
 };
 ModesLayout modes_layout(int m);
 
 cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st);
+// The same outputs for complex windows (G complex128 Hermitian): FP64 Jacobi
+// for G_X, complex A~, W, M and amplitudes.
+cudaError_t launch_modes_complex(const ModesArgs& a, cudaStream_t st);
 
 struct PhiArgs {
   const uint8_t* ring;
@@ -214,6 +218,29 @@ int sparse_chunks(int nnz);
 cudaError_t launch_sparse_scatter(const int* idx, const float2* val, int nnz, int64_t n, int stamp, int* tag,
                                   float2* tval, int* status, cudaStream_t st);
 cudaError_t launch_sparse_row(const SparseRowArgs& a, cudaStream_t st);
+
+// Modes of a Fourier-sparse window in coefficient space (compressed Phi-hat).
+struct FourierPhiArgs {
+  const int* idx_ring;       // slot j's sorted indices at idx_ring + j * nnz_max
+  const float2* val_ring;    // slot j's complex64 values
+  int nnz_max;
+  int nnz[SDMD_MAX_M];       // entries per physical slot
+  int m;                     // ring modulus
+  int start;                 // physical slot of the oldest resident snapshot
+  int p;                     // X' columns: slots start + 1 .. start + p
+  int r, R;                  // modes to write; stride of Mf (modes of the modes call)
+  const float* Mf;           // p x 2R (re, im) of M = V Sigma^-1 W
+  int64_t n;                 // coefficients per snapshot
+  unsigned* bitmap;          // ceil(n / 32) words
+  unsigned long long* prefix;// ceil(n / 32) exclusive popcount prefix
+  unsigned long long* count; // union size
+  int* idx_out;              // cap sorted coefficient indices
+  float2* phi_out;           // cap x r complex64, column-major (leading dimension cap)
+  int64_t cap;
+};
+// Marks and counts the union support; with `rows`, also writes idx_out and
+// phi_out (the first min(count, cap) entries).
+cudaError_t launch_fourier_phi(const FourierPhiArgs& a, bool rows, cudaStream_t st);
 
 // Records `msg` as this thread's sdmd_last_error() text; returns `code`.
 int set_last_error(int code, const char* msg);

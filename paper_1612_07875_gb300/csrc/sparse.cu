@@ -112,6 +112,109 @@ __global__ void __launch_bounds__(kThreads) sparse_row_kernel(SparseRowArgs a) {
   if (threadIdx.x == 0) *a.ticket = 0u;
 }
 
+
+// --------------------------------------------- modes in coefficient space --
+// Phi-hat = X'-hat M (Eq. 9 with the snapshots in Fourier coefficient space,
+// Sec. 3.5): column j of X'-hat is sparse, so Phi-hat is nonzero only on the
+// union of the X' supports. The union is marked in a bitmap, counted with an
+// exclusive popcount prefix and compacted (sorted coefficient indices); each
+// union coefficient then gathers its value from every X' slot by binary
+// search in the slot's sorted index list and accumulates the r mode values.
+
+__global__ void fphi_mark_kernel(FourierPhiArgs a) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = (int)(t / a.nnz_max), e = (int)(t - (int64_t)j * a.nnz_max);
+  if (j >= a.p) return;
+  const int slot = (a.start + 1 + j) % a.m;
+  if (e >= a.nnz[slot]) return;
+  const int k = a.idx_ring[(int64_t)slot * a.nnz_max + e];
+  if (k < 0 || (int64_t)k >= a.n) return;             // rejected at push (status word)
+  atomicOr(a.bitmap + (k >> 5), 1u << (k & 31));
+}
+
+constexpr int kScanThreads = 1024;
+
+__global__ void __launch_bounds__(kScanThreads) fphi_scan_kernel(FourierPhiArgs a) {
+  __shared__ unsigned long long part[kScanThreads];
+  const int64_t nw = (a.n + 31) / 32;
+  const int64_t per = (nw + kScanThreads - 1) / kScanThreads;
+  const int64_t w0 = (int64_t)threadIdx.x * per, w1 = (w0 + per < nw) ? w0 + per : nw;
+  unsigned long long s = 0;
+  for (int64_t w = w0; w < w1; ++w) s += (unsigned)__popc(a.bitmap[w]);
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {      // inclusive scan of the thread sums
+    const unsigned long long v = (threadIdx.x >= (unsigned)o) ? part[threadIdx.x - o] : 0ull;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  unsigned long long run = (threadIdx.x > 0) ? part[threadIdx.x - 1] : 0ull;
+  for (int64_t w = w0; w < w1; ++w) {
+    a.prefix[w] = run;
+    run += (unsigned)__popc(a.bitmap[w]);
+  }
+  if (threadIdx.x == kScanThreads - 1) *a.count = part[kScanThreads - 1];
+}
+
+__global__ void fphi_compact_kernel(FourierPhiArgs a) {
+  const int64_t nw = (a.n + 31) / 32;
+  for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += (int64_t)gridDim.x * blockDim.x) {
+    unsigned bits = a.bitmap[w];
+    unsigned long long pos = a.prefix[w];
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      if (pos < (unsigned long long)a.cap) a.idx_out[pos] = (int)(w * 32 + b);
+      ++pos;
+      bits &= bits - 1u;
+    }
+  }
+}
+
+constexpr int kFModes = 16;   // modes per thread (grid.y tiles the modes)
+
+__global__ void __launch_bounds__(256) fphi_rows_kernel(FourierPhiArgs a) {
+  __shared__ float2 Ms[SDMD_MAX_M * kFModes];
+  const int k0 = blockIdx.y * kFModes;
+  const int kt = (a.r - k0 < kFModes) ? a.r - k0 : kFModes;
+  for (int idx = threadIdx.x; idx < a.p * kFModes; idx += blockDim.x) {
+    const int j = idx / kFModes, q = idx - j * kFModes;
+    Ms[idx] = (q < kt) ? make_float2(a.Mf[(int64_t)j * 2 * a.R + 2 * (k0 + q)], a.Mf[(int64_t)j * 2 * a.R + 2 * (k0 + q) + 1])
+                       : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  const unsigned long long total = *a.count;
+  const int64_t lim = (total < (unsigned long long)a.cap) ? (int64_t)total : a.cap;
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < lim; u += (int64_t)gridDim.x * blockDim.x) {
+    const int k = a.idx_out[u];
+    float2 acc[kFModes];
+#pragma unroll
+    for (int q = 0; q < kFModes; ++q) acc[q] = make_float2(0.f, 0.f);
+    for (int j = 0; j < a.p; ++j) {
+      const int slot = (a.start + 1 + j) % a.m;
+      const int* list = a.idx_ring + (int64_t)slot * a.nnz_max;
+      int lo = 0, hi = a.nnz[slot];                    // first entry >= k
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(list + mid) < k) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo < a.nnz[slot] && __ldg(list + lo) == k) {
+        const float2 v = __ldg(a.val_ring + (int64_t)slot * a.nnz_max + lo);
+        const float2* mr = Ms + j * kFModes;
+#pragma unroll
+        for (int q = 0; q < kFModes; ++q) {
+          acc[q].x = fmaf(v.x, mr[q].x, fmaf(-v.y, mr[q].y, acc[q].x));
+          acc[q].y = fmaf(v.x, mr[q].y, fmaf(v.y, mr[q].x, acc[q].y));
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kFModes; ++q)
+      if (q < kt) a.phi_out[(int64_t)(k0 + q) * a.cap + u] = acc[q];
+  }
+}
+
 }  // namespace
 
 int sparse_chunks(int nnz) { return nnz > 0 ? (nnz + kChunk - 1) / kChunk : 1; }
@@ -126,6 +229,30 @@ cudaError_t launch_sparse_scatter(const int* idx, const float2* val, int nnz, in
 
 cudaError_t launch_sparse_row(const SparseRowArgs& a, cudaStream_t st) {
   sparse_row_kernel<<<a.nblk, kThreads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_phi(const FourierPhiArgs& a, bool rows, cudaStream_t st) {
+  if (a.p < 1 || a.p > SDMD_MAX_M - 1) return cudaErrorNotSupported;
+  const int64_t nw = (a.n + 31) / 32;
+  cudaError_t e = cudaMemsetAsync(a.bitmap, 0, (size_t)nw * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const int64_t marks = (int64_t)a.p * a.nnz_max;
+  fphi_mark_kernel<<<(unsigned)((marks + 255) / 256), 256, 0, st>>>(a);
+  fphi_scan_kernel<<<1, kScanThreads, 0, st>>>(a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || !rows) return e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (sms < 1) sms = 1;
+  int64_t cb = (nw + 255) / 256;
+  if (cb > (int64_t)sms * 8) cb = (int64_t)sms * 8;
+  fphi_compact_kernel<<<(unsigned)(cb > 0 ? cb : 1), 256, 0, st>>>(a);
+  int64_t rb = (a.cap + 255) / 256;
+  if (rb > (int64_t)sms * 8) rb = (int64_t)sms * 8;
+  dim3 grid((unsigned)(rb > 0 ? rb : 1), (unsigned)((a.r + kFModes - 1) / kFModes));
+  fphi_rows_kernel<<<grid, 256, 0, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ _SIGNATURES = {
     "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
     "sdmd_reconstruct_ex": [_VP, _I64, _I32, ctypes.c_double, _VP, _VP],
     "sdmd_pod_modes": [_VP, _I32, _VP, _VP],
+    "sdmd_fourier_modes": [_VP, _I32, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP],
 }
 
 
@@ -324,6 +325,15 @@ def sdmd_reconstruct(h, t, what, out, stream=None):
 def sdmd_reconstruct_ex(h, t, what, tol, out, stream=None):
     _check(lib().sdmd_reconstruct_ex(h, int(t), int(what), float(tol), ptr(out), stream_handle(stream)),
            "sdmd_reconstruct_ex")
+
+
+def sdmd_fourier_modes(h, r, idx=None, phi=None, cap=0, stream=None):
+    """Compressed Phi-hat of the last sdmd_modes on a Fourier-sparse handle;
+    returns the union size (cap = 0: count only)."""
+    cnt = _I64()
+    _check(lib().sdmd_fourier_modes(h, int(r), ptr(idx), ptr(phi), int(cap), ctypes.byref(cnt), stream_handle(stream)),
+           "sdmd_fourier_modes")
+    return cnt.value
 
 
 def sdmd_pod_modes(h, r, U, stream=None):
