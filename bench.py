@@ -268,6 +268,19 @@ def measure_isolated(S, h, frames, t0, stream, phi, n, steps=8):
         us = 1e3 * ev0.elapsed_time(ev1) / steps
         out[name] = {"launches": 2 * steps, "us": us,
                      "GB/s": ((M_WIN - 1) * n + 4 * n + extra) / (us * 1e-6) / 1e9}
+    # POD modes U = X V Sigma^-1 (SVD-only output), n x r FP32, one pass over X
+    U = torch.empty(R_MODES, n, dtype=torch.float32, device=frames.device)
+    with torch.cuda.stream(stream):
+        S.sdmd_pod_modes(h, R_MODES, U, sh)
+        ev0.record(stream)
+        for _ in range(steps):
+            S.sdmd_pod_modes(h, R_MODES, U, sh)
+        ev1.record(stream)
+    stream.synchronize()
+    us = 1e3 * ev0.elapsed_time(ev1) / steps
+    out["pod_modes"] = {"launches": 2 * steps, "us": us,
+                        "GB/s": ((M_WIN - 1) * n + 4 * n * R_MODES) / (us * 1e-6) / 1e9}
+    del U
     return out
 
 
@@ -449,6 +462,27 @@ def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
         tot = e0.elapsed_time(e1)
         rl, rms = S.sdmd_trace_read(h, S.SDMD_K_GRAM_ROW)
         S.sdmd_trace(h, False)
+        # f3: DMD in coefficient space -- complex small-matrix DMD, then the
+        # compressed modes on the union support of X'
+        r = 10
+        fm = {}
+        for rep in range(4):
+            e0.record(stream)
+            S.sdmd_modes(h, r, None, None, None, sh)
+            e1.record(stream)
+            stream.synchronize()
+            t_modes = e0.elapsed_time(e1)
+            cnt = S.sdmd_fourier_modes(h, r, stream=sh)
+            if rep == 0:
+                idx = torch.empty(cnt, dtype=torch.int32, device=dev)
+                phi = torch.empty(r, cnt, 2, dtype=torch.float32, device=dev)
+            e0.record(stream)
+            S.sdmd_fourier_modes(h, r, idx, phi, cnt, sh)
+            e1.record(stream)
+            stream.synchronize()
+            if rep:
+                fm.setdefault("modes_ms", []).append(t_modes)
+                fm.setdefault("fourier_modes_ms", []).append(e0.elapsed_time(e1))
         ok = S.sdmd_status(h, sh) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
@@ -457,7 +491,13 @@ def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
             "snapshots/s": pushes / (tot * 1e-3), "push_us": 1e3 * tot / pushes,
             "row_kernels_us": 1e3 * rms / max(rl, 1),
             "algorithmic_bytes_per_push": m * nnz * 12 + nnz * 12, "status_ok": ok,
-            "bound": "latency / L2 (lookup table 12 MB and window 8 MB are L2-resident)"}
+            "bound": "latency / L2 (lookup table 12 MB and window 8 MB are L2-resident)",
+            "fourier_dmd": {"r": r, "modes_complex_ms": float(np.mean(fm["modes_ms"])),
+                            "fourier_modes_ms": float(np.mean(fm["fourier_modes_ms"])),
+                            "support": cnt, "compressed_output_bytes": cnt * (4 + 8 * r),
+                            "dense_output_bytes": fs.N * 8 * r,
+                            "note": "sdmd_modes (FP64 Jacobi + complex A~) and sdmd_fourier_modes "
+                                    "(support bitmap, prefix, compaction, gathers) on the same window"}}
 
 
 def measure_serving(S, synth, dev, seconds, capacity_ticks=12):
