@@ -430,7 +430,8 @@ enum {
     SDMD_K_MODES = 2,     /* FP64 eigensolvers / small products (one CTA)     */
     SDMD_K_PHI = 3,       /* Phi = X' (V Sigma^-1 W)                          */
     SDMD_K_FRAME = 4,     /* one sdmd_step frame: call start to outputs done  */
-    SDMD_K_COUNT = 5
+    SDMD_K_FUSED = 5,     /* Phi of an earlier frame + this snapshot's Gram row in one pass */
+    SDMD_K_COUNT = 6
 };
 
 /*

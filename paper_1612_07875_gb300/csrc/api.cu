@@ -8,6 +8,7 @@
 
 #include <new>
 #include <string>
+#include <deque>
 #include <vector>
 
 #include "sdmd.h"
@@ -24,9 +25,16 @@ struct PipeCtx {
   void* gsnap = nullptr;      // time-ordered c x c copy of G for this frame
   cudaStream_t st = nullptr;
   cudaEvent_t ev_g = nullptr;     // G snapshot taken (push stream)
-  cudaEvent_t ev_done = nullptr;  // modes, Phi and output copies done (ctx stream)
+  cudaEvent_t ev_done = nullptr;  // modes, Phi and output copies done (ctx stream, or the push
+                                  // stream when Phi ran fused with a later Gram row)
+  cudaEvent_t ev_modes = nullptr; // modes and output copies done (ctx stream)
   bool busy = false;
   int64_t frame = -1;         // push count of the frame being processed
+  // Phi deferred to a later step (fused with that step's Gram row)
+  bool phi_pending = false;
+  float* phi = nullptr;
+  int32_t r = 0, start = 0, p = 0;
+  cudaEvent_t fr1 = nullptr;  // frame-trace end, recorded when the deferred Phi completes
 };
 
 struct sdmd_s {
@@ -37,6 +45,8 @@ struct sdmd_s {
   int32_t cap = 0;            // ring slots (m, or m + depth when pipelined)
   int32_t depth = 1;          // DMD frames in flight (sdmd_step)
   std::vector<PipeCtx> ctx;
+  std::deque<int> pending;    // contexts whose Phi is deferred, oldest first
+  long long* fgpart = nullptr;  // fused Gram row: per-CTA sums (allocated on first use)
   int64_t steps = 0;
   int32_t dtype = 0;
   int64_t elem = 0;
@@ -77,7 +87,7 @@ struct sdmd_s {
   // tracing: per kernel class, event pairs recorded since the last read
   bool trace = false;
   std::vector<cudaEvent_t> tr_ev[SDMD_K_COUNT];
-  size_t tr_used[SDMD_K_COUNT] = {0, 0, 0, 0, 0};
+  size_t tr_used[SDMD_K_COUNT] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -216,6 +226,7 @@ void free_ctx(sdmd_s* h) {
     cudaFree(c.gsnap);
     if (c.ev_g) cudaEventDestroy(c.ev_g);
     if (c.ev_done) cudaEventDestroy(c.ev_done);
+    if (c.ev_modes) cudaEventDestroy(c.ev_modes);
     if (c.st) cudaStreamDestroy(c.st);
   }
   h->ctx.clear();
@@ -237,6 +248,7 @@ void free_all(sdmd_s* h) {
   cudaFree(h->phi_sched);
   cudaFree(h->gf_partials);
   cudaFree(h->gf_sched);
+  cudaFree(h->fgpart);
 }
 
 inline int32_t resident(const sdmd_s* h) { return (int32_t)(h->count < h->m ? h->count : h->m); }
@@ -244,14 +256,64 @@ inline int32_t oldest_slot(const sdmd_s* h) { return (int32_t)((h->count - resid
 
 // Before push number t overwrites slot t % cap (the snapshot pushed cap
 // earlier), wait for every in-flight DMD whose X' still contains it.
+int flush_pending(sdmd_s* h, cudaStream_t st);
+
 void wait_ring_readers(sdmd_s* h, cudaStream_t st) {
   const int64_t t = h->count;
   for (PipeCtx& c : h->ctx) {
     if (c.busy && c.frame - h->m + 2 <= t - h->cap) {
+      if (c.phi_pending) flush_pending(h, st);   // its Phi must run before the slot is reused
       cudaStreamWaitEvent(st, c.ev_done, 0);
       c.busy = false;
     }
   }
+}
+
+// Phi arguments of a pipelined frame (its window, its modes workspace).
+PhiArgs ctx_phi_args(const sdmd_s* h, const PipeCtx& k) {
+  const ModesLayout L = modes_layout(h->m);
+  PhiArgs pa;
+  pa.ring = h->ring;
+  pa.slot_bytes = h->slot_bytes;
+  pa.n = h->n;
+  pa.dtype = h->dtype;
+  pa.m = h->cap;
+  pa.start = k.start;
+  pa.p = k.p;
+  pa.r = k.r;
+  pa.Mf = reinterpret_cast<const float*>(k.ws + L.Mf);
+  pa.r_dev = k.r_dev;
+  pa.phi = k.phi;
+  pa.status = h->status;
+  pa.tensor = h->phi_tensor;
+  pa.sched = k.phi_sched;
+  return pa;
+}
+
+// The deferred Phi of the oldest pending frame, on its own, on `st`.
+int flush_one(sdmd_s* h, cudaStream_t st) {
+  const int ci = h->pending.front();
+  h->pending.pop_front();
+  PipeCtx& k = h->ctx[ci];
+  CK(cudaStreamWaitEvent(st, k.ev_modes, 0));
+  {
+    TraceScope ts(h, SDMD_K_PHI, st);
+    CK(launch_phi(ctx_phi_args(h, k), st));
+  }
+  CK(cudaEventRecord(k.ev_done, st));
+  if (k.fr1) CK(cudaEventRecord(k.fr1, st));
+  k.fr1 = nullptr;
+  k.phi_pending = false;
+  return SDMD_OK;
+}
+
+// Every deferred Phi, before anything else may touch the ring or read results.
+int flush_pending(sdmd_s* h, cudaStream_t st) {
+  while (!h->pending.empty()) {
+    const int rc = flush_one(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  return SDMD_OK;
 }
 
 }  // namespace
@@ -332,6 +394,7 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_g, cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_modes, cudaEventDisableTiming);
     }
   }
   if (e == cudaSuccess) e = cudaMemset(h->status, 0, sizeof(int));
@@ -463,19 +526,19 @@ int sdmd_destroy(sdmd_t h) {
   return SDMD_OK;
 }
 
-int sdmd_push(sdmd_t h, const void* x, void* stream) {
-  if (!h) return fail(SDMD_ERR_ARG, "sdmd_push: NULL handle");
-  if (h->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_push: sparse handle (use sdmd_push_sparse)");
-  if (!x) return fail(SDMD_ERR_ARG, "sdmd_push: NULL snapshot");
-  DeviceScope ds(h->device);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
+namespace {
+
+// Ingest into slot `head` (after every in-flight reader of that slot).
+int ingest(sdmd_s* h, const void* x, cudaStream_t st) {
   wait_ring_readers(h, st);
-  const int32_t s = h->head;
-  {
-    TraceScope ts(h, SDMD_K_INGEST, st);
-    CK(cudaMemcpyAsync(h->ring + (int64_t)s * h->slot_bytes, x, (size_t)(h->n * h->elem),
-                       cudaMemcpyDefault, st));
-  }
+  TraceScope ts(h, SDMD_K_INGEST, st);
+  CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, x, (size_t)(h->n * h->elem), cudaMemcpyDefault,
+                     st));
+  return SDMD_OK;
+}
+
+// Gram row of the snapshot just ingested into slot `s`, then advance the ring.
+int gram_row_and_advance(sdmd_s* h, int32_t s, cudaStream_t st) {
   GramRowArgs a;
   a.ring = h->ring;
   a.slot_bytes = h->slot_bytes;
@@ -496,6 +559,20 @@ int sdmd_push(sdmd_t h, const void* x, void* stream) {
   h->head = (s + 1) % h->cap;
   h->count += 1;
   return SDMD_OK;
+}
+
+}  // namespace
+
+int sdmd_push(sdmd_t h, const void* x, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_push: NULL handle");
+  if (h->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_push: sparse handle (use sdmd_push_sparse)");
+  if (!x) return fail(SDMD_ERR_ARG, "sdmd_push: NULL snapshot");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc = flush_pending(h, st);
+  if (rc == SDMD_OK) rc = ingest(h, x, st);
+  if (rc == SDMD_OK) rc = gram_row_and_advance(h, h->head, st);
+  return rc;
 }
 
 namespace {
@@ -540,6 +617,10 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
     return fail(SDMD_ERR_ARG, "sdmd_push_batch: k=%d (1..%d), ld=%lld (>= n) or NULL data", k, h->m, (long long)ld);
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   const int c_after = (int)(h->count + k < h->m ? h->count + k : h->m);
   const size_t elem_bytes = (size_t)h->elem;
   const uint8_t* src = static_cast<const uint8_t*>(X);
@@ -595,6 +676,10 @@ int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void*
   }
   DeviceScope ds(hs[0]->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) {
+    const int rc = flush_pending(hs[i], st);
+    if (rc != SDMD_OK) return rc;
+  }
   BatchArgs ba;
   ba.njobs = count;
   ba.nitems = 0;
@@ -638,6 +723,10 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_rebuild: NULL handle");
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   const int c = resident(h);
   const int first = oldest_slot(h);
   if (h->dtype == SDMD_F32 && h->f32_bf16x3 && c >= 1) return gram_f32_tensor(h, c, c, st);
@@ -746,6 +835,10 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
   if (r < 1 || r > h->m - 1) return fail(SDMD_ERR_ARG, "sdmd_modes: r=%d not in [1, %d]", r, h->m - 1);
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   if (phi && ptr_kind(phi) != kDevice)
     return fail(SDMD_ERR_ARG, "sdmd_modes: phi must be device memory (n x r complex64)");
   ModesArgs a;
@@ -811,20 +904,78 @@ int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32
     if (rc != SDMD_OK) return rc;
     return resident(h) >= 3 ? sdmd_modes(h, r, phi, lambda, r_out, stream) : SDMD_OK;
   }
-  if (r < 1 || r > h->m - 1) return fail(SDMD_ERR_ARG, "sdmd_step: r=%d not in [1, %d]", r, h->m - 1);
+  if (!x) return fail(SDMD_ERR_ARG, "sdmd_step: NULL snapshot");
   if (phi && ptr_kind(phi) != kDevice) return fail(SDMD_ERR_ARG, "sdmd_step: phi must be device memory");
   if ((lambda && ptr_kind(lambda) == kPageable) || (r_out && ptr_kind(r_out) == kPageable))
     return fail(SDMD_ERR_ARG, "sdmd_step: lambda / r_out must be device or pinned host memory");
-  cudaEvent_t fr0 = nullptr, fr1 = nullptr;
-  const bool ftrace = (h->count + 1 >= 3) && trace_pair(h, SDMD_K_FRAME, &fr0, &fr1);
-  if (ftrace) CK(cudaEventRecord(fr0, static_cast<cudaStream_t>(stream)));
-  int rc = sdmd_push(h, x, stream);
-  if (rc != SDMD_OK) return rc;
-  const int c = resident(h);
-  if (c < 3) return SDMD_OK;         // window too short: push only
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  PipeCtx& k = h->ctx[h->steps % h->depth];
+  // Phi of frame f runs fused with the Gram row of frame f + dfuse (uint8
+  // windows on the tensor cores, both windows full): one pass over the union
+  // of the two windows instead of two passes over nearly the same slots.
+  const int dfuse = h->depth - 1;
+  const bool can_fuse = h->dtype == SDMD_U8 && h->phi_tensor && (h->m - 1) + dfuse < 256;
+  const int64_t t = h->count;        // push index of this frame
+  cudaEvent_t fr0 = nullptr, fr1 = nullptr;
+  const bool ftrace = (t + 1 >= 3) && trace_pair(h, SDMD_K_FRAME, &fr0, &fr1);
+  if (ftrace) CK(cudaEventRecord(fr0, st));
+  while (!h->pending.empty() && h->ctx[h->pending.front()].frame < t - dfuse) {   // overdue: alone
+    const int rc = flush_one(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  {
+    const int rc = ingest(h, x, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  const int32_t s_new = h->head;
+  const int c_t = (int32_t)(t + 1 < h->m ? t + 1 : h->m);
+  bool fused = false;
+  if (!h->pending.empty() && h->ctx[h->pending.front()].frame == t - dfuse) {
+    PipeCtx& kf = h->ctx[h->pending.front()];
+    if (can_fuse && kf.p == h->m - 1 && c_t == h->m) {
+      if (!h->fgpart) {
+        if (cudaMalloc(&h->fgpart, (size_t)kFusedMaxCtas * 256 * sizeof(long long)) != cudaSuccess) {
+          cudaGetLastError();
+          return fail(SDMD_ERR_OOM, "sdmd_step: fused Gram scratch allocation failed");
+        }
+      }
+      PhiArgs pa = ctx_phi_args(h, kf);
+      pa.fuse = 1;
+      pa.ktot = kf.p + dfuse;        // X' of frame f, then the snapshots up to x_t
+      pa.g0 = dfuse - 1;             // the window of x_t: rows g0 .. ktot - 1
+      pa.gpart = h->fgpart;
+      const int32_t slot0 = (kf.start + 1 + pa.g0) % h->cap;
+      CK(cudaStreamWaitEvent(st, kf.ev_modes, 0));
+      {
+        TraceScope ts(h, SDMD_K_FUSED, st);
+        CK(launch_phi_fused(pa, static_cast<long long*>(h->G), h->cap, s_new, slot0, st));
+      }
+      CK(cudaEventRecord(kf.ev_done, st));
+      if (kf.fr1) CK(cudaEventRecord(kf.fr1, st));
+      kf.fr1 = nullptr;
+      kf.phi_pending = false;
+      h->pending.pop_front();
+      fused = true;
+    } else {
+      const int rc = flush_one(h, st);
+      if (rc != SDMD_OK) return rc;
+    }
+  }
+  if (fused) {
+    h->head = (s_new + 1) % h->cap;
+    h->count += 1;
+  } else {
+    const int rc = gram_row_and_advance(h, s_new, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  const int c = resident(h);
+  if (c < 3) return SDMD_OK;         // window too short: push only
+  const int ci = (int)(h->steps % h->depth);
+  PipeCtx& k = h->ctx[ci];
+  if (k.phi_pending) {               // (not reached with dfuse = depth - 1) its Phi first
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   if (k.busy) {                      // its workspace still belongs to an older frame
     CK(cudaStreamWaitEvent(st, k.ev_done, 0));
     k.busy = false;
@@ -851,31 +1002,27 @@ int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32
     CK(launch_modes_small(a, k.st));
   }
   const ModesLayout L = modes_layout(h->m);
-  if (phi) {
-    PhiArgs pa;
-    pa.ring = h->ring;
-    pa.slot_bytes = h->slot_bytes;
-    pa.n = h->n;
-    pa.dtype = h->dtype;
-    pa.m = h->cap;
-    pa.start = oldest_slot(h);
-    pa.p = c - 1;
-    pa.r = r;
-    pa.Mf = reinterpret_cast<const float*>(k.ws + L.Mf);
-    pa.r_dev = k.r_dev;
-    pa.phi = static_cast<float*>(phi);
-    pa.status = h->status;
-    pa.tensor = h->phi_tensor;
-    pa.sched = k.phi_sched;
-    TraceScope ts(h, SDMD_K_PHI, k.st);
-    CK(launch_phi(pa, k.st));
-  }
   if (lambda) CK(cudaMemcpyAsync(lambda, k.ws + L.lamout, (size_t)r * 16, cudaMemcpyDefault, k.st));
   if (r_out) CK(cudaMemcpyAsync(r_out, k.r_dev, sizeof(int32_t), cudaMemcpyDefault, k.st));
-  CK(cudaEventRecord(k.ev_done, k.st));
-  if (ftrace) CK(cudaEventRecord(fr1, k.st));
-  k.busy = true;
+  CK(cudaEventRecord(k.ev_modes, k.st));
+  k.phi = static_cast<float*>(phi);
+  k.r = r;
+  k.start = oldest_slot(h);
+  k.p = c - 1;
   k.frame = h->count - 1;
+  k.busy = true;
+  if (phi && can_fuse) {             // Phi later, with a Gram row (or at the next sync)
+    k.phi_pending = true;
+    k.fr1 = ftrace ? fr1 : nullptr;
+    h->pending.push_back(ci);
+  } else {
+    if (phi) {
+      TraceScope ts(h, SDMD_K_PHI, k.st);
+      CK(launch_phi(ctx_phi_args(h, k), k.st));
+    }
+    CK(cudaEventRecord(k.ev_done, k.st));
+    if (ftrace) CK(cudaEventRecord(fr1, k.st));
+  }
   h->steps += 1;
   return SDMD_OK;
 }
@@ -884,6 +1031,10 @@ int sdmd_sync(sdmd_t h, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_sync: NULL handle");
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   for (PipeCtx& k : h->ctx) {
     if (k.busy) {
       CK(cudaStreamWaitEvent(st, k.ev_done, 0));
@@ -1147,6 +1298,10 @@ int sdmd_status(sdmd_t h, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_status: NULL handle");
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   for (PipeCtx& k : h->ctx)
     if (k.busy) CK(cudaStreamWaitEvent(st, k.ev_done, 0));
   int v = 0;

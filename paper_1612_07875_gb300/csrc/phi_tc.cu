@@ -111,10 +111,14 @@ struct TcShared {
 
 // Dynamic shared memory: A ring, B, staging ring, slot offsets, state.
 struct TcLayout {
-  int a_bytes, b_off, b_bytes, st_off, st_bytes, tab_off, sh_off, total;
+  int a_bytes, b_off, b_bytes, st_off, st_bytes, tab_off, xn_off, gs_off, sh_off, total;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages) {
+constexpr int kMaxConvWarps = 7;
+
+// fuse: add a private copy of the new snapshot's tile per converter warp and
+// stage (128 bytes each) and the CTA's Gram sums
+__host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages, int fuse = 0) {
   TcLayout L;
   L.a_bytes = kTileM * kpad * 2;                 // multiple of 4096
   L.b_off = n_a * L.a_bytes;
@@ -122,7 +126,9 @@ __host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages) {
   L.st_off = L.b_off + L.b_bytes;                // 16-byte aligned (cp.async destination)
   L.st_bytes = kpad * kTileM;
   L.tab_off = L.st_off + stages * L.st_bytes;    // window slot offsets (int64)
-  L.sh_off = L.tab_off + kMaxRows * 8;
+  L.xn_off = L.tab_off + kMaxRows * 8;
+  L.gs_off = L.xn_off + (fuse ? stages * kMaxConvWarps * kTileM : 0);
+  L.sh_off = L.gs_off + (fuse ? kMaxRows * 8 : 0);
   L.total = L.sh_off + (int)sizeof(TcShared);
   return L;
 }
@@ -148,7 +154,11 @@ template <int kIpt>
 __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, int kpad, int n_a, int stages) {
   constexpr int kU = kTileM;             // staging row bytes
   extern __shared__ __align__(1024) uint8_t smem[];
-  const TcLayout L = tc_layout(kpad, n_a, stages);
+  const TcLayout L = tc_layout(kpad, n_a, stages, a.fuse);
+  // fused Gram row: only the first mode pass computes it
+  const bool dots = a.fuse && blockIdx.y == 0;
+  const int krows = dots ? a.ktot : a.p;  // staged rows
+  unsigned long long* gsum = reinterpret_cast<unsigned long long*>(smem + L.gs_off);
   uint8_t* abuf = smem;
   uint8_t* bbuf = smem + L.b_off;
   uint8_t* stg = smem + L.st_off;
@@ -181,7 +191,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
   }
-  for (int q = tid; q < a.p; q += nthreads) tab[q] = (int64_t)((a.start + 1 + q) % a.m) * a.slot_bytes;
+  for (int q = tid; q < krows; q += nthreads) tab[q] = (int64_t)((a.start + 1 + q) % a.m) * a.slot_bytes;
+  if (dots)
+    for (int q = tid; q < kMaxRows; q += nthreads) gsum[q] = 0ull;
   if (tid < kCols) {
     // column scale: the largest |M| of the column lands in [2^14, 2^15)
     const int mode = k0 + tid / 2;
@@ -238,7 +250,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       // copy: lane -> slot 8 kg + lr, chunk pl (a quarter warp: slots r and r + 4, 4 chunks each)
       const int lr = (lane >> 3) + 4 * ((lane >> 2) & 1), pl = 4 * h + (lane & 3);
       const int ql = 8 * kg + lr;
-      src[j] = (ql < a.p) ? tab[ql] + 16 * pl : -1;
+      src[j] = (ql < krows) ? tab[ql] + 16 * pl : -1;
       ldo[j] = (unsigned)(ql * kU + 16 * (pl ^ lr));
       // conversion: lane -> slot 8 kg + kr, chunk pc (a quarter warp: 8 slots, one chunk)
       const int kr = lane & 7, pc = 4 * h + (lane >> 3);
@@ -289,6 +301,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       return t;
     };
     const unsigned stg0 = smem_u32(stg);
+    // fused Gram row: this warp's private copy of the new snapshot's tile
+    // (lanes 0..7, 16 bytes each) per stage, and per step j the exact sum of
+    // <x_slot, x_new> over this lane's 16 positions
+    uint8_t* xnw = smem + L.xn_off + cw * kTileM;       // stage s at + s * kMaxConvWarps * kTileM
+    const int64_t xsrc = dots ? tab[a.ktot - 1] + 16 * (lane & 7) : 0;
+    unsigned long long gacc[kIpt];
+    bool gslot[kIpt];
+#pragma unroll
+    for (int j = 0; j < kIpt; ++j) {
+      gacc[j] = 0ull;
+      const int u = cw + conv_warps * j;
+      const int sl = 8 * (u >> 1) + (lane & 7);
+      gslot[j] = dots && sl >= a.g0 && sl < a.ktot;
+    }
     int ld_stage = 0;
     auto load_next = [&]() {
       const int t = fix_next();
@@ -298,6 +324,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 #pragma unroll
         for (int j = 0; j < kIpt; ++j)
           if (src[j] >= 0) cp_async16(dst + ldo[j], tsrc + src[j]);
+        if (dots && lane < 8)
+          cp_async16(smem_u32(xnw + ld_stage * kMaxConvWarps * kTileM + 16 * lane), tsrc + xsrc);
       }
       ld_stage = (ld_stage + 1 == stages) ? 0 : ld_stage + 1;
     };
@@ -314,6 +342,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       cp_async_wait_pending(stages - 1);     // this lane's copies of tile `it` have landed
       __syncwarp();                          // ... and those of the other lanes of the warp
       const uint8_t* sb = stg + stage * L.st_bytes;
+      const uint8_t* xb = xnw + stage * kMaxConvWarps * kTileM;
       stage = (stage + 1 == stages) ? 0 : stage + 1;
       {
         int ok = 1;
@@ -332,6 +361,20 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
         uint4 w[kIpt];
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) w[j] = *reinterpret_cast<const uint4*>(sb + sto[j]);
+        if (dots) {
+#pragma unroll
+          for (int j = 0; j < kIpt; ++j) {
+            if (gslot[j]) {
+              const int pc = 4 * ((cw + conv_warps * j) & 1) + (lane >> 3);
+              const uint4 xv = *reinterpret_cast<const uint4*>(xb + 16 * pc);
+              unsigned d = __dp4a(w[j].x, xv.x, 0u);
+              d = __dp4a(w[j].y, xv.y, d);
+              d = __dp4a(w[j].z, xv.z, d);
+              d = __dp4a(w[j].w, xv.w, d);
+              gacc[j] += d;
+            }
+          }
+        }
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) {
           uint4 lo, hi;
@@ -353,6 +396,15 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       }
     }
     cp_async_wait<0>();                      // no copy lands after the CTA exits
+    if (dots) {                              // lanes kr, kr + 8, kr + 16, kr + 24 share a slot
+#pragma unroll
+      for (int j = 0; j < kIpt; ++j) {
+        unsigned long long v = gacc[j];
+        v += __shfl_xor_sync(0xffffffffu, v, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 16);
+        if (lane < 8 && gslot[j]) atomicAdd(&gsum[8 * ((cw + conv_warps * j) >> 1) + lane], v);
+      }
+    }
   } else if (warp == kMmaWarp) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
@@ -445,6 +497,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   __syncwarp();
   if (warp == kMmaWarp)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tbase), "r"(kTmemCols) : "memory");
+  if (dots)                                  // this CTA's sums (every CTA writes all of them)
+    for (int q = a.g0 + tid; q < a.ktot; q += nthreads)
+      a.gpart[(int64_t)(q - a.g0) * kFusedMaxCtas + blockIdx.x] = (long long)gsum[q];
   // the last CTA out (all grabs are done) zeroes the counters for the next launch
   if (tid == 0) {
     __threadfence();
@@ -458,7 +513,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 }
 
 template <int kIpt>
-cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem) {
+cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem, int* ctas) {
   static size_t attr = 0;
   if (smem > attr) {
     cudaError_t e =
@@ -475,24 +530,43 @@ cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int
   int64_t bx = ((int64_t)sms + ky - 1) / ky;
   if (bx > ntiles) bx = ntiles;
   if (bx < 1) bx = 1;
+  if (a.fuse && bx > kFusedMaxCtas) bx = kFusedMaxCtas;
   const int threads = 32 * (kConvWarp0 + kpad / (4 * kIpt));
   phi_tc_u8_kernel<kIpt><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
+  if (ctas) *ctas = (int)bx;
   return cudaGetLastError();
 }
 
-}  // namespace
+// G's new row and column from the per-CTA sums (exact int64): one block per
+// window slot jj, its CTA sums contiguous at gpart + jj * kFusedMaxCtas
+__global__ void __launch_bounds__(128) fused_gram_finish_kernel(const long long* gpart, int ctas, long long* G, int gm,
+                                                                 int s_new, int slot0) {
+  __shared__ long long red[4];
+  const int jj = blockIdx.x;
+  long long s = 0;
+  for (int b = threadIdx.x; b < ctas; b += blockDim.x) s += gpart[(int64_t)jj * kFusedMaxCtas + b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const long long v = red[0] + red[1] + red[2] + red[3];
+    const int j = (slot0 + jj) % gm;
+    G[(int64_t)s_new * gm + j] = v;
+    G[(int64_t)j * gm + s_new] = v;
+  }
+}
 
-// Tensor-core Phi for uint8 windows. Returns cudaErrorNotSupported when the
-// shape is outside what this kernel handles (the caller then uses the SIMT
-// kernel).
-cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st) {
+cudaError_t launch_phi_tc_impl(const PhiArgs& a, cudaStream_t st, int* ctas) {
   if (a.dtype != SDMD_U8 || a.p < 1 || a.p >= kMaxRows || a.sched == nullptr) return cudaErrorNotSupported;
+  const int rows = a.fuse ? a.ktot : a.p;
+  if (a.fuse && (rows >= kMaxRows || a.g0 < 0 || a.g0 >= rows || a.gpart == nullptr)) return cudaErrorNotSupported;
   // K padding and units per converter lane, at most 7 converter warps:
   // K <= 112: 4 units (K / 16 warps); K <= 224: K to a multiple of 32 and
   // 8 units (K / 32 warps); else K = 256 and 16 units (4 warps)
-  int kpad = ((a.p + 15) / 16) * 16, ipt = 4;
+  int kpad = ((rows + 15) / 16) * 16, ipt = 4;
   if (kpad > 112) {
-    kpad = ((a.p + 31) / 32) * 32;
+    kpad = ((rows + 31) / 32) * 32;
     ipt = 8;
     if (kpad > 224) {
       kpad = 256;
@@ -503,16 +577,37 @@ cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st) {
   static const int kConfigs[][2] = {{4, 6}, {4, 5}, {4, 4}, {3, 5}, {3, 4}, {2, 6}, {2, 4}, {2, 3}, {1, 4}, {1, 3}};
   const int kLimit = 227 * 1024;
   for (const auto& cf : kConfigs) {
-    const TcLayout L = tc_layout(kpad, cf[0], cf[1]);
+    const TcLayout L = tc_layout(kpad, cf[0], cf[1], a.fuse);
     if (L.total > kLimit) continue;
     // at least 116 KiB: one of these CTAs per SM, so its 512 tensor-memory
     // columns are always free
     const size_t smem = L.total < 116 * 1024 ? 116 * 1024 : (size_t)L.total;
-    if (ipt == 4) return launch_cfg<4>(a, st, kpad, cf[0], cf[1], smem);
-    if (ipt == 8) return launch_cfg<8>(a, st, kpad, cf[0], cf[1], smem);
-    return launch_cfg<16>(a, st, kpad, cf[0], cf[1], smem);
+    if (ipt == 4) return launch_cfg<4>(a, st, kpad, cf[0], cf[1], smem, ctas);
+    if (ipt == 8) return launch_cfg<8>(a, st, kpad, cf[0], cf[1], smem, ctas);
+    return launch_cfg<16>(a, st, kpad, cf[0], cf[1], smem, ctas);
   }
   return cudaErrorNotSupported;
+}
+
+}  // namespace
+
+// Tensor-core Phi for uint8 windows. Returns cudaErrorNotSupported when the
+// shape is outside what this kernel handles (the caller then uses the SIMT
+// kernel).
+cudaError_t launch_phi_tc(const PhiArgs& a, cudaStream_t st) {
+  PhiArgs b = a;
+  b.fuse = 0;
+  return launch_phi_tc_impl(b, st, nullptr);
+}
+
+cudaError_t launch_phi_fused(const PhiArgs& a, long long* G, int32_t gm, int32_t s_new, int32_t slot0,
+                             cudaStream_t st) {
+  if (!a.fuse) return cudaErrorInvalidValue;
+  int ctas = 0;
+  cudaError_t e = launch_phi_tc_impl(a, st, &ctas);
+  if (e != cudaSuccess) return e;
+  fused_gram_finish_kernel<<<a.ktot - a.g0, 128, 0, st>>>(a.gpart, ctas, G, gm, s_new, slot0);
+  return cudaGetLastError();
 }
 
 }  // namespace sdmd

@@ -162,11 +162,25 @@ struct PhiArgs {
   unsigned* sched;      // kPhiSchedWords zeroed words: per-pass tile counters, CTA-done counter
   int32_t xoff = 1;     // first window column read: 1 = X' (Phi), 0 = X (POD modes)
   int32_t real_out = 0; // 1: Mf is p x r real, phi is n x r FP32 (CUDA-core kernel)
+  // Fused Gram row (tensor-core uint8 kernel): the staged rows continue past
+  // X' to ktot slots in time order (slots start + 1 .. start + ktot), the
+  // last being the new snapshot; rows g0 .. ktot - 1 are the new window, and
+  // each CTA adds its exact sums of <x_u, x_new> to gpart[cta][u - g0].
+  int32_t fuse = 0;
+  int32_t ktot = 0, g0 = 0;
+  long long* gpart = nullptr;
 };
+// Per-CTA partial capacity of the fused Gram row (CTAs x window slots).
+constexpr int kFusedMaxCtas = 160;
 constexpr int kPhiSchedPasses = 16;                 // mode passes of 16 (r <= 256)
 constexpr int kPhiSchedWords = kPhiSchedPasses + 1;
 
 cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st);
+// Phi of one frame and the Gram row of a later snapshot in one pass over the
+// union of their windows (uint8, tensor cores), then G's new row and column
+// (int64, physical slots: s_new, and slot0 + jj for window index jj).
+cudaError_t launch_phi_fused(const PhiArgs& a, long long* G, int32_t gm, int32_t s_new, int32_t slot0,
+                             cudaStream_t st);
 // Mu[j][k] = V[k][j] / sigma_k (zero beyond the kept rank), then
 // U = X Mu with the real CUDA-core Phi kernel (xoff = 0, real_out = 1).
 cudaError_t launch_pod_modes(const PhiArgs& a, const double* V, const double* sig, float* Mu, cudaStream_t st);

@@ -43,7 +43,8 @@ SDMD_K_GRAM_ROW = 1
 SDMD_K_MODES = 2
 SDMD_K_PHI = 3
 SDMD_K_FRAME = 4
-SDMD_K_COUNT = 5
+SDMD_K_FUSED = 5
+SDMD_K_COUNT = 6
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libsdmd.so")
 

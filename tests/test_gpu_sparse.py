@@ -125,9 +125,13 @@ def test_sparse_edge_cases(cuda_device):
         S.sdmd_push_sparse(h, 2, bad_dev, torch.ones(4, dtype=torch.float32, device=cuda_device))
         assert S.sdmd_status(h) == S.SDMD_ERR_ARG
         assert S.sdmd_status(h) == S.SDMD_OK
+        # modes of a sparse window stay in coefficient space (sdmd_fourier_modes):
+        # a dense Phi is refused, the small-matrix part runs
         with pytest.raises(S.SdmdError) as ei:
-            S.sdmd_modes(h, 1, None, None)
+            S.sdmd_modes(h, 1, torch.zeros(1, n, 2, device=cuda_device), None)
         assert ei.value.code == S.SDMD_ERR_UNSUPPORTED
+        S.sdmd_modes(h, 1, None, None)
+        assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
 
