@@ -224,6 +224,14 @@ SDMD_API int sdmd_server_close(sdmd_server_t s, int32_t sid);
 SDMD_API int sdmd_server_stats(sdmd_server_t s, double *p50_ms, double *p99_ms, int64_t *frames);
 /* device bytes held by active streams (-1 for a NULL server) */
 SDMD_API int64_t sdmd_server_used_bytes(sdmd_server_t s);
+/* on (default): each tick's batch is one CUDA graph launch (copy nodes and
+ * the batched kernel node), built once per set of streams and updated in
+ * place on later ticks; off: copies and a kernel launch on the stream */
+SDMD_API int sdmd_server_set_graphs(sdmd_server_t s, int32_t on);
+/* graphs built and updated in place so far (host pointers, may be NULL) */
+SDMD_API int sdmd_server_graph_stats(sdmd_server_t s, int64_t *builds, int64_t *updates);
+/* sdmd_autotune on every active stream holding a snapshot (server stream) */
+SDMD_API int sdmd_server_autotune(sdmd_server_t s);
 /* forget the latencies and frame count gathered so far (e.g. after warm-up) */
 SDMD_API int sdmd_server_reset_stats(sdmd_server_t s);
 /* the clock that arrival_ms and the latencies use: milliseconds of a
@@ -289,6 +297,20 @@ SDMD_API int sdmd_modes(sdmd_t h, int32_t r, void *phi, void *lambda, int32_t *r
  */
 SDMD_API int sdmd_step(sdmd_t h, const void *x, int32_t r, void *phi, void *lambda, int32_t *r_out,
                        void *stream);
+
+/*
+ * sdmd_autotune -- pick the Gram-row schedule of this handle by measurement:
+ * the newest snapshot's row over the current window is timed (CUDA events,
+ * 3 runs after a warm-up) with 1, 2, 3, 4 and 6 chunks per SM (chunks of 4 to
+ * 24 KiB taken from a counter by persistent CTAs) and the fastest is kept for
+ * later pushes (and for sdmd_push_many). The row is recomputed with the kept
+ * schedule at the end. uint8 rows are exact under every schedule; float rows
+ * change only in rounding (the reduction order follows the chunks).
+ * chunk_bytes / us (host, may be NULL) receive the kept chunk size and its
+ * time per row. Waits for the stream. Dense handles with at least one
+ * snapshot (SDMD_ERR_NOT_READY otherwise).
+ */
+SDMD_API int sdmd_autotune(sdmd_t h, int64_t *chunk_bytes, double *us, void *stream);
 
 /* sdmd_sync -- make `stream` wait for every sdmd_step frame still in flight. */
 SDMD_API int sdmd_sync(sdmd_t h, void *stream);

@@ -47,6 +47,7 @@ struct sdmd_s {
   std::vector<PipeCtx> ctx;
   std::deque<int> pending;    // contexts whose Phi is deferred, oldest first
   long long* fgpart = nullptr;  // fused Gram row: per-CTA sums (allocated on first use)
+  int32_t nblk_alloc = 0;       // chunks the partials array holds
   int64_t steps = 0;
   int32_t dtype = 0;
   int64_t elem = 0;
@@ -372,6 +373,7 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
   if (e == cudaSuccess) e = cudaMalloc(&h->G, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->gtmp, gbytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->partials, (size_t)m * h->nblk * h->gsz);
+  h->nblk_alloc = h->nblk;
   if (e == cudaSuccess) e = cudaMalloc(&h->ticket, 4 * sizeof(unsigned int));
   if (e == cudaSuccess) e = cudaMalloc(&h->ws, ws_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&h->status, sizeof(int));
@@ -664,8 +666,9 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   return SDMD_OK;
 }
 
-int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void* stream) {
-  if (!hs || !xs || count < 1 || count > kMaxBatchJobs)
+extern "C++" int sdmd::push_many_plan(sdmd_t const* hs, const void* const* xs, int count, cudaStream_t st,
+                                      BatchPlan* plan) {
+  if (!hs || !xs || !plan || count < 1 || count > kMaxBatchJobs)
     return fail(SDMD_ERR_ARG, "sdmd_push_many: count=%d not in [1, %d] or NULL arrays", count, kMaxBatchJobs);
   for (int i = 0; i < count; ++i) {
     if (!hs[i] || !xs[i]) return fail(SDMD_ERR_ARG, "sdmd_push_many: NULL handle or snapshot %d", i);
@@ -674,26 +677,23 @@ int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void*
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(SDMD_ERR_ARG, "sdmd_push_many: handle %d appears twice", i);
   }
-  DeviceScope ds(hs[0]->device);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < count; ++i) {
     const int rc = flush_pending(hs[i], st);
     if (rc != SDMD_OK) return rc;
   }
-  BatchArgs ba;
+  BatchArgs& ba = plan->args;
   ba.njobs = count;
   ba.nitems = 0;
   ba.grab = hs[0]->ticket + 2;
   ba.status = hs[0]->status;
+  plan->ncopies = count;
   for (int i = 0; i < count; ++i) {
     sdmd_s* h = hs[i];
     wait_ring_readers(h, st);
     const int32_t s_new = h->head;
-    {
-      TraceScope ts(h, SDMD_K_INGEST, st);
-      CK(cudaMemcpyAsync(h->ring + (int64_t)s_new * h->slot_bytes, xs[i], (size_t)(h->n * h->elem), cudaMemcpyDefault,
-                         st));
-    }
+    plan->dst[i] = h->ring + (int64_t)s_new * h->slot_bytes;
+    plan->src[i] = xs[i];
+    plan->bytes[i] = (size_t)(h->n * h->elem);
     RowJob& J = ba.job[i];
     J.ring = h->ring;
     J.slot_bytes = h->slot_bytes;
@@ -712,9 +712,25 @@ int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void*
     h->head = (s_new + 1) % h->cap;
     h->count += 1;
   }
+  return SDMD_OK;
+}
+
+int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void* stream) {
+  if (!hs || count < 1) return fail(SDMD_ERR_ARG, "sdmd_push_many: count=%d not in [1, %d] or NULL arrays", count,
+                                    kMaxBatchJobs);
+  if (!hs[0]) return fail(SDMD_ERR_ARG, "sdmd_push_many: NULL handle or snapshot 0");
+  DeviceScope ds(hs[0]->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  BatchPlan plan;
+  const int rc = push_many_plan(hs, xs, count, st, &plan);
+  if (rc != SDMD_OK) return rc;
+  for (int i = 0; i < plan.ncopies; ++i) {
+    TraceScope ts(hs[i], SDMD_K_INGEST, st);
+    CK(cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, st));
+  }
   {
     TraceScope ts(hs[0], SDMD_K_GRAM_ROW, st);
-    CK(launch_gram_rows_batched(ba, st));
+    CK(launch_gram_rows_batched(plan.args, st));
   }
   return SDMD_OK;
 }
@@ -1024,6 +1040,92 @@ int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32
     if (ftrace) CK(cudaEventRecord(fr1, k.st));
   }
   h->steps += 1;
+  return SDMD_OK;
+}
+
+int sdmd_autotune(sdmd_t h, int64_t* chunk_bytes, double* us, void* stream) {
+  if (!h) return fail(SDMD_ERR_ARG, "sdmd_autotune: NULL handle");
+  if (h->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_autotune: dense handles only");
+  if (h->count < 1) return fail(SDMD_ERR_NOT_READY, "sdmd_autotune: no snapshot pushed yet");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  static const int kCands[] = {1, 2, 3, 4, 6};   // chunks per SM
+  int64_t cch[5];
+  int32_t cnb[5];
+  int32_t need = h->nblk;
+  for (int i = 0; i < 5; ++i) {
+    gram_row_schedule_k(h->slot_bytes, h->num_sms, kCands[i], &cch[i], &cnb[i]);
+    if (cnb[i] > need) need = cnb[i];
+  }
+  if (need > h->nblk_alloc) {
+    CK(cudaStreamSynchronize(st));
+    void* np = nullptr;
+    if (cudaMalloc(&np, (size_t)h->m * need * h->gsz) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(SDMD_ERR_OOM, "sdmd_autotune: partials allocation failed");
+    }
+    cudaFree(h->partials);
+    h->partials = np;
+    h->nblk_alloc = need;
+  }
+  // the newest snapshot's Gram row over the current window, without advancing
+  GramRowArgs a;
+  a.ring = h->ring;
+  a.slot_bytes = h->slot_bytes;
+  a.c = resident(h);
+  a.s_first = oldest_slot(h);
+  a.s_new = (int32_t)((h->head + h->cap - 1) % h->cap);
+  a.m = h->cap;
+  a.partials = h->partials;
+  a.ticket = h->ticket;
+  a.G = h->G;
+  a.status = h->status;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  int bi = 1;
+  int rc = SDMD_OK;
+  for (int i = 0; i < 5 && rc == SDMD_OK; ++i) {
+    bool dup = false;
+    for (int j = 0; j < i; ++j) dup = dup || (cch[j] == cch[i]);
+    if (dup) continue;
+    a.chunk = cch[i];
+    a.nblk = cnb[i];
+    cudaError_t e = launch_gram_row(h->dtype, h->f32_fp64 != 0, a, st);   // warm-up
+    double tot = 0.0;
+    for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+      if (e == cudaSuccess) e = launch_gram_row(h->dtype, h->f32_fp64 != 0, a, st);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      tot += ms;
+    }
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "sdmd_autotune: timing pass");
+      break;
+    }
+    if (tot < best) {
+      best = tot;
+      bi = i;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != SDMD_OK) return rc;
+  h->chunk = cch[bi];
+  h->nblk = cnb[bi];
+  a.chunk = h->chunk;                 // the newest row once more with the kept schedule
+  a.nblk = h->nblk;
+  CK(launch_gram_row(h->dtype, h->f32_fp64 != 0, a, st));
+  if (chunk_bytes) *chunk_bytes = h->chunk;
+  if (us) *us = 1e3 * best / 3.0;
   return SDMD_OK;
 }
 

@@ -644,8 +644,12 @@ __global__ void __launch_bounds__(kGrThreads, 1) gram_rows_batched_kernel(const 
 constexpr int kChunksPerSm = 2;
 
 void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t* nblk) {
+  gram_row_schedule_k(slot_bytes, num_sms, kChunksPerSm, chunk, nblk);
+}
+
+void gram_row_schedule_k(int64_t slot_bytes, int num_sms, int chunks_per_sm, int64_t* chunk, int32_t* nblk) {
   const int64_t units = (slot_bytes + kPiece - 1) / kPiece;
-  int64_t want = (int64_t)kChunksPerSm * (num_sms > 0 ? num_sms : 1);
+  int64_t want = (int64_t)(chunks_per_sm > 0 ? chunks_per_sm : 1) * (num_sms > 0 ? num_sms : 1);
   if (want > units) want = units;
   int64_t per = (units + want - 1) / want;           // 4 KiB units per chunk
   if (per > kXSub / kPiece) per = kXSub / kPiece;   // at most 24 KiB (x_new double buffer)
@@ -680,6 +684,28 @@ cudaError_t launch_gram_row(int dtype, bool f64_ref, const GramRowArgs& a, cudaS
   else
     gram_row_bulk_kernel<kModeF32><<<ctas, kGrThreads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t batched_kernel_config(const BatchArgs& a, cudaKernelNodeParams* p) {
+  static bool attr = false;
+  const size_t smem = sizeof(BatchSmem);
+  if (!attr) {
+    cudaError_t e =
+        cudaFuncSetAttribute(gram_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ctas = a.nitems < sms ? a.nitems : (sms > 0 ? sms : 1);
+  p->func = reinterpret_cast<void*>(gram_rows_batched_kernel);
+  p->gridDim = dim3((unsigned)(ctas > 0 ? ctas : 1));
+  p->blockDim = dim3(kGrThreads);
+  p->sharedMemBytes = (unsigned)smem;
+  p->kernelParams = nullptr;
+  p->extra = nullptr;
+  return cudaSuccess;
 }
 
 cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st) {

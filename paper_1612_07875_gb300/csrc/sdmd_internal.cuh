@@ -101,6 +101,23 @@ struct BatchArgs {
   int* status;           // status word of the first handle
 };
 cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st);
+// Launch configuration of the batched kernel for a graph kernel node (func,
+// grid, block, shared memory; kernelParams left to the caller); sets the
+// kernel's shared-memory attribute on first use.
+cudaError_t batched_kernel_config(const BatchArgs& a, cudaKernelNodeParams* p);
+
+// One batched push, planned: the handles' deferred work flushed, ring readers
+// waited for, the ingest copies and the batch arguments filled in, and every
+// handle's ring advanced on the host. The caller issues the copies, then the
+// batched kernel (directly or as graph nodes), on `st`.
+struct BatchPlan {
+  BatchArgs args;
+  int ncopies;
+  void* dst[kMaxBatchJobs];
+  const void* src[kMaxBatchJobs];
+  size_t bytes[kMaxBatchJobs];
+};
+int push_many_plan(sdmd_t const* hs, const void* const* xs, int count, cudaStream_t st, BatchPlan* plan);
 
 // Device bytes of a depth-1 dense handle (admission by footprint).
 int64_t handle_device_bytes(int64_t n, int32_t m, int32_t dtype, int num_sms);
@@ -112,6 +129,8 @@ cudaError_t launch_gram_row(int dtype, bool f64_ref, const GramRowArgs& a, cudaS
 // Schedule of the Gram-row kernel: a function of slot size and SM count only,
 // so that every entry of G sees the same summation order.
 void gram_row_schedule(int64_t slot_bytes, int num_sms, int64_t* chunk, int32_t* nblk);
+// The same with a given number of chunks per SM (the autotuner's candidates).
+void gram_row_schedule_k(int64_t slot_bytes, int num_sms, int chunks_per_sm, int64_t* chunk, int32_t* nblk);
 
 struct ModesArgs {
   const void* G;        // m x m physical (double or int64)

@@ -8,6 +8,12 @@
 // frame = completion of its tick minus its arrival (host clock, or the time
 // given at submit); p50 / p99 over all completed frames.
 //
+// A tick's work for up to 64 streams (the ingest copies of their queued
+// frames and one batched Gram-row kernel) is a CUDA graph: built once per
+// set of streams (copy nodes, then the kernel node after them), instantiated,
+// and on later ticks with the same streams updated in place (new slots,
+// sources and kernel arguments) and launched with one cudaGraphLaunch.
+//
 // A server is driven by one host thread; all its GPU work runs on its own
 // stream (sdmd_server_stream).
 #include <cuda_runtime.h>
@@ -48,6 +54,16 @@ int err(int code, const char* msg) { return sdmd::set_last_error(code, msg); }
 
 }  // namespace
 
+// Instantiated graph of one batch position (streams hs, in order).
+struct TickGraph {
+  std::vector<sdmd_t> key;
+  std::vector<size_t> bytes;           // frame bytes of each copy (part of the key)
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaGraphNode_t> copies;
+  cudaGraphNode_t kernel = nullptr;
+};
+
 struct sdmd_server_s {
   int device = 0;
   int num_sms = 1;
@@ -57,6 +73,9 @@ struct sdmd_server_s {
   std::deque<int32_t> waiting;
   std::vector<double> lat;
   int64_t frames = 0;
+  bool graphs = true;
+  std::vector<TickGraph> tg;          // per batch position
+  int64_t graph_builds = 0, graph_updates = 0;
 };
 
 namespace {
@@ -74,6 +93,69 @@ int activate(sdmd_server_s* s, int32_t sid) {
   }
   q.state = SDMD_STREAM_ACTIVE;
   s->used += q.footprint;
+  return SDMD_OK;
+}
+
+void drop_graph(TickGraph& t) {
+  if (t.exec) cudaGraphExecDestroy(t.exec);
+  if (t.g) cudaGraphDestroy(t.g);
+  t = TickGraph();
+}
+
+// Issue one planned batch on the server stream: as a graph (built or
+// updated) or, with graphs off, as copies plus a kernel launch.
+int run_batch(sdmd_server_s* s, size_t b, const std::vector<sdmd_t>& hs, const sdmd::BatchPlan& plan) {
+  if (!s->graphs) {
+    for (int i = 0; i < plan.ncopies; ++i)
+      if (cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, s->st) != cudaSuccess) {
+        cudaGetLastError();
+        return err(SDMD_ERR_CUDA, "sdmd_server_tick: copy failed");
+      }
+    if (sdmd::launch_gram_rows_batched(plan.args, s->st) != cudaSuccess) {
+      cudaGetLastError();
+      return err(SDMD_ERR_CUDA, "sdmd_server_tick: batched launch failed");
+    }
+    return SDMD_OK;
+  }
+  if (s->tg.size() <= b) s->tg.resize(b + 1);
+  TickGraph& t = s->tg[b];
+  cudaKernelNodeParams kp;
+  if (sdmd::batched_kernel_config(plan.args, &kp) != cudaSuccess) {
+    cudaGetLastError();
+    return err(SDMD_ERR_CUDA, "sdmd_server_tick: kernel configuration failed");
+  }
+  sdmd::BatchArgs args = plan.args;
+  void* kargs[1] = {&args};
+  kp.kernelParams = kargs;
+  cudaError_t e = cudaSuccess;
+  const std::vector<size_t> bytes(plan.bytes, plan.bytes + plan.ncopies);
+  if (t.exec && t.key == hs && t.bytes == bytes) {   // same streams: update in place
+    for (int i = 0; i < plan.ncopies && e == cudaSuccess; ++i)
+      e = cudaGraphExecMemcpyNodeSetParams1D(t.exec, t.copies[i], plan.dst[i], plan.src[i], plan.bytes[i],
+                                             cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaGraphExecKernelNodeSetParams(t.exec, t.kernel, &kp);
+    if (e == cudaSuccess) s->graph_updates += 1;
+  } else {
+    drop_graph(t);
+    e = cudaGraphCreate(&t.g, 0);
+    t.copies.resize(plan.ncopies);
+    for (int i = 0; i < plan.ncopies && e == cudaSuccess; ++i)
+      e = cudaGraphAddMemcpyNode1D(&t.copies[i], t.g, nullptr, 0, plan.dst[i], plan.src[i], plan.bytes[i],
+                                   cudaMemcpyDefault);
+    if (e == cudaSuccess) e = cudaGraphAddKernelNode(&t.kernel, t.g, t.copies.data(), t.copies.size(), &kp);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&t.exec, t.g, 0);
+    if (e == cudaSuccess) {
+      t.key = hs;
+      t.bytes = bytes;
+      s->graph_builds += 1;
+    }
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(t.exec, s->st);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    drop_graph(t);
+    return err(SDMD_ERR_CUDA, "sdmd_server_tick: graph build, update or launch failed");
+  }
   return SDMD_OK;
 }
 
@@ -112,6 +194,7 @@ int sdmd_server_create(int64_t hbm_budget, sdmd_server_t* out) {
 int sdmd_server_destroy(sdmd_server_t s) {
   if (!s) return err(SDMD_ERR_ARG, "sdmd_server_destroy: NULL server");
   cudaStreamSynchronize(s->st);
+  for (TickGraph& t : s->tg) drop_graph(t);
   for (ServedStream& q : s->streams) {
     if (q.h) sdmd_destroy(q.h);
     cudaFree(q.fifo);
@@ -187,7 +270,9 @@ int sdmd_server_tick(sdmd_server_t s, int32_t* frames_done) {
       hs.push_back(q.h);
       xs.push_back(q.fifo + (int64_t)q.head * q.frame_bytes);
     }
-    const int rc = sdmd_push_many(hs.data(), xs.data(), (int32_t)hs.size(), s->st);
+    sdmd::BatchPlan plan;
+    int rc = sdmd::push_many_plan(hs.data(), xs.data(), (int32_t)hs.size(), s->st, &plan);
+    if (rc == SDMD_OK) rc = run_batch(s, b / SDMD_MAX_BATCH, hs, plan);
     if (rc != SDMD_OK) return rc;
   }
   if (cudaStreamSynchronize(s->st) != cudaSuccess) {
@@ -235,6 +320,37 @@ int sdmd_server_stats(sdmd_server_t s, double* p50_ms, double* p99_ms, int64_t* 
 }
 
 int64_t sdmd_server_used_bytes(sdmd_server_t s) { return s ? s->used : -1; }
+
+int sdmd_server_set_graphs(sdmd_server_t s, int32_t on) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_set_graphs: NULL server");
+  cudaStreamSynchronize(s->st);
+  for (TickGraph& t : s->tg) drop_graph(t);
+  s->tg.clear();
+  s->graphs = on != 0;
+  return SDMD_OK;
+}
+
+int sdmd_server_graph_stats(sdmd_server_t s, int64_t* builds, int64_t* updates) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_graph_stats: NULL server");
+  if (builds) *builds = s->graph_builds;
+  if (updates) *updates = s->graph_updates;
+  return SDMD_OK;
+}
+
+int sdmd_server_autotune(sdmd_server_t s) {
+  if (!s) return err(SDMD_ERR_ARG, "sdmd_server_autotune: NULL server");
+  for (ServedStream& q : s->streams) {
+    if (q.state != SDMD_STREAM_ACTIVE) continue;
+    int64_t cnt = 0;
+    sdmd_count(q.h, &cnt);
+    if (cnt < 1) continue;
+    const int rc = sdmd_autotune(q.h, nullptr, nullptr, s->st);
+    if (rc != SDMD_OK) return rc;
+  }
+  // schedules changed: the graphs' kernel arguments are rebuilt on the next tick
+  for (TickGraph& t : s->tg) drop_graph(t);
+  return SDMD_OK;
+}
 
 int sdmd_server_reset_stats(sdmd_server_t s) {
   if (!s) return err(SDMD_ERR_ARG, "sdmd_server_reset_stats: NULL server");

@@ -92,11 +92,15 @@ _SIGNATURES = {
     "sdmd_server_stats": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)],
     "sdmd_server_used_bytes": [_VP],
     "sdmd_server_reset_stats": [_VP],
+    "sdmd_server_set_graphs": [_VP, _I32],
+    "sdmd_server_graph_stats": [_VP, ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
+    "sdmd_server_autotune": [_VP],
     "sdmd_server_clock_ms": [],
     "sdmd_reconstruct": [_VP, _I64, _I32, _VP, _VP],
     "sdmd_reconstruct_ex": [_VP, _I64, _I32, ctypes.c_double, _VP, _VP],
     "sdmd_pod_modes": [_VP, _I32, _VP, _VP],
     "sdmd_fourier_modes": [_VP, _I32, _VP, _VP, _I64, ctypes.POINTER(_I64), _VP],
+    "sdmd_autotune": [_VP, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double), _VP],
 }
 
 
@@ -302,6 +306,21 @@ def sdmd_server_used_bytes(s):
     return lib().sdmd_server_used_bytes(s)
 
 
+def sdmd_server_set_graphs(s, on):
+    _check(lib().sdmd_server_set_graphs(s, 1 if on else 0), "sdmd_server_set_graphs")
+
+
+def sdmd_server_graph_stats(s):
+    """(graphs built, graphs updated in place)"""
+    b, u = _I64(), _I64()
+    _check(lib().sdmd_server_graph_stats(s, ctypes.byref(b), ctypes.byref(u)), "sdmd_server_graph_stats")
+    return b.value, u.value
+
+
+def sdmd_server_autotune(s):
+    _check(lib().sdmd_server_autotune(s), "sdmd_server_autotune")
+
+
 def sdmd_server_reset_stats(s):
     _check(lib().sdmd_server_reset_stats(s), "sdmd_server_reset_stats")
 
@@ -335,6 +354,13 @@ def sdmd_fourier_modes(h, r, idx=None, phi=None, cap=0, stream=None):
     _check(lib().sdmd_fourier_modes(h, int(r), ptr(idx), ptr(phi), int(cap), ctypes.byref(cnt), stream_handle(stream)),
            "sdmd_fourier_modes")
     return cnt.value
+
+
+def sdmd_autotune(h, stream=None):
+    """Measure the Gram-row chunk schedules; returns (chunk_bytes, us per row)."""
+    ch, us = _I64(), ctypes.c_double()
+    _check(lib().sdmd_autotune(h, ctypes.byref(ch), ctypes.byref(us), stream_handle(stream)), "sdmd_autotune")
+    return ch.value, us.value
 
 
 def sdmd_pod_modes(h, r, U, stream=None):

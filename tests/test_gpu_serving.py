@@ -167,3 +167,74 @@ def test_server_admission_and_continuous_batching(cuda_device):
         S.sdmd_server_destroy(srv)
         for h in alone:
             S.sdmd_destroy(h)
+
+
+def test_graph_ticks_equal_direct_ticks(cuda_device):
+    # the same submissions through a server with graph ticks and one without:
+    # every stream's G bit for bit equal; graphs are built once per set of
+    # streams and then updated in place
+    rng = np.random.default_rng(21)
+    specs = [("u8", 30011, 9), ("f32", 20003, 12), ("u8", 7001, 5), ("c64", 3001, 6)]
+    srv = [S.sdmd_server_create(1 << 36), S.sdmd_server_create(1 << 36)]
+    S.sdmd_server_set_graphs(srv[1], False)
+    try:
+        sids = [[S.sdmd_server_open(v, n, m, DT[k]) for k, n, m in specs] for v in srv]
+        for t in range(30):
+            live = [i for i in range(len(specs)) if t < 12 or rng.random() < 0.6]   # steady, then mixed
+            for i in live:
+                k, n, _ = specs[i]
+                x = _frame(k, n, rng)
+                for v in range(2):
+                    S.sdmd_server_submit(srv[v], sids[v][i], x)
+            for v in range(2):
+                S.sdmd_server_tick(srv[v])
+        builds, updates = S.sdmd_server_graph_stats(srv[0])
+        assert builds >= 1 and updates >= 11
+        assert S.sdmd_server_graph_stats(srv[1]) == (0, 0)
+        for i, (k, n, m) in enumerate(specs):
+            hs = [S.sdmd_server_handle(srv[v], sids[v][i]) for v in range(2)]
+            c = min(S.sdmd_count(hs[0]), m)
+            Ga = _gram_bytes(hs[0], c, k, S.sdmd_server_stream(srv[0]))
+            Gb = _gram_bytes(hs[1], c, k, S.sdmd_server_stream(srv[1]))
+            assert np.array_equal(Ga, Gb), specs[i]
+        S.sdmd_server_autotune(srv[0])                 # schedules re-picked; graphs rebuilt on the next tick
+        for i, (k, n, _) in enumerate(specs):
+            S.sdmd_server_submit(srv[0], sids[0][i], _frame(k, n, rng))
+        assert S.sdmd_server_tick(srv[0]) == len(specs)
+        assert S.sdmd_server_graph_stats(srv[0])[0] == builds + 1
+        for i in range(len(specs)):
+            assert S.sdmd_status(S.sdmd_server_handle(srv[0], sids[0][i]), S.sdmd_server_stream(srv[0])) == S.SDMD_OK
+    finally:
+        for v in srv:
+            S.sdmd_server_destroy(v)
+
+
+def test_autotune_keeps_the_gram_exact(cuda_device):
+    # sdmd_autotune picks a chunk schedule by timing; uint8 Grams stay exact
+    # and float Grams within their tolerance of the oracle across the change
+    import oracle
+    rng = np.random.default_rng(5)
+    for kind, n, m in (("u8", 1920 * 1080 * 3 // 4, 12), ("f32", (1 << 18) + 3, 10)):
+        h = S.sdmd_create(n, m, DT[kind])
+        so = oracle.StreamOracle(n, m, kind)
+        try:
+            with pytest.raises(S.SdmdError) as ei:
+                S.sdmd_autotune(h)
+            assert ei.value.code == S.SDMD_ERR_NOT_READY
+            for t in range(m + 5):
+                x = _frame(kind, n, rng)
+                S.sdmd_push(h, torch.from_numpy(x).to(cuda_device))
+                so.push(x)
+                if t == m // 2:
+                    chunk, us = S.sdmd_autotune(h)
+                    assert chunk % 4096 == 0 and 4096 <= chunk <= 24576 and us > 0
+            G = _gram_bytes(h, m, kind)
+            ref = so.gram()
+            if kind == "u8":
+                assert np.array_equal(G[..., 0], ref)
+            else:
+                Gf = G[..., 0].view(np.float64)
+                assert np.linalg.norm(Gf - ref) <= 1e-9 * np.linalg.norm(ref)
+            assert S.sdmd_status(h) == S.SDMD_OK
+        finally:
+            S.sdmd_destroy(h)
