@@ -537,12 +537,15 @@ def measure_serving(S, synth, dev, seconds, capacity_ticks=12):
             fcount[i] += 1
             return a
 
-        # warm-up: every window filled
+        # warm-up: every window filled, then the Gram-row schedules autotuned
         for j in range(max(s[2] for s in specs)):
             for i in range(ns):
                 if j < specs[i][2]:
                     S.sdmd_server_submit(srv, sids[i], haddr(i))
             S.sdmd_server_tick(srv)
+        t_at = time.perf_counter()
+        S.sdmd_server_autotune(srv)
+        autotune_s = time.perf_counter() - t_at
         arr = mix.arrivals(seconds)
         ev_t = np.concatenate(arr) * 1e3
         ev_s = np.concatenate([np.full(len(a), i) for i, a in enumerate(arr)])
@@ -596,6 +599,33 @@ def measure_serving(S, synth, dev, seconds, capacity_ticks=12):
                                  "definition": "tick completion (host) minus the frame's scheduled arrival"},
                   "hbm_footprint_GB": S.sdmd_server_used_bytes(srv) / 1e9, "budget_GB": budget / 1e9,
                   "clocks": clk}
+
+        # tick cost, every stream one queued frame (device sources), graph
+        # ticks against copies + kernel launched on the stream
+        def daddr0(i):
+            k, n, _, _ = specs[i]
+            a = dbase[k] + EL[k] * mix.offset(i, fcount[i])
+            fcount[i] += 1
+            return a
+        ticks = {}
+        for graphs in (True, False, True, False):
+            S.sdmd_server_set_graphs(srv, graphs)
+            for rep in range(2):
+                t0 = time.perf_counter()
+                for _ in range(capacity_ticks):
+                    for i in range(ns):
+                        S.sdmd_server_submit(srv, sids[i], daddr0(i))
+                    S.sdmd_server_tick(srv)
+                el = (time.perf_counter() - t0) / capacity_ticks
+                if rep:
+                    key = "graph" if graphs else "direct"
+                    ticks[key] = min(ticks.get(key, 1e9), el)
+        S.sdmd_server_set_graphs(srv, True)
+        served["tick_ms"] = {"graph": 1e3 * ticks["graph"], "direct": 1e3 * ticks["direct"],
+                             "note": "host clock per closed-loop tick (64 submits of device-resident frames, "
+                                     "the batched push, synchronisation)"}
+        served["autotune_s"] = autotune_s
+        served["graph_stats"] = dict(zip(("builds", "updates"), S.sdmd_server_graph_stats(srv)))
 
         # closed-loop capacity, device-resident frames
         hs = [S.sdmd_server_handle(srv, s) for s in sids]
