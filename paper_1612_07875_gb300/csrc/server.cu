@@ -9,10 +9,11 @@
 // given at submit); p50 / p99 over all completed frames.
 //
 // A tick's work for up to 64 streams (the ingest copies of their queued
-// frames and one batched Gram-row kernel) is a CUDA graph: built once per
-// set of streams (copy nodes, then the kernel node after them), instantiated,
-// and on later ticks with the same streams updated in place (new slots,
-// sources and kernel arguments) and launched with one cudaGraphLaunch.
+// frames and one batched Gram-row kernel) is a CUDA graph once the same set
+// of streams comes back tick after tick: built once per set (copy nodes,
+// then the kernel node after them), instantiated, and on later ticks updated
+// in place (new slots, sources and kernel arguments) and launched with one
+// cudaGraphLaunch. Sets that change every tick launch directly.
 //
 // A server is driven by one host thread; all its GPU work runs on its own
 // stream (sdmd_server_stream).
@@ -62,6 +63,7 @@ struct TickGraph {
   cudaGraphExec_t exec = nullptr;
   std::vector<cudaGraphNode_t> copies;
   cudaGraphNode_t kernel = nullptr;
+  std::vector<sdmd_t> last;            // streams of the previous tick at this position
 };
 
 struct sdmd_server_s {
@@ -99,26 +101,36 @@ int activate(sdmd_server_s* s, int32_t sid) {
 void drop_graph(TickGraph& t) {
   if (t.exec) cudaGraphExecDestroy(t.exec);
   if (t.g) cudaGraphDestroy(t.g);
+  std::vector<sdmd_t> last;
+  last.swap(t.last);
   t = TickGraph();
+  t.last.swap(last);
+}
+
+int run_direct(sdmd_server_s* s, const sdmd::BatchPlan& plan) {
+  for (int i = 0; i < plan.ncopies; ++i)
+    if (cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, s->st) != cudaSuccess) {
+      cudaGetLastError();
+      return err(SDMD_ERR_CUDA, "sdmd_server_tick: copy failed");
+    }
+  if (sdmd::launch_gram_rows_batched(plan.args, s->st) != cudaSuccess) {
+    cudaGetLastError();
+    return err(SDMD_ERR_CUDA, "sdmd_server_tick: batched launch failed");
+  }
+  return SDMD_OK;
 }
 
 // Issue one planned batch on the server stream: as a graph (built or
 // updated) or, with graphs off, as copies plus a kernel launch.
+// A set of streams gets a graph once it has come twice in a row at a batch
+// position (a steady set); sets that change every tick launch directly.
 int run_batch(sdmd_server_s* s, size_t b, const std::vector<sdmd_t>& hs, const sdmd::BatchPlan& plan) {
-  if (!s->graphs) {
-    for (int i = 0; i < plan.ncopies; ++i)
-      if (cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, s->st) != cudaSuccess) {
-        cudaGetLastError();
-        return err(SDMD_ERR_CUDA, "sdmd_server_tick: copy failed");
-      }
-    if (sdmd::launch_gram_rows_batched(plan.args, s->st) != cudaSuccess) {
-      cudaGetLastError();
-      return err(SDMD_ERR_CUDA, "sdmd_server_tick: batched launch failed");
-    }
-    return SDMD_OK;
-  }
+  if (!s->graphs) return run_direct(s, plan);
   if (s->tg.size() <= b) s->tg.resize(b + 1);
   TickGraph& t = s->tg[b];
+  const bool steady = (t.exec && t.key == hs) || t.last == hs;
+  t.last = hs;
+  if (!steady) return run_direct(s, plan);
   cudaKernelNodeParams kp;
   if (sdmd::batched_kernel_config(plan.args, &kp) != cudaSuccess) {
     cudaGetLastError();

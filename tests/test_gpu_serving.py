@@ -189,7 +189,7 @@ def test_graph_ticks_equal_direct_ticks(cuda_device):
             for v in range(2):
                 S.sdmd_server_tick(srv[v])
         builds, updates = S.sdmd_server_graph_stats(srv[0])
-        assert builds >= 1 and updates >= 11
+        assert builds >= 1 and updates >= 9           # steady ticks: one build, then in-place updates
         assert S.sdmd_server_graph_stats(srv[1]) == (0, 0)
         for i, (k, n, m) in enumerate(specs):
             hs = [S.sdmd_server_handle(srv[v], sids[v][i]) for v in range(2)]
@@ -197,10 +197,12 @@ def test_graph_ticks_equal_direct_ticks(cuda_device):
             Ga = _gram_bytes(hs[0], c, k, S.sdmd_server_stream(srv[0]))
             Gb = _gram_bytes(hs[1], c, k, S.sdmd_server_stream(srv[1]))
             assert np.array_equal(Ga, Gb), specs[i]
-        S.sdmd_server_autotune(srv[0])                 # schedules re-picked; graphs rebuilt on the next tick
-        for i, (k, n, _) in enumerate(specs):
-            S.sdmd_server_submit(srv[0], sids[0][i], _frame(k, n, rng))
-        assert S.sdmd_server_tick(srv[0]) == len(specs)
+        builds = S.sdmd_server_graph_stats(srv[0])[0]
+        S.sdmd_server_autotune(srv[0])                 # schedules re-picked; graphs rebuilt when steady again
+        for _ in range(2):
+            for i, (k, n, _) in enumerate(specs):
+                S.sdmd_server_submit(srv[0], sids[0][i], _frame(k, n, rng))
+            assert S.sdmd_server_tick(srv[0]) == len(specs)
         assert S.sdmd_server_graph_stats(srv[0])[0] == builds + 1
         for i in range(len(specs)):
             assert S.sdmd_status(S.sdmd_server_handle(srv[0], sids[0][i]), S.sdmd_server_stream(srv[0])) == S.SDMD_OK
