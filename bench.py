@@ -238,6 +238,7 @@ def measure_isolated(S, h, frames, t0, stream, phi, n, steps=8):
     lam = torch.empty(2 * R_MODES, dtype=torch.float64, device=frames.device)
     S.sdmd_sync(h, sh)
     stream.synchronize()
+    chunk, tuned_us = S.sdmd_autotune(h, sh)          # the Gram-row schedule picked by measurement
     S.sdmd_trace(h, True)
     with torch.cuda.stream(stream):
         for i in range(steps):
@@ -251,6 +252,8 @@ def measure_isolated(S, h, frames, t0, stream, phi, n, steps=8):
         out[name] = {"launches": cnt, "us": 1e3 * ms / max(cnt, 1)}
     S.sdmd_trace(h, False)
     out["gram_row"]["GB/s"] = M_WIN * n / (out["gram_row"]["us"] * 1e-6) / 1e9
+    out["gram_row"]["autotuned_chunk_bytes"] = chunk
+    out["gram_row"]["autotune_us"] = tuned_us
     out["phi"]["GB/s"] = ((M_WIN - 1) * n + n * R_MODES * 8) / (out["phi"]["us"] * 1e-6) / 1e9
     out["serial_step_us"] = sum(out[k]["us"] for k in ("gram_row", "phi", "modes_small_f64", "ingest_copy"))
     # streaming background subtraction of the newest frame (Algorithm 3):
