@@ -13,11 +13,15 @@ from paper_1612_07875_gb300 import synth
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("kind,depth", [("u8", 4), ("f32", 3), ("u8", 1)])
-def test_pipelined_step_equals_serial(cuda_device, kind, depth):
-    m, r = 12, 5
+@pytest.mark.parametrize("kind,depth,m", [("u8", 4, 12), ("f32", 3, 12), ("u8", 1, 12), ("u8", 2, 12), ("u8", 6, 12),
+                                          ("u8", 3, 130)])
+def test_pipelined_step_equals_serial(cuda_device, kind, depth, m):
+    # uint8 with depth >= 2: each frame's Phi runs fused with the Gram row
+    # depth - 1 frames later (depth 2: the new window starts at the first
+    # staged row; m = 130: K padded to 160, eight units per converter lane)
+    r = 5
     if kind == "u8":
-        vs = synth.VideoStream(H=60, W=80, C=3, seed=synth.config_seed(2))
+        vs = synth.VideoStream(H=60 if m < 100 else 24, W=80 if m < 100 else 40, C=3, seed=synth.config_seed(2))
         n = vs.n
         frames = [vs.frame(t) for t in range(3 * (m + depth) + 5)]
         dt = S.SDMD_U8
