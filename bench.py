@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the rebuild and Fourier-sparse measurements")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--scpu-seconds", type=float, default=3.0,
+                    help="seconds of the streaming CPU Gram update (host cores)")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served Poisson-arrival run (0 skips the serving measurement)")
     return ap.parse_args()
@@ -109,6 +111,34 @@ def oracle_rate(band_frames, n_total, seconds):
     info = {"steps": steps, "seconds": el, "band_pixels": band,
             "threads": max(native.num_threads(), _blas_threads())}
     return rate_full, info
+
+
+def streaming_cpu_rate(frames, seconds):
+    """The streaming method on the host cores (Sec. 3.1, Eq. 12a-b; the
+    paper's streaming CPU configuration): per push, the frame's copy into a
+    100-slot host ring, its 100 exact int64 inner products and G's row and
+    column, threaded over position blocks. Full HD frames; frames is (T, n)
+    uint8, generated before timing (the cost does not depend on the values)."""
+    from oracle import native
+    T, n = frames.shape
+    sc = native.StreamingCPU(n, M_WIN, "u8")
+    sc.fill(frames)
+    sc.push(frames[0])                                   # untimed warm-up push
+    k = 0
+    t0 = time.perf_counter()
+    while True:
+        sc.push(frames[k % T])
+        k += 1
+        if k >= 3 and time.perf_counter() - t0 >= seconds:
+            break
+    el = time.perf_counter() - t0
+    rate = k / el
+    return {"value": rate, "unit": UNIT, "cores": native.scpu_threads(),
+            "kind": "streaming CPU method: per push, ingest + %d exact int64 dot products + G row/column "
+                    "(the Gram update only: no eigensolve, no Phi)" % M_WIN,
+            "sample": "%d pushes of full %d-pixel frames into a %d-slot host ring, %.1f s" % (k, n, M_WIN, el),
+            "GB/s": rate * M_WIN * n / 1e9,
+            "gpu_counterpart": "kernels_isolated.gram_row (the same update on the GPU)"}
 
 
 def _blas_threads():
@@ -815,6 +845,9 @@ def run_ours(args):
         catchup = measure_catchup(S, h, frames, 0, stream, n)
     S.sdmd_destroy(h)
     band_frames = frames[:, :n // 64].cpu().numpy()     # CPU oracle sample (generated above)
+    scpu_frames = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scpu_frames = frames[:4].cpu().numpy()          # streaming CPU sample
     del frames
     torch.cuda.empty_cache()
     # ---- a10: Fourier-sparse Gram row, 1024x1024 field, nnz 10,486, m = 64
@@ -831,8 +864,9 @@ def run_ours(args):
     if not args.no_secondary and args.serve_seconds > 0:
         serving = measure_serving(S, synth, dev, args.serve_seconds)
 
-    cpu = None
+    cpu = scpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        scpu = streaming_cpu_rate(scpu_frames, args.scpu_seconds)
         rate, info = oracle_rate(band_frames, n, args.cpu_sample_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": info["threads"], "kind": "oracle",
                "sample": "%d oracle steps (exact int64 Gram recompute + dense FP64 DMD r=10) on a "
@@ -878,6 +912,7 @@ def run_ours(args):
         "fp32_bf16x3": bf16x3,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "cpu_streaming": scpu,
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -1,7 +1,8 @@
 """CPU oracle for streaming method-of-snapshots DMD (arXiv 1612.07875).
 
 THIS PACKAGE IS TEST INFRASTRUCTURE. Only ``tests/``, ``__graft_entry__.smoke()``
-and ``bench.py`` (its ``cpu_baseline`` leg and ``--impl reference`` arm) may
+and ``bench.py`` (its CPU legs ``cpu_baseline`` and ``cpu_streaming`` and its
+``--impl reference`` arm) may
 import, call, link or execute anything under ``oracle/``. The product package
 ``paper_1612_07875_gb300`` never imports it, and the oracle imports nothing
 from the product package except the seeded input generators, which hold none
@@ -17,6 +18,10 @@ What the oracle computes, after every streamed snapshot, from scratch:
   Phi = X' V Sigma^-1 W;
 * the mode amplitudes from POD coefficients (Sec. 3.3, Eq. 14a-e) and the
   background mode of Algorithm 3.
+
+``native.StreamingCPU`` (C, ``stream_cpu.c``) is not a parity reference but the
+timed streaming CPU baseline: the streaming Gram update of Eq. 12a-b run on
+the host cores, pinned to the brute-force Gram of its ring.
 
 Equation numbers follow the order of the equations in the paper's LaTeX
 source: (1) X, (2) X = U Sigma V*, (3) X*X V = V Lambda, (4) U = X V Sigma^-1,

@@ -303,7 +303,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     const unsigned stg0 = smem_u32(stg);
     // fused Gram row: this warp's private copy of the new snapshot's tile
     // (lanes 0..7, 16 bytes each) per stage, and per step j the exact sum of
-    // <x_slot, x_new> over this lane's 16 positions
+    // <x_slot, x_new> over this lane's 16 positions (computed for every lane,
+    // branch-free, in two independent DP4A chains; lanes whose slot is not in
+    // the new window drop their sums at the end)
     uint8_t* xnw = smem + L.xn_off + cw * kTileM;       // stage s at + s * kMaxConvWarps * kTileM
     const int64_t xsrc = dots ? tab[a.ktot - 1] + 16 * (lane & 7) : 0;
     unsigned long long gacc[kIpt];
@@ -362,17 +364,16 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) w[j] = *reinterpret_cast<const uint4*>(sb + sto[j]);
         if (dots) {
+          const uint4 xv0 = *reinterpret_cast<const uint4*>(xb + 16 * (lane >> 3));
+          const uint4 xv1 = *reinterpret_cast<const uint4*>(xb + 16 * (4 + (lane >> 3)));
 #pragma unroll
           for (int j = 0; j < kIpt; ++j) {
-            if (gslot[j]) {
-              const int pc = 4 * ((cw + conv_warps * j) & 1) + (lane >> 3);
-              const uint4 xv = *reinterpret_cast<const uint4*>(xb + 16 * pc);
-              unsigned d = __dp4a(w[j].x, xv.x, 0u);
-              d = __dp4a(w[j].y, xv.y, d);
-              d = __dp4a(w[j].z, xv.z, d);
-              d = __dp4a(w[j].w, xv.w, d);
-              gacc[j] += d;
-            }
+            const uint4 xv = ((cw + conv_warps * j) & 1) ? xv1 : xv0;
+            unsigned d0 = __dp4a(w[j].x, xv.x, 0u);
+            unsigned d1 = __dp4a(w[j].y, xv.y, 0u);
+            d0 = __dp4a(w[j].z, xv.z, d0);
+            d1 = __dp4a(w[j].w, xv.w, d1);
+            gacc[j] += (unsigned long long)(d0 + d1);
           }
         }
 #pragma unroll
