@@ -72,6 +72,29 @@ def dist_env():
     return rank, world, local
 
 
+def rank_seed(base, rank):
+    """Seed of a rank's video: every rank streams its own independent video
+    (the workload partitions into independent streams; no data exchange)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's timed region (each rank times its own, between two
+    barriers); on one rank, its own."""
+    if world == 1:
+        return float(ms)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def job_rate(world, steps, t_max_ms):
+    """Whole-job throughput: the steps of every rank over the slowest rank's time."""
+    return world * steps / (t_max_ms / 1e3)
+
+
 def workload_config(n, extra=None):
     cfg = {"workload": "hd_video_u8: n=1920x1080x3 uint8, window m=100, DMD rank r=10, "
                        "one frame per step (push + modes)",
@@ -716,7 +739,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     K, Wm = args.steps, max(args.warmup, 3)
-    vs = synth.VideoStream(seed=synth.config_seed(2) + 1000 * rank)
+    vs = synth.VideoStream(seed=rank_seed(synth.config_seed(2), rank))
     n = vs.n
     nframes = M_WIN + Wm + K
     # every frame of the run resident in HBM before timing
@@ -773,12 +796,8 @@ def run_ours(args):
     if S.sdmd_status(h, sh) != S.SDMD_OK:
         raise RuntimeError("device status after timed region: " + S.sdmd_last_error())
     per_step = frame_ms if frame_ms.size else np.array([total_ms / K])
-    t_max = total_ms
-    if world > 1:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * K / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = job_rate(world, K, t_max)
 
     # ---- the same kernels launched one at a time (no overlap): per-kernel
     #      durations without contention, for the kernel rooflines
@@ -827,6 +846,8 @@ def run_ours(args):
         r_h = torch.empty(Ke, dtype=torch.int32).pin_memory()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        if world > 1:
+            dist.barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         with torch.cuda.stream(stream):
@@ -835,8 +856,8 @@ def run_ours(args):
             S.sdmd_sync(h, sh)
         e1.record(stream)
         stream.synchronize()
-        ems = e0.elapsed_time(e1)
-        e2e = {"value": world * Ke / (ems / 1e3), "unit": UNIT, "h2d_bytes_per_step": n,
+        ems = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        e2e = {"value": job_rate(world, Ke, ems), "unit": UNIT, "h2d_bytes_per_step": n,
                "d2h_bytes_per_step": 2 * R_MODES * 8 + 4, "steps": Ke}
     # ---- a9: full-window rebuild of G; f2: multi-column catch-up of 8 frames
     rebuild = sparse = catchup = None
