@@ -67,3 +67,58 @@ def test_pipelined_step_equals_serial(cuda_device, kind, depth, m):
     finally:
         S.sdmd_destroy(hp)
         S.sdmd_destroy(hs)
+
+
+def test_full_size_hd_video_pipelined_depth10(cuda_device):
+    # The benchmark's launch configuration: n = 1920*1080*3 uint8, m = 100,
+    # r = 10, sdmd_step with 10 frames in flight (each frame's Phi fused with
+    # the Gram row of the frame nine steps later, K = 108 slots per tile).
+    # Against the oracle: the final G exactly, and for two of the last frames
+    # the rank, the eigenvalues (1e-6) and 64 sampled rows of Phi (1e-4 of
+    # each column's largest sampled entry, after fixing the column's phase).
+    import oracle
+    from helpers import match_eigs
+    vs = synth.VideoStream(seed=synth.config_seed(2))
+    n, m, r, D = vs.n, 100, 10, 10
+    T = m + D + 6
+    frames = [vs.frame(t) for t in range(T)]
+    dev_frames = [torch.from_numpy(f).to(cuda_device) for f in frames]
+    h = S.sdmd_create_ex(n, m, S.SDMD_U8, D)
+    phis = [torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device) for _ in range(D)]
+    lam = torch.zeros(T, 2 * r, dtype=torch.float64, device=cuda_device)
+    rk = torch.zeros(T, dtype=torch.int32, device=cuda_device)
+    stream = torch.cuda.Stream(device=cuda_device)
+    try:
+        with torch.cuda.stream(stream):
+            for t in range(T):
+                S.sdmd_step(h, dev_frames[t], r, phis[t % D], lam[t], rk[t:t + 1], stream)
+            S.sdmd_sync(h, stream)
+        stream.synchronize()
+        assert S.sdmd_status(h) == S.SDMD_OK
+        G = torch.empty(m, m, dtype=torch.int64, device=cuda_device)
+        S.sdmd_gram(h, G)
+        torch.cuda.synchronize()
+        Gall = oracle.gram_u8_cols(frames)                      # exact, all T frames
+        assert np.array_equal(G.cpu().numpy(), Gall[T - m:, T - m:])
+        lam_h = lam.cpu().numpy()
+        rk_h = rk.cpu().numpy()
+        rows = np.random.default_rng(2).integers(0, n, 64)
+        for t in (T - 1, T - D):
+            Gw = Gall[t - m + 1:t + 1, t - m + 1:t + 1].astype(np.float64)
+            ref = oracle.dmd_from_gram(Gw[:-1, :-1], Gw[:-1, 1:], r)
+            k = int(rk_h[t])
+            assert k == ref.r, t
+            got_lam = lam_h[t, 0::2] + 1j * lam_h[t, 1::2]
+            err, perm = match_eigs(got_lam[:k], ref.lam)
+            assert err <= 1e-6, (t, err)
+            P = phis[t % D].cpu().numpy()
+            got = (P[..., 0] + 1j * P[..., 1]).T[rows, :k]
+            Xp_rows = np.stack([frames[s][rows] for s in range(t - m + 2, t + 1)], axis=1).astype(np.float64)
+            Pref = Xp_rows @ ref.M[:, perm]
+            scale = np.abs(Pref).max(axis=0)
+            for q in range(k):
+                i = int(np.argmax(np.abs(Pref[:, q])))
+                got[:, q] *= (Pref[i, q] / got[i, q]) / abs(Pref[i, q] / got[i, q])
+            assert (np.abs(got - Pref).max(axis=0) <= 1e-4 * scale).all(), t
+    finally:
+        S.sdmd_destroy(h)
