@@ -440,6 +440,22 @@ enum {
                                for FP32 inputs) and FP64 sums, the reference
                                precision (GB300 runs FP64 at a small fraction
                                of FP32: several times slower) */
+    ,
+    SDMD_OPT_HOST_EARLY_READ = 5 /* 0 (default): a snapshot in host memory is
+                               read in stream order, like a device one; 1: a
+                               snapshot in pinned (page-locked) host memory
+                               given to sdmd_push / sdmd_step is copied as
+                               soon as the call is made, on the handle's own
+                               copy stream into one of two device staging
+                               slots, so the transfer overlaps the kernels
+                               queued before the call; the stream then waits
+                               for it and moves it into the ring. The host
+                               buffer must hold the snapshot when the call is
+                               made (not only when the stream reaches it) and
+                               must not change until the stream passes the
+                               push. Costs 2 x n x element size of device
+                               memory. Dense handles only (sparse:
+                               SDMD_ERR_UNSUPPORTED). */
 };
 
 /* sdmd_set_option -- set a handle option (SDMD_OPT_*). Host-side only. */

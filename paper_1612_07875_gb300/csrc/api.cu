@@ -73,6 +73,12 @@ struct sdmd_s {
   int32_t rebuild_tensor = 1; // SDMD_OPT_REBUILD_TENSOR
   int32_t f32_bf16x3 = 0;     // SDMD_OPT_F32_BF16X3 (0 off, 1 three terms, 2 two terms)
   int32_t f32_fp64 = 0;       // SDMD_OPT_F32_FP64
+  int32_t host_early = 0;     // SDMD_OPT_HOST_EARLY_READ
+  cudaStream_t cst = nullptr; // its copy stream, two staging slots and events (made on first use)
+  uint8_t* stage = nullptr;
+  cudaEvent_t ev_h2d = nullptr;
+  cudaEvent_t ev_stage_free[2] = {nullptr, nullptr};
+  int64_t stage_i = 0;
   long long* gf_partials = nullptr;  // tensor-core rebuild: per-CTA sums (allocated on first use)
   unsigned* gf_sched = nullptr;      // tensor-core rebuild: chunk counter
   // sparse handles
@@ -250,6 +256,11 @@ void free_all(sdmd_s* h) {
   cudaFree(h->gf_partials);
   cudaFree(h->gf_sched);
   cudaFree(h->fgpart);
+  cudaFree(h->stage);
+  if (h->ev_h2d) cudaEventDestroy(h->ev_h2d);
+  for (cudaEvent_t e : h->ev_stage_free)
+    if (e) cudaEventDestroy(e);
+  if (h->cst) cudaStreamDestroy(h->cst);
 }
 
 inline int32_t resident(const sdmd_s* h) { return (int32_t)(h->count < h->m ? h->count : h->m); }
@@ -530,8 +541,57 @@ int sdmd_destroy(sdmd_t h) {
 
 namespace {
 
+bool is_pinned_host(const void* x) {
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, x) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeHost;
+}
+
+// The copy stream, two staging slots and their events of
+// SDMD_OPT_HOST_EARLY_READ (made on first use).
+int ensure_stage(sdmd_s* h) {
+  if (h->stage) return SDMD_OK;
+  if (cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_h2d, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_stage_free[0], cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_stage_free[1], cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SDMD_ERR_CUDA, "host early read: stream or event creation failed");
+  }
+  if (cudaMalloc(&h->stage, 2 * (size_t)h->slot_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    h->stage = nullptr;
+    return fail(SDMD_ERR_OOM, "host early read: staging allocation failed");
+  }
+  return SDMD_OK;
+}
+
 // Ingest into slot `head` (after every in-flight reader of that slot).
+// With SDMD_OPT_HOST_EARLY_READ, a snapshot in pinned host memory is copied
+// at once on the handle's copy stream into one of two staging slots (after
+// the push stream has moved that slot's previous snapshot into the ring), so
+// the host-to-device transfer overlaps the kernels queued before it; the push
+// stream then waits for it and copies device to device into the ring slot.
 int ingest(sdmd_s* h, const void* x, cudaStream_t st) {
+  if (h->host_early && is_pinned_host(x)) {
+    const int rc = ensure_stage(h);
+    if (rc != SDMD_OK) return rc;
+    const int b = (int)(h->stage_i++ & 1);
+    uint8_t* sb = h->stage + (int64_t)b * h->slot_bytes;
+    const size_t bytes = (size_t)(h->n * h->elem);
+    CK(cudaStreamWaitEvent(h->cst, h->ev_stage_free[b], 0));
+    CK(cudaMemcpyAsync(sb, x, bytes, cudaMemcpyHostToDevice, h->cst));
+    CK(cudaEventRecord(h->ev_h2d, h->cst));
+    wait_ring_readers(h, st);
+    TraceScope ts(h, SDMD_K_INGEST, st);
+    CK(cudaStreamWaitEvent(st, h->ev_h2d, 0));
+    CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, sb, bytes, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(h->ev_stage_free[b], st));
+    return SDMD_OK;
+  }
   wait_ring_readers(h, st);
   TraceScope ts(h, SDMD_K_INGEST, st);
   CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, x, (size_t)(h->n * h->elem), cudaMemcpyDefault,
@@ -1183,6 +1243,10 @@ int sdmd_set_option(sdmd_t h, int32_t option, int64_t value) {
       return SDMD_OK;
     case SDMD_OPT_F32_FP64:
       h->f32_fp64 = value ? 1 : 0;
+      return SDMD_OK;
+    case SDMD_OPT_HOST_EARLY_READ:
+      if (h->dtype == SDMD_C64_SPARSE) return fail(SDMD_ERR_UNSUPPORTED, "sdmd_set_option: sparse handle");
+      h->host_early = value ? 1 : 0;
       return SDMD_OK;
     default:
       return fail(SDMD_ERR_ARG, "sdmd_set_option: unknown option %d", option);

@@ -31,6 +31,7 @@ SDMD_OPT_PHI_TENSOR = 1
 SDMD_OPT_REBUILD_TENSOR = 2
 SDMD_OPT_F32_BF16X3 = 3
 SDMD_OPT_F32_FP64 = 4
+SDMD_OPT_HOST_EARLY_READ = 5
 
 SDMD_RECON_MODES = 0
 SDMD_RECON_BACKGROUND = 1

@@ -128,3 +128,52 @@ def test_full_size_hd_video_pipelined_depth10(cuda_device):
             assert (np.abs(got - Pref).max(axis=0) <= 1e-4 * scale).all(), t
     finally:
         S.sdmd_destroy(h)
+
+
+def test_host_early_read_equals_device_frames(cuda_device):
+    # SDMD_OPT_HOST_EARLY_READ: pinned host frames copied on the handle's copy
+    # stream as soon as each call is made (two staging slots, then a device
+    # copy into the ring on the push stream). Every frame's eigenvalues, rank
+    # and modes, and the final G, equal those of the same frames given on the
+    # device; sdmd_push of host frames with the option gives the same G too.
+    vs = synth.VideoStream(H=60, W=80, C=3, seed=synth.config_seed(2) + 7)
+    n, m, depth, r = vs.n, 16, 4, 5
+    T = 3 * (m + depth) + 3
+    host = torch.from_numpy(np.stack([vs.frame(t) for t in range(T)])).pin_memory()
+    dev = host.to(cuda_device)
+    out = []
+    for early in (False, True):
+        h = S.sdmd_create_ex(n, m, S.SDMD_U8, depth)
+        if early:
+            S.sdmd_set_option(h, S.SDMD_OPT_HOST_EARLY_READ, 1)
+        phis = [torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device) for _ in range(depth)]
+        lam = torch.zeros(T, 2 * r, dtype=torch.float64, device=cuda_device)
+        rk = torch.zeros(T, dtype=torch.int32, device=cuda_device)
+        stream = torch.cuda.Stream(device=cuda_device)
+        try:
+            with torch.cuda.stream(stream):
+                for t in range(T):
+                    S.sdmd_step(h, host[t] if early else dev[t], r, phis[t % depth], lam[t], rk[t:t + 1], stream)
+                S.sdmd_sync(h, stream)
+            stream.synchronize()
+            assert S.sdmd_status(h) == S.SDMD_OK
+            G = torch.empty(m, m, dtype=torch.int64, device=cuda_device)
+            S.sdmd_gram(h, G)
+            torch.cuda.synchronize()
+            out.append((lam.cpu(), rk.cpu(), [p.cpu() for p in phis], G.cpu()))
+        finally:
+            S.sdmd_destroy(h)
+    (l0, r0, p0, g0), (l1, r1, p1, g1) = out
+    assert torch.equal(l0, l1) and torch.equal(r0, r1) and torch.equal(g0, g1)
+    assert all(torch.equal(a, b) for a, b in zip(p0, p1))
+    hs = S.sdmd_create(n, m, S.SDMD_U8)
+    try:
+        S.sdmd_set_option(hs, S.SDMD_OPT_HOST_EARLY_READ, 1)
+        for t in range(T):
+            S.sdmd_push(hs, host[t])
+        G = torch.empty(m, m, dtype=torch.int64, device=cuda_device)
+        S.sdmd_gram(hs, G)
+        torch.cuda.synchronize()
+        assert torch.equal(G.cpu(), g0)
+    finally:
+        S.sdmd_destroy(hs)
