@@ -556,6 +556,47 @@ def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
                                     "(support bitmap, prefix, compaction, gathers) on the same window"}}
 
 
+def measure_dense_complex(S, synth, dev, stream, m=64, pushes=20):
+    """The same 1024 x 1024 field pushed dense: the physical complex64 field
+    (the inverse transform of its coefficients) through the dense complex
+    Gram row, m = 64 -- the HBM-bound alternative to the sparse row (Sec. 3.5:
+    both give the same Gram by Parseval). Frames cycle through 8 fields
+    generated before timing (the row's cost does not depend on the values)."""
+    import torch
+    fs = synth.FourierSparseStream(seed=synth.config_seed(3))
+    n = fs.N
+    X = torch.stack([torch.from_numpy(fs.physical(t).astype(np.complex64).view(np.float32)) for t in range(8)])
+    X = X.to(dev)
+    sh = stream.cuda_stream
+    h = S.sdmd_create(n, m, S.SDMD_C64)
+    try:
+        for t in range(m + 2):
+            S.sdmd_push(h, X[t % 8], sh)
+        stream.synchronize()
+        S.sdmd_trace(h, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t in range(pushes):
+            S.sdmd_push(h, X[t % 8], sh)
+        e1.record(stream)
+        stream.synchronize()
+        tot = e0.elapsed_time(e1)
+        rl, rms = S.sdmd_trace_read(h, S.SDMD_K_GRAM_ROW)
+        S.sdmd_trace(h, False)
+        ok = S.sdmd_status(h, sh) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h)
+    peak, peak_kind = measured_peaks()
+    row_us = 1e3 * rms / max(rl, 1)
+    nbytes = m * n * 8
+    return {"config": "1024x1024 complex64 physical field, window m=%d" % m,
+            "snapshots/s": pushes / (tot * 1e-3), "push_us": 1e3 * tot / pushes, "row_kernel_us": row_us,
+            "algorithmic_bytes_per_push": nbytes, "GB/s": nbytes / (row_us * 1e-6) / 1e9,
+            "frac_of_copy_peak": nbytes / (row_us * 1e-6) / 1e9 / peak if peak else None,
+            "status_ok": ok, "bound": "hbm"}
+
+
 def measure_serving(S, synth, dev, seconds, capacity_ticks=12):
     """Batched serving of 64 concurrent streams (FP32 and uint8 mixed, n
     log-uniform in [2^16, 2^22], m in {16..256}, Poisson arrivals at 10-120 Hz
@@ -884,6 +925,7 @@ def run_ours(args):
     # ---- a10: Fourier-sparse Gram row, 1024x1024 field, nnz 10,486, m = 64
     if not args.no_secondary:
         sparse = measure_sparse(S, synth, dev, stream)
+        sparse["dense_physical"] = measure_dense_complex(S, synth, dev, stream)
 
     # ---- FP32 window n = 2^22, m = 256: BF16x3 tensor-core catch-up / rebuild
     bf16x3 = None
