@@ -573,6 +573,7 @@ def measure_dense_complex(S, synth, dev, stream, m=64, pushes=20):
         for t in range(m + 2):
             S.sdmd_push(h, X[t % 8], sh)
         stream.synchronize()
+        chunk, _ = S.sdmd_autotune(h, sh)            # the Gram row's schedule for this shape
         S.sdmd_trace(h, True)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -594,7 +595,7 @@ def measure_dense_complex(S, synth, dev, stream, m=64, pushes=20):
             "snapshots/s": pushes / (tot * 1e-3), "push_us": 1e3 * tot / pushes, "row_kernel_us": row_us,
             "algorithmic_bytes_per_push": nbytes, "GB/s": nbytes / (row_us * 1e-6) / 1e9,
             "frac_of_copy_peak": nbytes / (row_us * 1e-6) / 1e9 / peak if peak else None,
-            "status_ok": ok, "bound": "hbm"}
+            "autotuned_chunk_bytes": chunk, "status_ok": ok, "bound": "hbm"}
 
 
 def measure_serving(S, synth, dev, seconds, capacity_ticks=12):
