@@ -498,3 +498,105 @@ def test_pins_catch_wrong_atilde_block(monkeypatch):
     monkeypatch.undo()
     miss = max(np.min(np.abs(evA - lam)) for lam in res.lam)
     assert miss > 1e-3
+
+
+# --------------------------------------- pins of the building blocks -------
+
+def test_cross_gram_brute_force_conjugates_first_operand():
+    # A^H B entry (i, j) = sum_k conj(A_ki) B_kj: a missing conjugate or a
+    # transposed operand fails (A and B differ in column count on purpose)
+    rng = np.random.default_rng(71)
+    A = rng.standard_normal((9, 3)) + 1j * rng.standard_normal((9, 3))
+    B = rng.standard_normal((9, 4)) + 1j * rng.standard_normal((9, 4))
+    C = oracle.cross_gram(A, B)
+    assert C.shape == (3, 4)
+    for i in range(3):
+        for j in range(4):
+            re = math.fsum((A[k, i].conjugate() * B[k, j]).real for k in range(9))
+            im = math.fsum((A[k, i].conjugate() * B[k, j]).imag for k in range(9))
+            assert abs(C[i, j] - complex(re, im)) <= 1e-13
+    Ar, Br = A.real, B.real
+    Cr = oracle.cross_gram(Ar, Br)
+    for i in range(3):
+        for j in range(4):
+            assert Cr[i, j] == pytest.approx(math.fsum(Ar[k, i] * Br[k, j] for k in range(9)), abs=1e-13)
+
+
+def test_gram_u8_cols_brute_force_python_ints():
+    rng = np.random.default_rng(72)
+    cols = [rng.integers(0, 256, 301, dtype=np.uint8) for _ in range(5)]
+    cols[2][:] = 255                                   # the largest products
+    G = oracle.gram_u8_cols(cols)
+    ref = _brute_gram([[int(v) for v in c] for c in cols])
+    assert [[int(x) for x in row] for row in G] == ref
+
+
+def test_densify_sparse_round_trip_and_parseval_inner():
+    rng = np.random.default_rng(73)
+    n = 50
+    ia = np.sort(rng.choice(n, 12, replace=False)).astype(np.int32)
+    ib = np.sort(rng.choice(n, 15, replace=False)).astype(np.int32)
+    va = (rng.standard_normal(12) + 1j * rng.standard_normal(12)).astype(np.complex64)
+    vb = (rng.standard_normal(15) + 1j * rng.standard_normal(15)).astype(np.complex64)
+    da = oracle.densify_sparse(ia, va, n)
+    assert da.shape == (n,) and da.dtype == np.complex128
+    assert np.array_equal(da[ia], va.astype(np.complex128))
+    mask = np.ones(n, bool)
+    mask[ia] = False
+    assert not da[mask].any()
+    db = oracle.densify_sparse(ib, vb, n)
+    assert abs(oracle.sparse_inner(ia, va, ib, vb) - np.vdot(da, db)) <= 1e-12
+
+
+def test_numerical_rank_threshold_hand_built():
+    # rule: lambda_k > lambda_1 * 64 * p * eps64, strictly
+    p = 10
+    thr = 1.0 * odmd.RANK_RTOL_FACTOR * p * odmd.EPS64
+    assert oracle.numerical_rank([1.0, 1e-3, 1e-16], p) == 2
+    assert oracle.numerical_rank([1.0, thr * 1.0000001, thr * 0.5], p) == 2
+    assert oracle.numerical_rank([1.0, thr, 0.0], p) == 1          # at the threshold: dropped
+    assert oracle.numerical_rank([2.0, 1.0, 0.5], p) == 3
+    assert oracle.numerical_rank([0.0, 0.0], p) == 0
+    assert oracle.numerical_rank([-1.0, -2.0], p) == 0
+    assert oracle.numerical_rank([], p) == 0
+
+
+def test_dmd_from_gram_planted_system_from_gram_blocks_only():
+    # the small-matrix part given only G_X = X^T X and G_XY = X^T X' of a
+    # planted noise-free linear system recovers the planted eigenvalues and,
+    # through X' M, the modes; the transposed cross block (X'^T X) gives
+    # A~ transposed: the same eigenvalues but left eigenvectors, so modes that
+    # are not the planted ones
+    ps = synth.PlantedStream(side=16, noise_var=0.0, seed=31)
+    F = ps.fields
+    W = np.zeros((ps.n, 12))
+    for t in range(12):
+        for q in range(ps.n_pairs):
+            zz = ps.c_pairs[q] * ps.lam_pairs[q] ** t
+            W[:, t] += zz.real * F[:, 2 * q] + zz.imag * F[:, 2 * q + 1]
+        W[:, t] += ps.c_real[0] * ps.lam_real[0] ** t * F[:, 4]
+    X, Xp = W[:, :-1], W[:, 1:]
+    GX = X.T @ X
+    GXY = X.T @ Xp
+    res = oracle.dmd_from_gram(GX, GXY, 10)
+    assert res.r == 5 and res.Phi is None
+    planted = ps.planted_lambdas()
+    for lp in planted:
+        assert np.min(np.abs(res.lam - lp)) < 1e-10
+    # M = vsi W maps X' to the modes: X' M equals exact_dmd's Phi
+    ref = oracle.exact_dmd(W, 10)
+    assert np.allclose(Xp @ res.M, ref.Phi, rtol=0, atol=1e-10 * np.abs(ref.Phi).max())
+    modes = ps.planted_modes()
+
+    def worst_cos(res_):
+        Phi = Xp @ res_.M
+        worst = 1.0
+        for k in range(res_.r):
+            j = int(np.argmin(np.abs(planted - res_.lam[k])))
+            a, b = Phi[:, k], modes[:, j]
+            worst = min(worst, abs(np.vdot(a, b)) / (np.linalg.norm(a) * np.linalg.norm(b)))
+        return worst
+
+    assert worst_cos(res) > 1 - 1e-10
+    wrong = oracle.dmd_from_gram(GX, GXY.T, 10)
+    assert worst_cos(wrong) < 1 - 1e-6
