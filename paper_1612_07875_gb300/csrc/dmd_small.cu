@@ -701,9 +701,14 @@ struct SmemPlan {
   int a_in_smem;
   int rr_in_smem;
   int eig_in_smem;
+  int inv_in_smem;       // inverse-iteration LU, Ritz scratch and vectors Z in shared memory
   int rr_dim;            // Rayleigh-Ritz size limit: r plus the cluster extension
-  int64_t P, vec_units, rr_units, big_units;
+  int64_t P, vec_units, rr_units, big_units, inv_units;
 };
+
+// Dynamic shared memory the plan may use (8-byte units): the SM's 227 KiB
+// less the kernel's static arrays, with margin.
+constexpr int64_t kSmemDynUnits = (220 * 1024) / 8;
 
 __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   SmemPlan s;
@@ -718,6 +723,12 @@ __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   const int64_t a = s.a_in_smem ? (int64_t)p * p : 0;
   const int64_t g = s.eig_in_smem ? (int64_t)5 * r * r : 0;   // H, Q, W, U, y (complex float)
   s.big_units = a > g ? a : g;
+  // the inverse iteration's working set (per vector: LU 5p, Ritz scratch p,
+  // the vector p) on chip when it fits: its tridiagonal recurrences are
+  // chains of dependent loads and stores
+  const int64_t inv = (int64_t)s.rr_dim * 7 * p;
+  s.inv_in_smem = (s.vec_units + s.rr_units + s.big_units + inv <= kSmemDynUnits);
+  s.inv_units = s.inv_in_smem ? inv : 0;
   return s;
 }
 
@@ -751,6 +762,11 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   dd* rrR = rrH + (int64_t)plan.rr_dim * plan.rr_dim;
   dd* big = base + plan.vec_units + plan.rr_units;
   dd* A = plan.a_in_smem ? big : w.Ad;
+  // inverse iteration: LU factors + Ritz scratch (rr_dim x 6p) and the vectors
+  // Z (rr_dim x p; later the eigenvectors, then vsi)
+  dd* inv_base = big + plan.big_units;
+  dd* LU = plan.inv_in_smem ? inv_base : w.lu;
+  dd* Z = plan.inv_in_smem ? inv_base + (int64_t)plan.rr_dim * 6 * p : w.Z;
   if (tid == 0) w.clk[0] = clock64();
 
   // ---- 0. scale (exact power of two from the largest diagonal), gather, convert
@@ -874,13 +890,13 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   for (int round = 0; round < 2; ++round) {
     const float sep = (round == 0) ? 2.f * kEps32 * tnorm : 1e-12f * tnorm;
     for (int i = tid; i < rwe; i += kThreads) {
-      dd* u0 = w.lu + (int64_t)i * 5 * p;
+      dd* u0 = LU + (int64_t)i * 5 * p;
       dd shift = lam[i];
       for (int q = 0; q < i; ++q)    // (numerically) equal shifts: separate them slightly
         if (fabsf(lam[q].hi - shift.hi) <= sep) shift = dd_sub(shift, dd_make(sep));
       tri_lu_dd(d, e, p, shift, tiny, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p);
       if (round == 0) {
-        dd* z = w.Z + (int64_t)i * p;
+        dd* z = Z + (int64_t)i * p;
         for (int j = 0; j < p; ++j)
           z[j] = dd_make(1.f + 0.1f * (float)(((j + 1) * 7919 + (i + 1) * 104729) % 97) / 97.f);
       }
@@ -888,19 +904,19 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
     __syncthreads();
     for (int it = 0; it < kInvIters; ++it) {
       for (int i = tid; i < rwe; i += kThreads) {
-        dd* u0 = w.lu + (int64_t)i * 5 * p;
-        tri_solve_dd(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, w.Z + (int64_t)i * p);
+        dd* u0 = LU + (int64_t)i * 5 * p;
+        tri_solve_dd(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, Z + (int64_t)i * p);
       }
       __syncthreads();
-      cgs_dd(w.Z, rwe, p, (it + 1 == kInvIters) ? 2 : 1, coef, red, sc);
+      cgs_dd(Z, rwe, p, (it + 1 == kInvIters) ? 2 : 1, coef, red, sc);
     }
-    rayleigh_ritz(w.Z, rwe, p, d, e, rrH, rrR, w.lu + (int64_t)rwe * 5 * p, lam, sc, ord);
+    rayleigh_ritz(Z, rwe, p, d, e, rrH, rrR, LU + (int64_t)rwe * 5 * p, lam, sc, ord);
   }
   if (tid == 0) w.clk[4] = clock64();
 
   // ---- 4. back-transform: v = H_0 H_1 ... H_{p-3} z  (warp per vector)
   for (int i = warp; i < rw; i += kWarps) {
-    dd* z = w.Z + (int64_t)i * p;
+    dd* z = Z + (int64_t)i * p;
     for (int k = p - 3; k >= 0; --k) {
       const int Lk = p - k - 1;
       const dd* v = A + (int64_t)k * p + (k + 1);
@@ -933,9 +949,9 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   __syncthreads();
   for (int idx = tid; idx < a.r_req * p; idx += kThreads) {
     const int i = idx / p;
-    const dd z = (i < re) ? w.Z[idx] : dd{0.f, 0.f};
+    const dd z = (i < re) ? Z[idx] : dd{0.f, 0.f};
     w.V[idx] = dd_to_double(z);
-    if (i < re) w.Z[idx] = dd_mul(z, coef[i]);
+    if (i < re) Z[idx] = dd_mul(z, coef[i]);
   }
   __syncthreads();
 
@@ -943,7 +959,7 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   for (int idx = tid; idx < re * p; idx += kThreads) {
     const int k = idx / p, row = idx - k * p;
     const dd* g = w.GXYd + (int64_t)row * p;
-    const dd* v = w.Z + (int64_t)k * p;
+    const dd* v = Z + (int64_t)k * p;
     dd s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
     int b = 0;
     for (; b + 1 < p; b += 2) {
@@ -962,7 +978,7 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   CF* yc = Uc + re * re;
   for (int idx = tid; idx < re * re; idx += kThreads) {
     const int k = idx / re, l = idx - k * re;
-    const dd* v = w.Z + (int64_t)k * p;
+    const dd* v = Z + (int64_t)k * p;
     const dd* y = w.Y + (int64_t)l * p;
     dd s = {0.f, 0.f};
     for (int b = 0; b < p; ++b) s = dd_fma(v[b], y[b], s);
@@ -1035,7 +1051,7 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
     if (k < re) {
       const int kk = ord[k];
       for (int l = 0; l < re; ++l) {
-        const dd z = w.Z[(int64_t)l * p + row];
+        const dd z = Z[(int64_t)l * p + row];
         const CF wv2 = Wc[l * re + kk];
         sr = dd_fma(z, dd_make(wv2.re), sr);
         si = dd_fma(z, dd_make(wv2.im), si);
@@ -1485,7 +1501,7 @@ int64_t modes_ws_doubles(int m) { return modes_layout(m).total; }
 cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
   static size_t attr_bytes = 0;   // dynamic shared memory opted in so far
   const SmemPlan plan = smem_plan(a.c - 1, a.r_req);
-  const size_t bytes = (size_t)(plan.vec_units + plan.rr_units + plan.big_units) * 8;
+  const size_t bytes = (size_t)(plan.vec_units + plan.rr_units + plan.big_units + plan.inv_units) * 8;
   if (bytes > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(modes_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
