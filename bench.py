@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--depth", type=int, default=10, help="DMD frames in flight (sdmd_step pipeline)")
+    ap.add_argument("--depth", type=int, default=8, help="DMD frames in flight (sdmd_step pipeline)")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the rebuild and Fourier-sparse measurements")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)

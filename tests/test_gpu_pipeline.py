@@ -75,17 +75,19 @@ def test_pipelined_step_equals_serial(cuda_device, kind, depth, m, r):
         S.sdmd_destroy(hs)
 
 
-def test_full_size_hd_video_pipelined_depth10(cuda_device):
+@pytest.mark.parametrize("D", [8, 10])
+def test_full_size_hd_video_pipelined(cuda_device, D):
     # The benchmark's launch configuration: n = 1920*1080*3 uint8, m = 100,
-    # r = 10, sdmd_step with 10 frames in flight (each frame's Phi fused with
-    # the Gram row of the frame nine steps later, K = 108 slots per tile).
+    # r = 10, sdmd_step with D frames in flight (each frame's Phi fused with
+    # the Gram row of the frame D - 1 steps later: 106 or 108 union slots,
+    # K = 112; the bench default is 8).
     # Against the oracle: the final G exactly, and for two of the last frames
     # the rank, the eigenvalues (1e-6) and 64 sampled rows of Phi (1e-4 of
     # each column's largest sampled entry, after fixing the column's phase).
     import oracle
     from helpers import match_eigs
     vs = synth.VideoStream(seed=synth.config_seed(2))
-    n, m, r, D = vs.n, 100, 10, 10
+    n, m, r = vs.n, 100, 10
     T = m + D + 6
     frames = [vs.frame(t) for t in range(T)]
     dev_frames = [torch.from_numpy(f).to(cuda_device) for f in frames]
