@@ -270,15 +270,19 @@ inline int32_t oldest_slot(const sdmd_s* h) { return (int32_t)((h->count - resid
 // earlier), wait for every in-flight DMD whose X' still contains it.
 int flush_pending(sdmd_s* h, cudaStream_t st);
 
-void wait_ring_readers(sdmd_s* h, cudaStream_t st) {
+int wait_ring_readers(sdmd_s* h, cudaStream_t st) {
   const int64_t t = h->count;
   for (PipeCtx& c : h->ctx) {
     if (c.busy && c.frame - h->m + 2 <= t - h->cap) {
-      if (c.phi_pending) flush_pending(h, st);   // its Phi must run before the slot is reused
-      cudaStreamWaitEvent(st, c.ev_done, 0);
+      if (c.phi_pending) {                     // its Phi must run before the slot is reused
+        const int rc = flush_pending(h, st);
+        if (rc != SDMD_OK) return rc;
+      }
+      CK(cudaStreamWaitEvent(st, c.ev_done, 0));
       c.busy = false;
     }
   }
+  return SDMD_OK;
 }
 
 // Phi arguments of a pipelined frame (its window, its modes workspace).
@@ -585,14 +589,20 @@ int ingest(sdmd_s* h, const void* x, cudaStream_t st) {
     CK(cudaStreamWaitEvent(h->cst, h->ev_stage_free[b], 0));
     CK(cudaMemcpyAsync(sb, x, bytes, cudaMemcpyHostToDevice, h->cst));
     CK(cudaEventRecord(h->ev_h2d, h->cst));
-    wait_ring_readers(h, st);
+    {
+      const int rc = wait_ring_readers(h, st);
+      if (rc != SDMD_OK) return rc;
+    }
     TraceScope ts(h, SDMD_K_INGEST, st);
     CK(cudaStreamWaitEvent(st, h->ev_h2d, 0));
     CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, sb, bytes, cudaMemcpyDeviceToDevice, st));
     CK(cudaEventRecord(h->ev_stage_free[b], st));
     return SDMD_OK;
   }
-  wait_ring_readers(h, st);
+  {
+    const int rc = wait_ring_readers(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
   TraceScope ts(h, SDMD_K_INGEST, st);
   CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, x, (size_t)(h->n * h->elem), cudaMemcpyDefault,
                      st));
@@ -699,7 +709,10 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   const int rc0 = ensure_gram_full_scratch(h);
   if (rc0 != SDMD_OK) return rc0;
   for (int j = 0; j < k; ++j) {        // ingest only
-    wait_ring_readers(h, st);
+    {
+      const int rc = wait_ring_readers(h, st);
+      if (rc != SDMD_OK) return rc;
+    }
     TraceScope ts(h, SDMD_K_INGEST, st);
     CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, src + (size_t)j * ld * elem_bytes,
                        (size_t)(h->n * h->elem), cudaMemcpyDefault, st));
@@ -749,7 +762,10 @@ extern "C++" int sdmd::push_many_plan(sdmd_t const* hs, const void* const* xs, i
   plan->ncopies = count;
   for (int i = 0; i < count; ++i) {
     sdmd_s* h = hs[i];
-    wait_ring_readers(h, st);
+    {
+      const int rc = wait_ring_readers(h, st);
+      if (rc != SDMD_OK) return rc;
+    }
     const int32_t s_new = h->head;
     plan->dst[i] = h->ring + (int64_t)s_new * h->slot_bytes;
     plan->src[i] = xs[i];
