@@ -84,3 +84,22 @@ def test_argument_errors_need_no_gpu(built):
 def test_graft_entry_build_runs(built):
     import __graft_entry__ as g
     g.build()
+
+
+def test_binding_constants_match_header():
+    # every enum value and size limit the header defines (dtypes, statuses,
+    # options, reconstruction kinds, trace classes, stream states, maxima)
+    # has the same value in the Python binding
+    from paper_1612_07875_gb300 import sdmd
+    txt = ""
+    inc = os.path.join(ROOT, "include")
+    for f in os.listdir(inc):
+        if f.endswith(".h"):
+            txt += open(os.path.join(inc, f)).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    consts = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(SDMD_[A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    consts.update({m.group(1): int(m.group(2))
+                   for m in re.finditer(r"#define\s+(SDMD_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", txt)})
+    assert len(consts) > 20
+    for name, value in consts.items():
+        assert getattr(sdmd, name, None) == value, name
