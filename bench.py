@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--scpu-seconds", type=float, default=3.0,
                     help="seconds of the streaming CPU Gram update (host cores)")
+    ap.add_argument("--case", choices=["bf16x3_catchup", "batched_rows"], default=None,
+                    help="run one small fixed workload (for a profiler capture of its kernel) and exit")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served Poisson-arrival run (0 skips the serving measurement)")
     return ap.parse_args()
@@ -992,8 +994,61 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+def run_case(name):
+    """Small fixed workloads for profiler captures of one kernel each:
+    bf16x3_catchup: 128 random FP32 frames of n = 2^20 fill a window of 128,
+      then three sdmd_push_batch calls of k = 8 under SDMD_OPT_F32_BF16X3 = 1
+      (gram_f32_tc launches);
+    batched_rows: 24 streams of the serving mix (each window at most 200 MB)
+      take 260 frames each through sdmd_push_many (gram_rows_batched launches)."""
+    import torch
+
+    from paper_1612_07875_gb300 import sdmd as S
+    from paper_1612_07875_gb300 import synth
+    dev = torch.device("cuda", 0)
+    if name == "bf16x3_catchup":
+        n, m, k = 1 << 20, 128, 8
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        frames = torch.randn(m + k, n, device=dev, generator=g)
+        h = S.sdmd_create(n, m, S.SDMD_F32)
+        for t in range(m):
+            S.sdmd_push(h, frames[t])
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
+        for _ in range(3):
+            S.sdmd_push_batch(h, k, frames[m:m + k], n)
+        torch.cuda.synchronize()
+        ok = S.sdmd_status(h) == S.SDMD_OK
+        S.sdmd_destroy(h)
+        info = {"n": n, "m": m, "k": k, "launches": 3}
+    else:
+        mix = synth.ServingMix()
+        specs = [sp for sp in mix.specs if sp[2] * sp[1] * (1 if sp[0] == "u8" else 4) <= 200e6][:24]
+        dts = {"u8": S.SDMD_U8, "f32": S.SDMD_F32}
+        hs = [S.sdmd_create(n, m, dts[kind]) for kind, n, m, _ in specs]
+        g = torch.Generator(device=dev)
+        g.manual_seed(3)
+        pool = {"u8": torch.randint(0, 256, (mix.pool_len,), dtype=torch.uint8, device=dev, generator=g),
+                "f32": torch.randn(mix.pool_len, device=dev, generator=g)}
+        for j in range(260):
+            S.sdmd_push_many(hs, [pool[kind][mix.offset(i, j):mix.offset(i, j) + n]
+                                  for i, (kind, n, m, _) in enumerate(specs)])
+        torch.cuda.synchronize()
+        ok = all(S.sdmd_status(h) == S.SDMD_OK for h in hs)
+        for h in hs:
+            S.sdmd_destroy(h)
+        info = {"streams": len(specs), "launches": 260,
+                "GB_per_launch": sum(m * n * (1 if kind == "u8" else 4) for kind, n, m, _ in specs) / 1e9}
+    if not ok:
+        raise RuntimeError("device status after the %s case: %s" % (name, S.sdmd_last_error()))
+    print(json.dumps({"case": name, "ok": True, **info}), flush=True)
+
+
 def main():
     args = parse()
+    if args.case:
+        run_case(args.case)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
