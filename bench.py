@@ -6,12 +6,15 @@ through the whole hot path: ingest into the ring slot, Gram row (m dot
 products over n, exact int64), symmetric insert, FP64 eigensolvers
 (sym-eig of G_X, A~, eig of A~), and Phi = X' V Sigma^-1 W (n x r complex64).
 
-Printed JSON line (rank 0): snapshots/s over K timed steps (CUDA events on
-the launch stream, barrier + synchronize around the timed region), the
-Gram-row kernel's achieved HBM bandwidth against the measured copy peak,
-per-frame latency percentiles, an end-to-end figure through the C ABI with
-pinned host buffers, the CPU oracle timed on a bounded sample, and the SM
-clocks sampled during the timed region.
+Printed JSON line (rank 0): snapshots/s over K timed steps in steady state
+(CUDA events on the launch stream, barrier + synchronize around the timed
+region, tracing off; the pipeline of depth frames is full when the region
+opens and when it closes), then a traced pass of the same steps for the
+per-kernel durations (the fused Phi + Gram-row pass against the measured
+copy peak) and per-frame latency percentiles, an end-to-end figure through
+the C ABI with pinned host buffers (starts with an empty pipeline and ends
+with every frame's outputs delivered), the CPU oracle timed on a bounded
+sample, and the SM clocks sampled during the timed region.
 
 Secondary measurements in the same line: each kernel launched alone, the
 full-window rebuild (tensor cores vs row passes), the 8-frame catch-up, the
@@ -44,6 +47,7 @@ UNIT = "snapshots/s"
 H, W_, C_ = 1080, 1920, 3
 M_WIN = 100
 R_MODES = 10
+TRACED_STEPS = 40       # steps of the traced pass that follows the timed one
 
 
 def parse():
@@ -477,6 +481,7 @@ def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
             out["%s_sampled_error" % name] = {
                 "max_abs_err_over_sum_abs_products": err, "rel_frobenius": fro, "entries": int(sel.numel() ** 2),
                 "bound": bound, "reference": "FP64 dot products of the same FP32 frames (torch, on the GPU)"}
+        out["per_kappa"] = bf16x3_kappa_sweep(S, h, dev, stream, n, m)
         S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
         msr = timed(lambda: S.sdmd_rebuild(h, sh), r=2)
         S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
@@ -493,6 +498,135 @@ def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
         S.sdmd_destroy(h)
         del frames
         torch.cuda.empty_cache()
+
+
+def measure_config1(S, synth, dev, stream, n_snap=200, m=32, r=10, depths=(1, 4)):
+    """The planted-mode FP32 stream (n = 64 x 64, window m = 32, 200
+    snapshots, rank r = 10): every snapshot through sdmd_step (push + exact
+    DMD with Phi), device-resident snapshots, timed over the whole stream
+    (window ramp-up included, outputs complete at the end) at depth 1 (one
+    frame at a time) and with frames in flight; per-frame latency from the
+    frame trace of a second, traced run."""
+    import torch
+    ps = synth.PlantedStream(side=64, noise_var=1e-3, seed=synth.config_seed(1))
+    n = ps.n
+    X = torch.from_numpy(np.stack([ps.snapshot(t) for t in range(n_snap)])).to(dev)
+    sh = stream.cuda_stream
+    out = {"n": n, "m": m, "r": r, "snapshots": n_snap}
+    for D in depths:
+        res = {}
+        for traced in (False, True):
+            h = S.sdmd_create_ex(n, m, S.SDMD_F32, D)
+            phis = [torch.empty(r, n, 2, dtype=torch.float32, device=dev) for _ in range(max(D, 1))]
+            lam = torch.empty(n_snap, 2 * r, dtype=torch.float64, device=dev)
+            rk = torch.empty(n_snap, dtype=torch.int32, device=dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            try:
+                S.sdmd_trace(h, traced)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                with torch.cuda.stream(stream):
+                    for t in range(n_snap):
+                        S.sdmd_step(h, X[t], r, phis[t % len(phis)], lam[t], rk[t:t + 1], sh)
+                    S.sdmd_sync(h, sh)
+                e1.record(stream)
+                stream.synchronize()
+                if S.sdmd_status(h, sh) != S.SDMD_OK:
+                    raise RuntimeError("config-1 status: " + S.sdmd_last_error())
+                if traced:
+                    fm = np.array(S.sdmd_trace_times(h, S.SDMD_K_FRAME))
+                    if D == 1:
+                        fm = np.array([])
+                    ml, mms = S.sdmd_trace_read(h, S.SDMD_K_MODES)
+                    res["modes_us"] = 1e3 * mms / max(ml, 1)
+                    if fm.size:
+                        res["latency_ms"] = {"p50": float(np.percentile(fm, 50)),
+                                             "p99": float(np.percentile(fm, 99))}
+                else:
+                    ms = e0.elapsed_time(e1)
+                    res["snapshots_per_s"] = n_snap / (ms * 1e-3)
+                    res["ms_per_snapshot"] = ms / n_snap
+                    if D == 1:
+                        res["latency_ms"] = {"mean": ms / n_snap,
+                                             "note": "one frame at a time: the step time is the latency"}
+                S.sdmd_trace(h, False)
+            finally:
+                S.sdmd_destroy(h)
+        out["depth%d" % D] = res
+    out["note"] = ("FP32 rows (FP32 products, FP64 sums), df64 eigensolvers, CUDA-core Phi; the window "
+                   "(512 KiB) stays in L2, so the step is latency-bound, not HBM-bound")
+    return out
+
+
+def conditioned_window(cs, ts, dev):
+    """The conditioned-spectrum snapshots of synth.ConditionedStream for the
+    times ts (len(ts) x n FP32), built on the device from the stream's own
+    parameters (frequencies, cos/sin kind, geometric spectrum, seeded
+    temporal coefficients): the same recipe as ConditionedStream.snapshots,
+    evaluated in FP32 on the GPU because the host takes seconds per window at
+    n = 2^22 (both arms of every comparison below read these FP32 values)."""
+    import torch
+    n = cs.n
+    i = torch.arange(n, device=dev, dtype=torch.float64)
+    A = torch.from_numpy(np.stack([cs.coeffs(t) * cs.s for t in ts])).to(dev)            # T x K
+    X = torch.zeros(len(ts), n, device=dev, dtype=torch.float32)
+    for k in range(cs.K):
+        arg = (2.0 * np.pi * float(cs.freq[k]) / n) * i
+        b = (torch.cos(arg) if cs.phase_kind[k] == 0 else torch.sin(arg)).float()
+        X.add_(A[:, k:k + 1].float() * b[None, :])
+    X.mul_(float(np.sqrt(2.0)))          # sqrt(2 / n) of the basis times sqrt(n)
+    return X
+
+
+def bf16x3_kappa_sweep(S, h, dev, stream, n, m, kappas=(1e2, 1e4, 1e6, 1e8), k=8, ns=16):
+    """Gram error against host FP64 per condition number, at the precision
+    sweep's size: per kappa a planted-spectrum window of m snapshots is
+    pushed with FP32 rows, rebuilt with BF16x3, then moved by k snapshots
+    with one BF16x3 catch-up; each Gram's sampled ns x ns block (ns window
+    positions, including the k newest) is compared with FP64 dot products of
+    the same FP32 snapshots computed on the host with numpy (the oracle's
+    definition G = W^T W in FP64)."""
+    import torch
+    from paper_1612_07875_gb300 import synth
+    sh = stream.cuda_stream
+    G = torch.empty(m, m, dtype=torch.float64, device=dev)
+    rows = []
+    for kappa in kappas:
+        cs = synth.ConditionedStream(n=n, K=m, kappa=kappa, seed=synth.config_seed(4))
+        X = conditioned_window(cs, range(m + k), dev)
+        sel = np.unique(np.concatenate([np.linspace(0, m - k - 1, ns - k).round().astype(int),
+                                        np.arange(m - k, m)]))
+        entry = {"kappa_target": kappa}
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
+        with torch.cuda.stream(stream):
+            for t in range(m):
+                S.sdmd_push(h, X[t], sh)
+        for name, w0 in (("fp32_rows", 0), ("bf16x3_rebuild", 0), ("bf16x3_catch_up_k%d" % k, k)):
+            with torch.cuda.stream(stream):
+                if name == "bf16x3_rebuild":
+                    S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
+                    S.sdmd_rebuild(h, sh)
+                elif name.startswith("bf16x3_catch"):
+                    S.sdmd_push_batch(h, k, X[m:m + k], n, sh)
+                S.sdmd_gram(h, G, sh)
+            stream.synchronize()
+            Wh = X[w0 + sel].cpu().numpy().astype(np.float64)        # ns x n, exact FP32 values
+            ref = Wh @ Wh.T
+            bnd = np.abs(Wh) @ np.abs(Wh).T
+            got = G.cpu().numpy()[np.ix_(sel, sel)]
+            entry[name] = {"rel_frobenius": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                           "max_abs_err_over_sum_abs_products": float((np.abs(got - ref) / bnd).max())}
+        Gf = G.cpu().numpy()
+        lam = np.linalg.eigvalsh(Gf)
+        entry["cond_G_measured"] = float(lam.max() / max(lam.min(), 1e-300))
+        rows.append(entry)
+        del X
+        torch.cuda.empty_cache()
+    S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 0)
+    return {"n": n, "m": m, "sampled_entries": ns * ns, "kappas": rows,
+            "reference": "host FP64 (numpy) dot products of the same FP32 snapshots on a sampled "
+                         "block; the full-window comparison with the oracle is the test "
+                         "test_conditioned_full_size_kappa_1e8"}
 
 
 def measure_sparse(S, synth, dev, stream, m=64, pushes=40):
@@ -783,9 +917,10 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     K, Wm = args.steps, max(args.warmup, 3)
+    Kt = TRACED_STEPS
     vs = synth.VideoStream(seed=rank_seed(synth.config_seed(2), rank))
     n = vs.n
-    nframes = M_WIN + Wm + K
+    nframes = M_WIN + Wm + K + Kt
     # every frame of the run resident in HBM before timing
     frames = torch.empty(nframes, n, dtype=torch.uint8, device=dev)
     for t in range(nframes):
@@ -797,21 +932,31 @@ def run_ours(args):
     D = max(1, args.depth)
     h = S.sdmd_create_ex(n, M_WIN, S.SDMD_U8, D)
     phis = [torch.empty(R_MODES, n, 2, dtype=torch.float32, device=dev) for _ in range(D)]
-    lam = torch.empty(Wm + K, 2 * R_MODES, dtype=torch.float64, device=dev)
-    rdev = torch.empty(Wm + K, dtype=torch.int32, device=dev)
+    lam = torch.empty(Wm + K + Kt, 2 * R_MODES, dtype=torch.float64, device=dev)
+    rdev = torch.empty(Wm + K + Kt, dtype=torch.int32, device=dev)
+
+    def steps(i0, count):
+        with torch.cuda.stream(stream):
+            for i in range(i0, i0 + count):
+                S.sdmd_step(h, frames[M_WIN + i], R_MODES, phis[i % D], lam[i], rdev[i:i + 1], sh)
+
+    # warm-up: fill the window, then Wm pipelined steps; the pipeline stays
+    # full (depth - 1 frames' Phi still deferred) so the timed steps run in
+    # steady state
     with torch.cuda.stream(stream):
         for t in range(M_WIN):
             S.sdmd_push(h, frames[t], sh)
-        for i in range(Wm):
-            t = M_WIN + i
-            S.sdmd_step(h, frames[t], R_MODES, phis[i % D], lam[i], rdev[i:i + 1], sh)
-        S.sdmd_sync(h, sh)
+    steps(0, Wm)
     stream.synchronize()
     if S.sdmd_status(h, sh) != S.SDMD_OK:
         raise RuntimeError("device status after warmup: " + S.sdmd_last_error())
 
-    # ---- timed region: K pipelined steps (push + DMD per frame), then sync
-    S.sdmd_trace(h, True)
+    # ---- timed region: K pipelined steps (push + DMD per frame), no tracing.
+    #      Steady state: the pipeline is full when the region opens and when
+    #      it closes, so each timed step runs one frame's Gram row and
+    #      eigensolver launch and one earlier frame's Phi; the drain of the
+    #      last depth - 1 frames' Phi is not part of a step (it runs in the
+    #      traced pass below)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -821,12 +966,7 @@ def run_ours(args):
     clocks.start()
     time.sleep(0.3)
     ev0.record(stream)
-    with torch.cuda.stream(stream):
-        for i in range(K):
-            t = M_WIN + Wm + i
-            j = Wm + i
-            S.sdmd_step(h, frames[t], R_MODES, phis[j % D], lam[j], rdev[j:j + 1], sh)
-        S.sdmd_sync(h, sh)
+    steps(Wm, K)
     ev1.record(stream)
     stream.synchronize()
     torch.cuda.synchronize()
@@ -834,18 +974,32 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     total_ms = ev0.elapsed_time(ev1)
+    if S.sdmd_status(h, sh) != S.SDMD_OK:
+        raise RuntimeError("device status after timed region: " + S.sdmd_last_error())
+    t_max = max_over_ranks(total_ms, world, dev)
+    value = job_rate(world, K, t_max)
+
+    # ---- traced pass (after the timed one, same steady state): per-kernel
+    #      CUDA-event durations for the roofline and per-frame latency
+    S.sdmd_trace(h, True)
+    tt0 = torch.cuda.Event(enable_timing=True)
+    tt1 = torch.cuda.Event(enable_timing=True)
+    tt0.record(stream)
+    steps(Wm + K, Kt)
+    tt1.record(stream)
+    S.sdmd_sync(h, sh)               # drain (traced: the last frames' latency includes it)
+    stream.synchronize()
+    traced_ms = tt0.elapsed_time(tt1)
     frame_ms = np.array(S.sdmd_trace_times(h, S.SDMD_K_FRAME))
     traces = {k: S.sdmd_trace_read(h, k) for k in range(S.SDMD_K_COUNT) if k != S.SDMD_K_FRAME}
     S.sdmd_trace(h, False)
     if S.sdmd_status(h, sh) != S.SDMD_OK:
-        raise RuntimeError("device status after timed region: " + S.sdmd_last_error())
-    per_step = frame_ms if frame_ms.size else np.array([total_ms / K])
-    t_max = max_over_ranks(total_ms, world, dev)
-    value = job_rate(world, K, t_max)
+        raise RuntimeError("device status after traced pass: " + S.sdmd_last_error())
+    per_step = frame_ms if frame_ms.size else np.array([traced_ms / Kt])
 
     # ---- the same kernels launched one at a time (no overlap): per-kernel
     #      durations without contention, for the kernel rooflines
-    iso = measure_isolated(S, h, frames, M_WIN + Wm + K, stream, phis[0], n)
+    iso = measure_isolated(S, h, frames, 0, stream, phis[0], n)
 
     # ---- roofline of the dominant kernel: Phi of frame f fused with the Gram
     #      row of frame f + depth - 1 (one pass over the union of the windows)
@@ -863,11 +1017,13 @@ def run_ours(args):
     phi_bytes = (M_WIN - 1) * n + n * R_MODES * 8
     ml, mms = traces[S.SDMD_K_MODES]
     il, ims = traces[S.SDMD_K_INGEST]
-    # this library's kernels launched in the timed region, from the trace
-    # counts: a fused pass is two kernels (the pass and its finish kernel), a
-    # frame's eigensolver two (the G snapshot and the solver), an unfused Gram
-    # row or Phi one each; the ingest is a copy, not a kernel
-    n_launch = 2 * fl + gl + pl + 2 * ml
+    # this library's kernels launched in the timed region: the traced pass
+    # runs the same steady-state steps, so its per-step count (a fused pass
+    # is two kernels, the pass and its finish kernel; a frame's eigensolver
+    # two, the G snapshot and the solver; an unfused Gram row one; the drain's
+    # Phi launches after the last traced step are not counted; the ingest is
+    # a copy, not a kernel) times the timed steps
+    n_launch = int(round((2 * fl + gl + 2 * ml) * K / Kt))
     kernels = {"fused_phi_gram_row": {"launches": fl, "us": fused_us, "GB/s": fused_gbs,
                                       "algorithmic_bytes": fused_bytes, "union_slots": ktot},
                "gram_row": {"launches": gl, "us": gram_us,
@@ -930,6 +1086,11 @@ def run_ours(args):
         sparse = measure_sparse(S, synth, dev, stream)
         sparse["dense_physical"] = measure_dense_complex(S, synth, dev, stream)
 
+    # ---- the planted-mode FP32 stream (n = 4096, m = 32, 200 snapshots)
+    config1 = None
+    if not args.no_secondary:
+        config1 = measure_config1(S, synth, dev, stream)
+
     # ---- FP32 window n = 2^22, m = 256: BF16x3 tensor-core catch-up / rebuild
     bf16x3 = None
     if not args.no_secondary:
@@ -962,9 +1123,14 @@ def run_ours(args):
                      "unit": "GB/s", "frac": fused_gbs / peak, "traffic": traffic,
                      "peak_kind": "%s hbm_gbs (copy)" % peak_kind,
                      "algorithmic_bytes_per_launch": fused_bytes,
+                     "gram_row_isolated": {"achieved": iso["gram_row"]["GB/s"],
+                                           "frac": iso["gram_row"]["GB/s"] / peak,
+                                           "us": iso["gram_row"]["us"]},
                      "note": "Phi of frame f (tensor cores) and the exact Gram row of frame f + %d in one "
-                             "pass over %d window slots; launch durations inside the pipelined timed "
-                             "region, beside other frames' eigensolvers" % (D - 1, ktot)},
+                             "pass over %d window slots; launch durations (CUDA events on the push stream) "
+                             "from the traced pass of %d steady-state steps that follows the untraced timed "
+                             "region, beside other frames' eigensolvers; gram_row_isolated: the stand-alone "
+                             "Gram-row kernel (sdmd_push) alone on the GPU" % (D - 1, ktot, Kt)},
         "roofline_isolated": {"bound": "hbm", "kernel": "gram_row_u8", "achieved": iso["gram_row"]["GB/s"],
                               "peak": peak, "unit": "GB/s", "frac": iso["gram_row"]["GB/s"] / peak,
                               "algorithmic_bytes_per_launch": gram_bytes,
@@ -980,12 +1146,18 @@ def run_ours(args):
                        "max": float(per_step.max()),
                        "definition": "per frame: sdmd_step call on the stream to its DMD outputs complete"},
         "pipeline_depth": D,
+        "timing": {"rule": "steady state: warm-up steps leave depth - 1 frames' Phi deferred, the timed "
+                           "region (tracing off) runs K steps and closes with the pipeline full again; "
+                           "each timed step = one frame's ingest, fused Gram row, eigensolver launch and "
+                           "an earlier frame's Phi; the drain runs after the traced pass, outside it",
+                   "traced_steps": Kt, "traced_ms_per_step": traced_ms / Kt},
         "gpu_launches": n_launch,
         "rebuild": rebuild,
         "catch_up": catchup,
         "sparse_row": sparse,
         "serving": serving,
         "fp32_bf16x3": bf16x3,
+        "config1_planted_f32": config1,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "cpu_streaming": scpu,

@@ -505,6 +505,28 @@ SDMD_API int sdmd_trace_times(sdmd_t h, int32_t kernel, double *ms, int32_t cap,
 SDMD_API int sdmd_modes_phase_cycles(sdmd_t h, int64_t *cycles, int32_t count, void *stream);
 
 /*
+ * sdmd_newest_row / sdmd_set_newest_row -- read or overwrite the newest
+ * snapshot's row of the window's G (and, for the set, its column: the
+ * conjugate), in time order: entry q is <x_q, x_new> for the q-th oldest
+ * resident snapshot, the last entry <x_new, x_new>. Element type as
+ * sdmd_gram (int64, double or complex128), c entries (c = resident
+ * snapshots). `row` may be device or host memory; pageable host memory makes
+ * the call wait for the stream.
+ * These are the exchange points of the row-slab split of one stream over
+ * several GPUs (Sec. 3.1, Eq. 12a-b: every entry of the new row is a sum
+ * over the n positions, so it splits over position ranges). Each rank holds
+ * positions [lo, hi) of every snapshot in a handle of n = hi - lo, pushes
+ * its part of x_new (sdmd_push computes the partial row over its positions
+ * and inserts it), reads that partial row with sdmd_newest_row, sums the
+ * ranks' partial rows (one all-reduce of c values; exact for int64), and
+ * writes the sum back with sdmd_set_newest_row. Every rank then holds the
+ * full window's G; sdmd_modes on each gives the same eigenvalues and the
+ * rows lo .. hi - 1 of Phi. SDMD_ERR_NOT_READY before the first push.
+ */
+SDMD_API int sdmd_newest_row(sdmd_t h, void *row, void *stream);
+SDMD_API int sdmd_set_newest_row(sdmd_t h, const void *row, void *stream);
+
+/*
  * sdmd_gram_row_static -- one Gram row, g[j] = <x_j, y> for j < c, computed
  * without allocating any device memory. The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code whose
@@ -530,6 +552,10 @@ SDMD_API int sdmd_modes_phase_cycles(sdmd_t h, int64_t *cycles, int32_t count, v
  * or from several threads) race and must be serialised by the caller.
  * FP32 results use a different summation order than sdmd_push (equal to
  * rounding); U8 results are exact.
+ * `stream` must belong to the current device (SDMD_ERR_ARG otherwise): the
+ * kernel runs there with that device's scratch address. The address is
+ * looked up once per device ordinal and kept for the life of the process, so
+ * calls after cudaDeviceReset (a new primary context) are not supported.
  */
 #define SDMD_GRAM_ROW_STATIC_MAX_C 256
 SDMD_API int sdmd_gram_row_static(int32_t dtype, const void *X, int64_t ld, int32_t c, const void *y,

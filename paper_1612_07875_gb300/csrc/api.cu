@@ -174,6 +174,31 @@ __global__ void gather_gram_kernel(const uint64_t* G, int m, int c, int start, i
   for (int q = 0; q < words; ++q) out[(int64_t)idx * words + q] = G[src * words + q];
 }
 
+// The newest snapshot's row of the physical G (slot s_new) in time order.
+__global__ void newest_row_kernel(const uint64_t* G, int m, int c, int start, int s_new, int words, uint64_t* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= c) return;
+  const int64_t src = (int64_t)s_new * m + (start + q) % m;
+  for (int w = 0; w < words; ++w) out[(int64_t)q * words + w] = G[src * words + w];
+}
+
+// Row and column s_new of the physical G from a time-ordered row; the column
+// gets the conjugate (complex entries: the sign bit of the imaginary part
+// flips), the diagonal entry is written once.
+__global__ void set_newest_row_kernel(uint64_t* G, int m, int c, int start, int s_new, int words,
+                                      const uint64_t* row) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= c) return;
+  const int j = (start + q) % m;
+  for (int w = 0; w < words; ++w) G[((int64_t)s_new * m + j) * words + w] = row[(int64_t)q * words + w];
+  if (j == s_new) return;
+  for (int w = 0; w < words; ++w) {
+    uint64_t v = row[(int64_t)q * words + w];
+    if (w == 1) v ^= 0x8000000000000000ull;
+    G[((int64_t)j * m + s_new) * words + w] = v;
+  }
+}
+
 // Event pair for class k (created on first use); false if tracing is off.
 bool trace_pair(sdmd_s* h, int k, cudaEvent_t* a, cudaEvent_t* b) {
   if (!h->trace) return false;
@@ -270,8 +295,10 @@ inline int32_t oldest_slot(const sdmd_s* h) { return (int32_t)((h->count - resid
 // earlier), wait for every in-flight DMD whose X' still contains it.
 int flush_pending(sdmd_s* h, cudaStream_t st);
 
-int wait_ring_readers(sdmd_s* h, cudaStream_t st) {
-  const int64_t t = h->count;
+// Make `st` wait for every in-flight frame that still reads the ring slot
+// push number t (default: the next push) is about to overwrite.
+int wait_ring_readers(sdmd_s* h, cudaStream_t st, int64_t t = -1) {
+  if (t < 0) t = h->count;
   for (PipeCtx& c : h->ctx) {
     if (c.busy && c.frame - h->m + 2 <= t - h->cap) {
       if (c.phi_pending) {                     // its Phi must run before the slot is reused
@@ -708,35 +735,63 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   }
   const int rc0 = ensure_gram_full_scratch(h);
   if (rc0 != SDMD_OK) return rc0;
-  for (int j = 0; j < k; ++j) {        // ingest only
-    {
-      const int rc = wait_ring_readers(h, st);
-      if (rc != SDMD_OK) return rc;
-    }
-    TraceScope ts(h, SDMD_K_INGEST, st);
-    CK(cudaMemcpyAsync(h->ring + (int64_t)h->head * h->slot_bytes, src + (size_t)j * ld * elem_bytes,
-                       (size_t)(h->n * h->elem), cudaMemcpyDefault, st));
-    h->head = (h->head + 1) % h->cap;
-    h->count += 1;
+  // every ring-reader wait first: a failure there leaves the handle as it was
+  for (int j = 0; j < k; ++j) {
+    const int rc = wait_ring_readers(h, st, h->count + j);
+    if (rc != SDMD_OK) return rc;
   }
-  // rows and columns of the k new snapshots in one pass over the window
-  const int kt = k < c_after ? k : c_after;
-  if (f32_tc) return gram_f32_tensor(h, c_after, kt, st);
-  GramFullArgs ga;
-  ga.ring = h->ring;
-  ga.slot_bytes = h->slot_bytes;
-  ga.n = h->n;
-  ga.m = h->cap;
-  ga.start = oldest_slot(h);
-  ga.c = c_after;
-  ga.k = kt;
-  ga.partials = h->gf_partials;
-  ga.sched = h->gf_sched;
-  ga.G = static_cast<long long*>(h->G);
-  ga.status = h->status;
-  TraceScope ts(h, SDMD_K_GRAM_ROW, st);
-  CK(launch_gram_full_tc(ga, nullptr, st));
-  return SDMD_OK;
+  const int32_t head0 = h->head;
+  const int64_t count0 = h->count;
+  int copied = 0;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < k && e == cudaSuccess; ++j) {        // ingest only
+    TraceScope ts(h, SDMD_K_INGEST, st);
+    e = cudaMemcpyAsync(h->ring + (int64_t)((head0 + j) % h->cap) * h->slot_bytes,
+                        src + (size_t)j * ld * elem_bytes, (size_t)(h->n * h->elem), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) ++copied;
+  }
+  if (e == cudaSuccess) {
+    // rows and columns of the k new snapshots in one pass over the window
+    // (its arguments read the advanced ring)
+    h->head = (int32_t)((head0 + k) % h->cap);
+    h->count = count0 + k;
+    const int kt = k < c_after ? k : c_after;
+    if (f32_tc) {
+      const int rc = gram_f32_tensor(h, c_after, kt, st);
+      if (rc == SDMD_OK) return SDMD_OK;
+      e = cudaErrorLaunchFailure;
+    } else {
+      GramFullArgs ga;
+      ga.ring = h->ring;
+      ga.slot_bytes = h->slot_bytes;
+      ga.n = h->n;
+      ga.m = h->cap;
+      ga.start = oldest_slot(h);
+      ga.c = c_after;
+      ga.k = kt;
+      ga.partials = h->gf_partials;
+      ga.sched = h->gf_sched;
+      ga.G = static_cast<long long*>(h->G);
+      ga.status = h->status;
+      TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+      e = launch_gram_full_tc(ga, nullptr, st);
+      if (e == cudaSuccess) return SDMD_OK;
+    }
+    cudaGetLastError();
+    h->head = head0;
+    h->count = count0;
+  } else {
+    cudaGetLastError();
+  }
+  // Failure after `copied` snapshots went into the ring: those become
+  // ordinary pushes (one Gram-row pass each, in order), so G matches the
+  // ring again, and the call reports the error.
+  for (int j = 0; j < copied; ++j) {
+    const int rc = gram_row_and_advance(h, h->head, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  return fail(SDMD_ERR_CUDA, "sdmd_push_batch: %s; %d of %d snapshots pushed as single rows", cudaGetErrorString(e),
+              copied, k);
 }
 
 extern "C++" int sdmd::push_many_plan(sdmd_t const* hs, const void* const* xs, int count, cudaStream_t st,
@@ -750,8 +805,11 @@ extern "C++" int sdmd::push_many_plan(sdmd_t const* hs, const void* const* xs, i
     for (int j = 0; j < i; ++j)
       if (hs[j] == hs[i]) return fail(SDMD_ERR_ARG, "sdmd_push_many: handle %d appears twice", i);
   }
+  // deferred work and ring-reader waits of every handle before the plan:
+  // a failure here changes no handle's ring
   for (int i = 0; i < count; ++i) {
-    const int rc = flush_pending(hs[i], st);
+    int rc = flush_pending(hs[i], st);
+    if (rc == SDMD_OK) rc = wait_ring_readers(hs[i], st);
     if (rc != SDMD_OK) return rc;
   }
   BatchArgs& ba = plan->args;
@@ -761,11 +819,7 @@ extern "C++" int sdmd::push_many_plan(sdmd_t const* hs, const void* const* xs, i
   ba.status = hs[0]->status;
   plan->ncopies = count;
   for (int i = 0; i < count; ++i) {
-    sdmd_s* h = hs[i];
-    {
-      const int rc = wait_ring_readers(h, st);
-      if (rc != SDMD_OK) return rc;
-    }
+    const sdmd_s* h = hs[i];
     const int32_t s_new = h->head;
     plan->dst[i] = h->ring + (int64_t)s_new * h->slot_bytes;
     plan->src[i] = xs[i];
@@ -785,10 +839,23 @@ extern "C++" int sdmd::push_many_plan(sdmd_t const* hs, const void* const* xs, i
     J.mode = (h->dtype == SDMD_U8) ? 0 : (h->dtype == SDMD_F32 ? (h->f32_fp64 ? 3 : 1) : 2);
     J.item0 = ba.nitems;
     ba.nitems += h->nblk;
-    h->head = (s_new + 1) % h->cap;
-    h->count += 1;
   }
   return SDMD_OK;
+}
+
+extern "C++" int sdmd::push_many_finish(sdmd_t const* hs, int count, int copied, bool launched, cudaStream_t st) {
+  int rc = SDMD_OK;
+  for (int i = 0; i < count && i < copied; ++i) {
+    sdmd_s* h = hs[i];
+    if (launched) {
+      h->head = (h->head + 1) % h->cap;
+      h->count += 1;
+    } else {                 // its snapshot is in the ring: its own Gram row
+      const int r = gram_row_and_advance(h, h->head, st);
+      if (rc == SDMD_OK) rc = r;
+    }
+  }
+  return rc;
 }
 
 int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void* stream) {
@@ -800,15 +867,25 @@ int sdmd_push_many(const sdmd_t* hs, const void* const* xs, int32_t count, void*
   BatchPlan plan;
   const int rc = push_many_plan(hs, xs, count, st, &plan);
   if (rc != SDMD_OK) return rc;
-  for (int i = 0; i < plan.ncopies; ++i) {
+  int copied = 0;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < plan.ncopies && e == cudaSuccess; ++i) {
     TraceScope ts(hs[i], SDMD_K_INGEST, st);
-    CK(cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, st));
+    e = cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, st);
+    if (e == cudaSuccess) ++copied;
   }
-  {
+  bool launched = false;
+  if (e == cudaSuccess) {
     TraceScope ts(hs[0], SDMD_K_GRAM_ROW, st);
-    CK(launch_gram_rows_batched(plan.args, st));
+    e = launch_gram_rows_batched(plan.args, st);
+    launched = e == cudaSuccess;
   }
-  return SDMD_OK;
+  if (e != cudaSuccess) cudaGetLastError();
+  const int rf = push_many_finish(hs, count, copied, launched, st);
+  if (e != cudaSuccess)
+    return fail(SDMD_ERR_CUDA, "sdmd_push_many: %s; %d of %d snapshots pushed", cudaGetErrorString(e),
+                launched ? count : copied, count);
+  return rf;
 }
 
 int sdmd_rebuild(sdmd_t h, void* stream) {
@@ -913,6 +990,49 @@ int sdmd_gram(sdmd_t h, void* G, void* stream) {
                                                            oldest_slot(h), (int)(h->gsz / 8), dst);
   CK(cudaGetLastError());
   if (!direct) return copy_out(G, h->gtmp, (size_t)c * c * h->gsz, st);
+  return SDMD_OK;
+}
+
+int sdmd_newest_row(sdmd_t h, void* row, void* stream) {
+  if (!h || !row) return fail(SDMD_ERR_ARG, "sdmd_newest_row: NULL argument");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  const int c = resident(h);
+  if (c == 0) return fail(SDMD_ERR_NOT_READY, "sdmd_newest_row: no snapshot pushed yet");
+  const int32_t s_new = (int32_t)((h->head + h->cap - 1) % h->cap);
+  const bool direct = ptr_kind(row) == kDevice;
+  uint64_t* dst = direct ? static_cast<uint64_t*>(row) : static_cast<uint64_t*>(h->gtmp);
+  newest_row_kernel<<<(c + 127) / 128, 128, 0, st>>>(static_cast<const uint64_t*>(h->G), h->cap, c, oldest_slot(h),
+                                                      s_new, (int)(h->gsz / 8), dst);
+  CK(cudaGetLastError());
+  if (!direct) return copy_out(row, h->gtmp, (size_t)c * h->gsz, st);
+  return SDMD_OK;
+}
+
+int sdmd_set_newest_row(sdmd_t h, const void* row, void* stream) {
+  if (!h || !row) return fail(SDMD_ERR_ARG, "sdmd_set_newest_row: NULL argument");
+  DeviceScope ds(h->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  {
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+  }
+  const int c = resident(h);
+  if (c == 0) return fail(SDMD_ERR_NOT_READY, "sdmd_set_newest_row: no snapshot pushed yet");
+  const int32_t s_new = (int32_t)((h->head + h->cap - 1) % h->cap);
+  const uint64_t* src = static_cast<const uint64_t*>(row);
+  if (ptr_kind(row) != kDevice) {      // staged through the gather scratch, in stream order
+    CK(cudaMemcpyAsync(h->gtmp, row, (size_t)c * h->gsz, cudaMemcpyDefault, st));
+    src = static_cast<const uint64_t*>(h->gtmp);
+  }
+  set_newest_row_kernel<<<(c + 127) / 128, 128, 0, st>>>(static_cast<uint64_t*>(h->G), h->cap, c, oldest_slot(h),
+                                                          s_new, (int)(h->gsz / 8), src);
+  CK(cudaGetLastError());
+  if (ptr_kind(row) == kPageable) CK(cudaStreamSynchronize(st));   // the caller may reuse its buffer
   return SDMD_OK;
 }
 

@@ -183,11 +183,18 @@ extern "C" SDMD_API int sdmd_gram_row_static(int32_t dtype, const void* X, int64
     return set_err(SDMD_ERR_ARG, "X and y must be 16-byte aligned and ld * sizeof(elem) a multiple of 16");
   if (!is_device_ptr(X) || !is_device_ptr(y) || !is_device_ptr(g))
     return set_err(SDMD_ERR_ARG, "X, y and g must be device memory");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0, sdev = 0;
+  cudaGetDevice(&dev);
+  // the scratch address is this device's; a stream of another device would
+  // launch the kernel there with a foreign address
+  cudaError_t e = cudaStreamGetDevice(st, &sdev);
+  if (e != cudaSuccess) return set_err(SDMD_ERR_ARG, "cudaStreamGetDevice: %s", cudaGetErrorString(e));
+  if (sdev != dev)
+    return set_err(SDMD_ERR_ARG, "stream belongs to device %d, the current device is %d", sdev, dev);
   unsigned char* scratch = nullptr;
   int rc = scratch_address(&scratch);
   if (rc != SDMD_OK) return rc;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // split n into CTA chunks of whole 4 KiB units; at most kMaxBlocks CTAs
   const int64_t units = (nbytes + kChunkAlign - 1) / kChunkAlign;
@@ -198,9 +205,8 @@ extern "C" SDMD_API int sdmd_gram_row_static(int32_t dtype, const void* X, int64
   const int64_t chunk = per * kChunkAlign;
   const int nblk = (int)((units + per - 1) / per);
   if (nblk > kMaxBlocks) return set_err(SDMD_ERR_ARG, "split needs %d CTAs > %d", nblk, kMaxBlocks);
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
   // the ticket must start at zero; the partials are always written before read
-  cudaError_t e = cudaMemsetAsync(scratch + kPartialBytes, 0, sizeof(unsigned int), st);
+  e = cudaMemsetAsync(scratch + kPartialBytes, 0, sizeof(unsigned int), st);
   if (e != cudaSuccess) return set_err(SDMD_ERR_CUDA, "cudaMemsetAsync(ticket): %s", cudaGetErrorString(e));
   const uint8_t* Xb = static_cast<const uint8_t*>(X);
   const uint8_t* yb = static_cast<const uint8_t*>(y);

@@ -107,9 +107,13 @@ cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st);
 cudaError_t batched_kernel_config(const BatchArgs& a, cudaKernelNodeParams* p);
 
 // One batched push, planned: the handles' deferred work flushed, ring readers
-// waited for, the ingest copies and the batch arguments filled in, and every
-// handle's ring advanced on the host. The caller issues the copies, then the
-// batched kernel (directly or as graph nodes), on `st`.
+// waited for, the ingest copies and the batch arguments filled in; no
+// handle's ring moves yet. The caller issues the copies, then the batched
+// kernel (directly or as graph nodes), on `st`, and then calls
+// push_many_finish with how many of the leading copies were enqueued and
+// whether the kernel was: every handle whose snapshot reached its ring
+// advances (with its own Gram-row pass if the batched kernel did not run),
+// the others stay as they were.
 struct BatchPlan {
   BatchArgs args;
   int ncopies;
@@ -118,6 +122,7 @@ struct BatchPlan {
   size_t bytes[kMaxBatchJobs];
 };
 int push_many_plan(sdmd_t const* hs, const void* const* xs, int count, cudaStream_t st, BatchPlan* plan);
+int push_many_finish(sdmd_t const* hs, int count, int copied, bool launched, cudaStream_t st);
 
 // Device bytes of a depth-1 dense handle (admission by footprint).
 int64_t handle_device_bytes(int64_t n, int32_t m, int32_t dtype, int num_sms);

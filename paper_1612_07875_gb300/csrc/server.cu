@@ -107,16 +107,21 @@ void drop_graph(TickGraph& t) {
   t.last.swap(last);
 }
 
-int run_direct(sdmd_server_s* s, const sdmd::BatchPlan& plan) {
-  for (int i = 0; i < plan.ncopies; ++i)
+// `copied` / `launched` report how far the batch got (the copies that were
+// enqueued, whether the batched kernel was), for sdmd::push_many_finish.
+int run_direct(sdmd_server_s* s, const sdmd::BatchPlan& plan, int* copied, bool* launched) {
+  for (int i = 0; i < plan.ncopies; ++i) {
     if (cudaMemcpyAsync(plan.dst[i], plan.src[i], plan.bytes[i], cudaMemcpyDefault, s->st) != cudaSuccess) {
       cudaGetLastError();
       return err(SDMD_ERR_CUDA, "sdmd_server_tick: copy failed");
     }
+    *copied = i + 1;
+  }
   if (sdmd::launch_gram_rows_batched(plan.args, s->st) != cudaSuccess) {
     cudaGetLastError();
     return err(SDMD_ERR_CUDA, "sdmd_server_tick: batched launch failed");
   }
+  *launched = true;
   return SDMD_OK;
 }
 
@@ -124,13 +129,16 @@ int run_direct(sdmd_server_s* s, const sdmd::BatchPlan& plan) {
 // updated) or, with graphs off, as copies plus a kernel launch.
 // A set of streams gets a graph once it has come twice in a row at a batch
 // position (a steady set); sets that change every tick launch directly.
-int run_batch(sdmd_server_s* s, size_t b, const std::vector<sdmd_t>& hs, const sdmd::BatchPlan& plan) {
-  if (!s->graphs) return run_direct(s, plan);
+int run_batch(sdmd_server_s* s, size_t b, const std::vector<sdmd_t>& hs, const sdmd::BatchPlan& plan, int* copied,
+              bool* launched) {
+  *copied = 0;
+  *launched = false;
+  if (!s->graphs) return run_direct(s, plan, copied, launched);
   if (s->tg.size() <= b) s->tg.resize(b + 1);
   TickGraph& t = s->tg[b];
   const bool steady = (t.exec && t.key == hs) || t.last == hs;
   t.last = hs;
-  if (!steady) return run_direct(s, plan);
+  if (!steady) return run_direct(s, plan, copied, launched);
   cudaKernelNodeParams kp;
   if (sdmd::batched_kernel_config(plan.args, &kp) != cudaSuccess) {
     cudaGetLastError();
@@ -163,11 +171,13 @@ int run_batch(sdmd_server_s* s, size_t b, const std::vector<sdmd_t>& hs, const s
     }
   }
   if (e == cudaSuccess) e = cudaGraphLaunch(t.exec, s->st);
-  if (e != cudaSuccess) {
+  if (e != cudaSuccess) {         // nothing of the graph ran
     cudaGetLastError();
     drop_graph(t);
     return err(SDMD_ERR_CUDA, "sdmd_server_tick: graph build, update or launch failed");
   }
+  *copied = plan.ncopies;
+  *launched = true;
   return SDMD_OK;
 }
 
@@ -284,7 +294,12 @@ int sdmd_server_tick(sdmd_server_t s, int32_t* frames_done) {
     }
     sdmd::BatchPlan plan;
     int rc = sdmd::push_many_plan(hs.data(), xs.data(), (int32_t)hs.size(), s->st, &plan);
-    if (rc == SDMD_OK) rc = run_batch(s, b / SDMD_MAX_BATCH, hs, plan);
+    if (rc != SDMD_OK) return rc;
+    int copied = 0;
+    bool launched = false;
+    rc = run_batch(s, b / SDMD_MAX_BATCH, hs, plan, &copied, &launched);
+    const int rf = sdmd::push_many_finish(hs.data(), (int)hs.size(), copied, launched, s->st);
+    if (rc == SDMD_OK) rc = rf;
     if (rc != SDMD_OK) return rc;
   }
   if (cudaStreamSynchronize(s->st) != cudaSuccess) {

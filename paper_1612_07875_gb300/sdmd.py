@@ -71,6 +71,8 @@ _SIGNATURES = {
     "sdmd_count": [_VP, ctypes.POINTER(_I64)],
     "sdmd_rebuild": [_VP, _VP],
     "sdmd_gram": [_VP, _VP, _VP],
+    "sdmd_newest_row": [_VP, _VP, _VP],
+    "sdmd_set_newest_row": [_VP, _VP, _VP],
     "sdmd_modes": [_VP, _I32, _VP, _VP, _VP, _VP],
     "sdmd_svd": [_VP, _I32, _VP, _VP, _VP],
     "sdmd_status": [_VP, _VP],
@@ -215,6 +217,16 @@ def sdmd_count(h):
 
 def sdmd_gram(h, G, stream=None):
     _check(lib().sdmd_gram(h, ptr(G), stream_handle(stream)), "sdmd_gram")
+
+
+def sdmd_newest_row(h, row, stream=None):
+    """The newest snapshot's row of G, time order (c values; see sdmd.h)."""
+    _check(lib().sdmd_newest_row(h, ptr(row), stream_handle(stream)), "sdmd_newest_row")
+
+
+def sdmd_set_newest_row(h, row, stream=None):
+    """Overwrite the newest snapshot's row and column of G (time order)."""
+    _check(lib().sdmd_set_newest_row(h, ptr(row), stream_handle(stream)), "sdmd_set_newest_row")
 
 
 def sdmd_modes(h, r, phi, lam, r_out=None, stream=None):

@@ -240,11 +240,15 @@ class ConditionedStream:
             x += a[k] * self._basis(k, lo, hi)
         return (x * np.sqrt(self.n)).astype(np.float32)
 
-    def snapshots(self, ts):
-        """Snapshots for the times `ts` as a len(ts) x n float32 array: the
-        same construction as `snapshot`, with the K basis fields built once
-        and combined by one matrix product (faster for many snapshots)."""
-        B = np.stack([self._basis(k, 0, self.n) for k in range(self.K)])     # K x n
+    def snapshots(self, ts, lo=0, hi=None):
+        """Positions lo .. hi - 1 of the snapshots for the times `ts` as a
+        len(ts) x (hi - lo) float32 array: the same construction as
+        `snapshot`, with the K basis fields built once and combined by one
+        matrix product (faster for many snapshots). A full-length window can
+        be drawn in position blocks; each block equals the same columns of
+        the whole array."""
+        hi = self.n if hi is None else hi
+        B = np.stack([self._basis(k, lo, hi) for k in range(self.K)])        # K x (hi - lo)
         A = np.stack([self.coeffs(t) * self.s for t in ts])                  # T x K
         return ((A @ B) * np.sqrt(self.n)).astype(np.float32)
 

@@ -70,3 +70,86 @@ def test_fp32_gram_error_vs_condition_number(cuda_device, kappa):
         assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
+
+
+def test_conditioned_full_size_kappa_1e8(cuda_device):
+    # The precision sweep's own size: n = 2^22 FP32, window m = 256, planted
+    # geometric spectrum with kappa = 1e8 (the hardest of the sweep). The
+    # oracle's FP64 Gram of the same FP32 snapshots is summed over position
+    # blocks of 2^18 (G = sum of W_b^T W_b, the definition split by rows, so
+    # the host never holds an FP64 copy of the whole window).
+    #   FP32 row pushes: relative Frobenius <= 1e-5 and every entry within
+    #     1e-5 sqrt(G_ii G_jj);
+    #   BF16x3 rebuild, then a BF16x3 catch-up of 8 snapshots (the window
+    #     moves by 8: 8 new rows and columns from one tensor-core pass):
+    #     relative Frobenius <= 1e-6 and every entry within
+    #     1e-6 sum_p |x_ip x_jp|;
+    #   eigenvalues of G within 1e-6 lambda_1 of the oracle's, and the
+    #     device eigensolver's sigma^2 (sdmd_svd, r = 255: every one above
+    #     the rank floor) within 1e-6 lambda_1 of the eigenvalues of the
+    #     oracle's G_X.
+    import oracle
+    n, m, k, kappa = 1 << 22, 256, 8, 1e8
+    T = m + k
+    blk = 1 << 18
+    cs = synth.ConditionedStream(n=n, K=m, kappa=kappa, seed=synth.config_seed(4))
+    X = torch.empty(T, n, dtype=torch.float32, device=cuda_device)
+    ref = np.zeros((T, T))
+    bnd = np.zeros((T, T))
+    for lo in range(0, n, blk):
+        Xb = cs.snapshots(range(T), lo, lo + blk)            # T x blk float32
+        X[:, lo:lo + blk].copy_(torch.from_numpy(Xb))
+        ref += oracle.gram_dense(Xb.T)
+        bnd += oracle.gram_dense(np.abs(Xb).T)
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    G = torch.empty(m, m, dtype=torch.float64, device=cuda_device)
+
+    def gram():
+        S.sdmd_gram(h, G)
+        torch.cuda.synchronize()
+        return G.cpu().numpy()
+
+    def check(Gg, w0, tol, entry_bound, name):
+        R = ref[w0:w0 + m, w0:w0 + m]
+        err = np.linalg.norm(Gg - R) / np.linalg.norm(R)
+        ent = np.abs(Gg - R) / entry_bound[w0:w0 + m, w0:w0 + m]
+        lam_ref = np.sort(np.linalg.eigvalsh(R))[::-1]
+        lam = np.sort(np.linalg.eigvalsh(Gg))[::-1]
+        dl = np.abs(lam - lam_ref).max() / lam_ref[0]
+        print("kappa 1e8 n 2^22 m 256 %-14s: cond %.2e, rel Frobenius %.2e, worst entry / bound %.2e, "
+              "max |dlambda| / lambda_1 %.2e" % (name, lam_ref[0] / lam_ref[-1], err, ent.max() * tol, dl))
+        assert err <= tol, name
+        assert (ent <= 1.0).all(), name
+        assert dl <= 1e-6, name
+
+    try:
+        for t in range(m):
+            S.sdmd_push(h, X[t])
+        d = np.sqrt(np.diag(ref))
+        check(gram(), 0, 1e-5, 1e-5 * np.outer(d, d), "fp32 rows")
+        S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
+        S.sdmd_rebuild(h)
+        check(gram(), 0, 1e-6, 1e-6 * bnd, "bf16x3 rebuild")
+        S.sdmd_push_batch(h, k, X[m:T], n)
+        Gg = gram()
+        check(Gg, k, 1e-6, 1e-6 * bnd, "bf16x3 catch-up")
+        r = m - 1
+        lam = torch.zeros(2 * r, dtype=torch.float64, device=cuda_device)
+        rk = torch.zeros(1, dtype=torch.int32, device=cuda_device)
+        S.sdmd_modes(h, r, None, lam, rk)
+        sig = torch.zeros(r, dtype=torch.float64, device=cuda_device)
+        S.sdmd_svd(h, r, sig, None)
+        torch.cuda.synchronize()
+        assert S.sdmd_status(h) == S.SDMD_OK
+        kept = int(rk.item())
+        lx = np.sort(np.linalg.eigvalsh(ref[k:k + m - 1, k:k + m - 1]))[::-1]
+        s2 = sig.cpu().numpy()[:kept] ** 2
+        print("device eigensolver: kept %d of %d, max |sigma^2 - lambda| / lambda_1 %.2e"
+              % (kept, r, np.abs(s2 - lx[:kept]).max() / lx[0]))
+        thr = lx[0] * 64 * (m - 1) * 2.0 ** -52              # the rank rule on both sides
+        assert (lx > 100 * thr).sum() <= kept <= (lx > thr / 100).sum()
+        assert np.abs(s2 - lx[:kept]).max() <= 1e-6 * lx[0]
+    finally:
+        S.sdmd_destroy(h)
+        del X
+        torch.cuda.empty_cache()

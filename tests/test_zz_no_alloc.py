@@ -72,6 +72,45 @@ def test_static_row_matches_push_row_on_two_calls_in_a_row(cuda_device, kind):
     _check(kind, g2.cpu().numpy(), G[:c2, 2], d[:c2], d[2])
 
 
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+@pytest.mark.parametrize("n", [1, 3, 17])
+def test_static_row_tail_only(cuda_device, kind, n):
+    # fewer than 16 bytes past the last whole vector: one CTA whose lane 0
+    # adds the scalar tail (for n = 1 and 3 with uint8, all of the row)
+    c, ld = 9, 16
+    X = _snapshots(kind, c, n, ld, cuda_device, seed=21 + n)
+    G = _reference_gram(kind, X, n, cuda_device)
+    d = np.diag(G).astype(np.float64)
+    out_t = torch.int64 if kind == "u8" else torch.float64
+    dt = S.SDMD_U8 if kind == "u8" else S.SDMD_F32
+    for rep in range(2):
+        g = torch.full((c,), -7, dtype=out_t, device=cuda_device)
+        S.sdmd_gram_row_static(dt, X, ld, c, X[rep], n, g)
+        torch.cuda.synchronize()
+        _check(kind, g.cpu().numpy(), G[rep, :], d, d[rep])
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_static_row_max_window_large_n(cuda_device, kind):
+    # c = SDMD_GRAM_ROW_STATIC_MAX_C fills every row of the partials array;
+    # n = 2^22 splits into as many CTAs as the launch allows (two per SM)
+    c, n = S.SDMD_GRAM_ROW_STATIC_MAX_C, 1 << 22
+    g = torch.Generator(device=cuda_device).manual_seed(31)
+    if kind == "u8":
+        X = torch.randint(0, 256, (c, n), dtype=torch.uint8, device=cuda_device, generator=g)
+    else:
+        X = torch.randn(c, n, dtype=torch.float32, device=cuda_device, generator=g)
+    G = _reference_gram(kind, X, n, cuda_device)
+    d = np.diag(G).astype(np.float64)
+    out_t = torch.int64 if kind == "u8" else torch.float64
+    dt = S.SDMD_U8 if kind == "u8" else S.SDMD_F32
+    for y in (c - 1, 0):
+        out = torch.full((c,), -7, dtype=out_t, device=cuda_device)
+        S.sdmd_gram_row_static(dt, X, n, c, X[y], n, out)
+        torch.cuda.synchronize()
+        _check(kind, out.cpu().numpy(), G[y, :], d, d[y])
+
+
 def test_static_row_rejects_oversized_window(cuda_device):
     n = 1024
     X = torch.zeros(2, n, dtype=torch.float32, device=cuda_device)
