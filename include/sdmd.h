@@ -414,8 +414,11 @@ enum {
     SDMD_OPT_PHI_TENSOR = 1 /* 1 (default): Phi of uint8 handles on the tensor
                                cores (tcgen05, fp16 operands: pixels exact,
                                M = V Sigma^-1 W as three power-of-two-scaled
-                               fp16 terms, FP32 accumulation); 0: CUDA-core
-                               FP32 kernel */
+                               fp16 terms, FP32 accumulation), the modes
+                               of a pass fitted to r (r <= 10: one pass of
+                               10 modes); 2: the same arithmetic in passes
+                               of 16 modes whatever r (results are
+                               identical); 0: CUDA-core FP32 kernel */
     ,
     SDMD_OPT_REBUILD_TENSOR = 2 /* 1 (default): sdmd_rebuild and sdmd_push_batch
                                    of uint8 windows of at most 127 snapshots

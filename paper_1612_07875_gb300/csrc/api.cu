@@ -328,7 +328,8 @@ PhiArgs ctx_phi_args(const sdmd_s* h, const PipeCtx& k) {
   pa.r_dev = k.r_dev;
   pa.phi = k.phi;
   pa.status = h->status;
-  pa.tensor = h->phi_tensor;
+  pa.tensor = h->phi_tensor != 0;
+  pa.fit_modes = h->phi_tensor == 1;
   pa.sched = k.phi_sched;
   return pa;
 }
@@ -1087,7 +1088,8 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
     pa.r_dev = h->r_dev;
     pa.phi = static_cast<float*>(phi);
     pa.status = h->status;
-    pa.tensor = h->phi_tensor;
+    pa.tensor = h->phi_tensor != 0;
+    pa.fit_modes = h->phi_tensor == 1;
     pa.sched = h->phi_sched;
     TraceScope ts(h, SDMD_K_PHI, st);
     CK(launch_phi(pa, st));
@@ -1368,7 +1370,8 @@ int sdmd_set_option(sdmd_t h, int32_t option, int64_t value) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_set_option: NULL handle");
   switch (option) {
     case SDMD_OPT_PHI_TENSOR:
-      h->phi_tensor = value ? 1 : 0;
+      if (value < 0 || value > 2) return fail(SDMD_ERR_ARG, "sdmd_set_option: SDMD_OPT_PHI_TENSOR value %lld not in 0..2", (long long)value);
+      h->phi_tensor = (int32_t)value;
       return SDMD_OK;
     case SDMD_OPT_REBUILD_TENSOR:
       h->rebuild_tensor = value ? 1 : 0;

@@ -173,7 +173,7 @@ __device__ void tridiagonalize(dd* A, int p, dd* d, dd* e, dd* vs, dd* pv, dd* w
     const dd v0 = sc[1];
     for (int i = tid; i < L; i += kThreads) vs[i] = dd_mul(i == 0 ? v0 : rowk[i], inv);
     __syncthreads();
-    // pv = A_sub v, each row split into np parts (np * L <= 256)
+    // pv = A_sub v, each row split into np parts (np * L <= kThreads)
     dd* As = A + (int64_t)(k + 1) * p + (k + 1);
     int np = kThreads / L;
     np = np >= 8 ? 8 : (np >= 4 ? 4 : (np >= 2 ? 2 : 1));
@@ -437,11 +437,17 @@ __device__ void rayleigh_ritz(dd* Z, int rw, int p, const dd* d, const dd* e, dd
           const dd hab = H[a * rw + b];
           if (hab.hi != 0.f) {
             const dd tau = dd_div(dd_sub(H[b * rw + b], H[a * rw + a]), dd_scale(hab, 2.f));
-            const dd root = dd_sqrt(dd_fma(tau, tau, dd_make(1.f)));
-            dd t = dd_div(dd_make(1.f), dd_add(dd_abs(tau), root));
-            if (tau.hi < 0.f) t = dd_neg(t);
-            c = dd_div(dd_make(1.f), dd_sqrt(dd_fma(t, t, dd_make(1.f))));
-            s = dd_mul(t, c);
+            // |tau| > 1e18 (or not finite: h_ab is a denormal): h_ab is below
+            // 1e-18 of the diagonal gap, under df64 resolution, and the
+            // rotation would be the identity to working precision; tau^2
+            // would also leave the FP32 exponent range. Skip it.
+            if (fabsf(tau.hi) <= 1e18f) {
+              const dd root = dd_sqrt(dd_fma(tau, tau, dd_make(1.f)));
+              dd t = dd_div(dd_make(1.f), dd_add(dd_abs(tau), root));
+              if (tau.hi < 0.f) t = dd_neg(t);
+              c = dd_div(dd_make(1.f), dd_sqrt(dd_fma(t, t, dd_make(1.f))));
+              s = dd_mul(t, c);
+            }
           }
         }
         ord[2 * k] = a;
@@ -713,8 +719,8 @@ constexpr int64_t kSmemDynUnits = (220 * 1024) / 8;
 __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   SmemPlan s;
   s.P = (p + 3) & ~3;
-  // d, e, vs, pv, wv, lam (df64) + part (256 df64) + d32, e2_32 (float) + 32 df64 scalars
-  s.vec_units = 6 * s.P + 256 + s.P + 32;
+  // d, e, vs, pv, wv, lam (df64) + part (one df64 per thread) + d32, e2_32 (float) + 32 df64 scalars
+  s.vec_units = 6 * s.P + kThreads + s.P + 32;
   s.rr_dim = (r + kClusterExt < p) ? r + kClusterExt : p;
   s.rr_in_smem = (s.rr_dim <= kRRMax);
   s.rr_units = s.rr_in_smem ? 2 * (int64_t)s.rr_dim * s.rr_dim : 0;
@@ -755,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   dd* wv = pv + P;
   dd* lam = wv + P;
   dd* part = lam + P;
-  float* d32 = reinterpret_cast<float*>(part + 256);
+  float* d32 = reinterpret_cast<float*>(part + kThreads);
   float* e2_32 = d32 + P;
   dd* sc = reinterpret_cast<dd*>(e2_32 + P);
   dd* rrH = plan.rr_in_smem ? base + plan.vec_units : w.Y;
@@ -933,6 +939,9 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   // ---- 5. rank, sigma, V (FP64 out), vsi = V Sigma^-1 (df64, scaled units)
   if (tid == 0) {
     int k = 0;
+    bool finite = true;                // a breakdown is reported, not returned as rank 0
+    for (int i = 0; i < rw; ++i) finite = finite && isfinite(dd_to_double(lam[i]));
+    if (!finite) atomicOr(a.status, kDevRank);
     const double lam0 = (rw > 0) ? dd_to_double(lam[0]) : 0.0;
     if (lam0 > 0.0) {
       const double thr = lam0 * kRankRtol * (double)p * kEps;

@@ -66,13 +66,21 @@ constexpr int kMmaWarp = 4;
 constexpr int kConvWarp0 = 5;        // converter warps 5 .. 5 + K / (4 kIpt) - 1
 constexpr int kMaxThreads = 32 * (kConvWarp0 + 7);
 constexpr int kTileM = 128;          // positions per tile (MMA M)
-constexpr int kModes = 16;           // modes per pass (gridDim.y covers r)
-constexpr int kCols = 2 * kModes;    // re/im columns of one fp16 term
+constexpr int kMaxModes = 16;        // modes per pass, at most (gridDim.y covers r)
+constexpr int kMaxCols = 2 * kMaxModes;
 constexpr int kSplits = 3;
-constexpr int kN = kSplits * kCols;  // 96 accumulator columns per tile
+constexpr int kMaxN = kSplits * kMaxCols;   // 96 accumulator columns per tile, at most
+// A pass of kMd modes: 2 kMd re/im columns per fp16 term, the three terms
+// side by side along N, N rounded up to a multiple of 16 (kMd = 10: N = 64)
+template <int kMd>
+struct PassShape {
+  static constexpr int kCols = 2 * kMd;
+  static constexpr int kN = ((kSplits * kCols + 15) / 16) * 16;
+  static constexpr int kLoad = ((kN + 31) / 32) * 32;   // tensor-memory columns read per tile
+};
 constexpr int kAcc = 4;              // TMEM accumulators (ring)
 constexpr int kMaxA = 4;             // A-tile buffers (ring)
-constexpr int kTmemCols = 512;       // kAcc x kN = 384, power of two
+constexpr int kTmemCols = 512;       // kAcc x kN <= 384, power of two
 constexpr int kMaxRows = 256;        // K padded (p <= 255)
 constexpr int kChunk = 8;            // tiles per scheduling grab
 constexpr int kTix = 16;             // tile-index ring
@@ -106,7 +114,7 @@ struct TcShared {
   unsigned long long chunk_bar[2];        // chunk start published (by chunk parity)
   int chunk[2];                           // tile chunks grabbed by the converter leader (by parity)
   int tix[kTix];                          // tile index of iteration it at it % kTix, -1: no more
-  int expo[kCols];                        // per-column power-of-two scaling of M
+  int expo[kMaxCols];                     // per-column power-of-two scaling of M
 };
 
 // Dynamic shared memory: A ring, B, staging ring, slot offsets, state.
@@ -122,7 +130,7 @@ __host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages, int
   TcLayout L;
   L.a_bytes = kTileM * kpad * 2;                 // multiple of 4096
   L.b_off = n_a * L.a_bytes;
-  L.b_bytes = kN * kpad * 2;                     // multiple of 3072
+  L.b_bytes = kMaxN * kpad * 2;                  // multiple of 3072 (room for 16 modes)
   L.st_off = L.b_off + L.b_bytes;                // 16-byte aligned (cp.async destination)
   L.st_bytes = kpad * kTileM;
   L.tab_off = L.st_off + stages * L.st_bytes;    // window slot offsets (int64)
@@ -150,9 +158,11 @@ __device__ __forceinline__ void raise_timeout(const PhiArgs& a, volatile int* st
   *stop = 1;
 }
 
-template <int kIpt>
+template <int kIpt, int kMd>
 __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, int kpad, int n_a, int stages) {
   constexpr int kU = kTileM;             // staging row bytes
+  constexpr int kCols = PassShape<kMd>::kCols;
+  constexpr int kN = PassShape<kMd>::kN;
   extern __shared__ __align__(1024) uint8_t smem[];
   const TcLayout L = tc_layout(kpad, n_a, stages, a.fuse);
   // fused Gram row: only the first mode pass computes it
@@ -168,7 +178,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nthreads = blockDim.x;
   const int conv_warps = (nthreads >> 5) - kConvWarp0;   // = kpad / (4 kIpt)
-  const int k0 = blockIdx.y * kModes;
+  const int k0 = blockIdx.y * kMd;
   const int nks = kpad / 16;
   const int ntiles = (int)((a.n + kTileM - 1) / kTileM);
 
@@ -208,6 +218,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     }
     sh.expo[tid] = e;
   }
+  // B columns past the three terms (kMd = 10: 60 .. 63) are zero
+  for (int idx = tid; idx < (kN - kSplits * kCols) * kpad; idx += nthreads) {
+    const int nn = kSplits * kCols + idx / kpad, k = idx % kpad;
+    *reinterpret_cast<unsigned short*>(bbuf + ((k >> 3) * (kN / 8) + (nn >> 3)) * 128 + (nn & 7) * 16 + (k & 7) * 2) = 0;
+  }
   __syncthreads();
   // B: three fp16 terms of the scaled M, K-major cores, zero padded
   for (int idx = tid; idx < kCols * kpad; idx += nthreads) {
@@ -240,7 +255,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     // kg = u / 2 (slots 8 kg .. 8 kg + 7) and positions 64 h .. 64 h + 63
     // (h = u % 2) of a tile; every (kg, h) is covered exactly once
     const int cw = warp - kConvWarp0;
-    int64_t src[kIpt];                      // copy source in the ring (without tile), -1: slot >= p
+    int64_t src[kIpt];                      // copy source in the ring (without tile)
     unsigned ldo[kIpt];                     // copy destination in a stage (first tile's segment)
     unsigned sto[kIpt], ao[kIpt];           // conversion source in a stage, A-tile destination
 #pragma unroll
@@ -250,7 +265,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       // copy: lane -> slot 8 kg + lr, chunk pl (a quarter warp: slots r and r + 4, 4 chunks each)
       const int lr = (lane >> 3) + 4 * ((lane >> 2) & 1), pl = 4 * h + (lane & 3);
       const int ql = 8 * kg + lr;
-      src[j] = (ql < krows) ? tab[ql] + 16 * pl : -1;
+      // rows past the staged ones (K padding) copy the last staged row's bytes
+      // again (L2 hits: the same tile reads that row), so every lane issues
+      // the same copies with no branch; B is zero on those rows and their
+      // dots are dropped
+      src[j] = tab[(ql < krows) ? ql : krows - 1] + 16 * pl;
       ldo[j] = (unsigned)(ql * kU + 16 * (pl ^ lr));
       // conversion: lane -> slot 8 kg + kr, chunk pc (a quarter warp: 8 slots, one chunk)
       const int kr = lane & 7, pc = 4 * h + (lane >> 3);
@@ -325,7 +344,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
         const uint8_t* tsrc = a.ring + (int64_t)t * kTileM;
 #pragma unroll
         for (int j = 0; j < kIpt; ++j)
-          if (src[j] >= 0) cp_async16(dst + ldo[j], tsrc + src[j]);
+          cp_async16(dst + ldo[j], tsrc + src[j]);
         if (dots && lane < 8)
           cp_async16(smem_u32(xnw + ld_stage * kMaxConvWarps * kTileM + 16 * lane), tsrc + xsrc);
       }
@@ -364,11 +383,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 #pragma unroll
         for (int j = 0; j < kIpt; ++j) w[j] = *reinterpret_cast<const uint4*>(sb + sto[j]);
         if (dots) {
-          const uint4 xv0 = *reinterpret_cast<const uint4*>(xb + 16 * (lane >> 3));
-          const uint4 xv1 = *reinterpret_cast<const uint4*>(xb + 16 * (4 + (lane >> 3)));
+          const uint8_t* xl = xb + 16 * (lane >> 3);
 #pragma unroll
           for (int j = 0; j < kIpt; ++j) {
-            const uint4 xv = ((cw + conv_warps * j) & 1) ? xv1 : xv0;
+            const uint4 xv = *reinterpret_cast<const uint4*>(xl + 64 * ((cw + conv_warps * j) & 1));
             unsigned d0 = __dp4a(w[j].x, xv.x, 0u);
             unsigned d1 = __dp4a(w[j].y, xv.y, 0u);
             d0 = __dp4a(w[j].z, xv.z, d0);
@@ -410,7 +428,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint32_t idesc = idesc_f16_amn(kTileM, kN);
-      const unsigned bbase = smem_u32(bbuf);
+      // K step ks advances A by 4096 bytes and B by 2 (kN / 8) 128 bytes: the
+      // descriptors' start-address field (bytes / 16) by 256 and by 16 kN / 8
+      const uint64_t bd0 = smem_desc(smem_u32(bbuf), (kN / 8) * 128u, 128u);
+      constexpr uint64_t kBStep = 2u * (kN / 8) * 128u / 16u;
       Ring ab, acc, last;
       int issued = 0;
       for (int it = 0;; ++it) {
@@ -426,13 +447,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
           break;
         }
         fence_after();
-        const unsigned abase = smem_u32(abuf + (size_t)ab.idx * L.a_bytes);
+        const uint64_t ad0 = smem_desc(smem_u32(abuf + (size_t)ab.idx * L.a_bytes), 2048u, 128u);
         const unsigned dt = tbase + (unsigned)(acc.idx * kN);
-        for (int ks = 0; ks < nks; ++ks) {
-          const uint64_t ad = smem_desc(abase + (unsigned)ks * 4096u, 2048u, 128u);
-          const uint64_t bd = smem_desc(bbase + (unsigned)ks * 2u * (kN / 8) * 128u, (kN / 8) * 128u, 128u);
-          mma_f16(dt, ad, bd, idesc, ks > 0 ? 1u : 0u);
-        }
+        mma_f16(dt, ad0, bd0, idesc, 0u);
+        for (int ks = 1; ks < nks; ++ks) mma_f16(dt, ad0 + 256u * ks, bd0 + kBStep * ks, idesc, 1u);
         mma_commit(smem_u32(&sh.a_free[ab.idx]));
         mma_commit(smem_u32(&sh.acc_full[acc.idx]));
         mbar_arrive(smem_u32(&sh.acc_full[acc.idx]));   // release: the epilogue sees tix[]
@@ -449,7 +467,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     float sc[kCols];
 #pragma unroll
     for (int c = 0; c < kCols; ++c) sc[c] = ldexpf(1.f, -sh.expo[c]);
-    float2* out = reinterpret_cast<float2*>(a.phi);
+    float2* out = reinterpret_cast<float2*>(a.phi) + (int64_t)k0 * a.n;
+    const int nq = (a.r - k0 < kMd) ? a.r - k0 : kMd;      // modes of this pass
     Ring acc;
     for (int it = 0;; ++it) {
       if (*stop) break;
@@ -464,31 +483,28 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       if (t < 0) break;                      // no more tiles
       const int64_t i = (int64_t)t * kTileM + 32 * warp + lane;
       fence_after();
-      unsigned v0[32], v1[32], v2[32];
+      unsigned v[PassShape<kMd>::kLoad];
       const unsigned taddr = tbase + ((unsigned)(32 * warp) << 16) + (unsigned)(acc.idx * kN);
-      tmem_ld32_nowait(taddr, v0);
-      tmem_ld32_nowait(taddr + kCols, v1);
-      tmem_ld32_nowait(taddr + 2 * kCols, v2);
-      tmem_ld_wait();
-#pragma unroll
-      for (int q = 0; q < 32; ++q) {     // uses of the loaded registers stay after the wait
-        asm volatile("" : "+r"(v0[q]));
-        asm volatile("" : "+r"(v1[q]));
-        asm volatile("" : "+r"(v2[q]));
-      }
+      if constexpr (PassShape<kMd>::kLoad == 64)
+        tmem_ld64_wait(taddr, v);
+      else
+        tmem_ld96_wait(taddr, v);
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sh.acc_empty[acc.idx]));
       acc.next(kAcc);
       if (i < a.n) {
+        float2* o = out + i;
 #pragma unroll
-        for (int q = 0; q < kModes; ++q) {
-          if (k0 + q < a.r) {
-            const float re = (__uint_as_float(v0[2 * q]) + __uint_as_float(v1[2 * q])) + __uint_as_float(v2[2 * q]);
-            const float im =
-                (__uint_as_float(v0[2 * q + 1]) + __uint_as_float(v1[2 * q + 1])) + __uint_as_float(v2[2 * q + 1]);
-            out[(int64_t)(k0 + q) * a.n + i] = make_float2(re * sc[2 * q], im * sc[2 * q + 1]);
+        for (int q = 0; q < kMd; ++q) {
+          if (nq == kMd || q < nq) {
+            const float re = (__uint_as_float(v[2 * q]) + __uint_as_float(v[kCols + 2 * q])) +
+                             __uint_as_float(v[2 * kCols + 2 * q]);
+            const float im = (__uint_as_float(v[2 * q + 1]) + __uint_as_float(v[kCols + 2 * q + 1])) +
+                             __uint_as_float(v[2 * kCols + 2 * q + 1]);
+            *o = make_float2(re * sc[2 * q], im * sc[2 * q + 1]);
           }
+          o += a.n;
         }
       }
     }
@@ -513,12 +529,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   }
 }
 
-template <int kIpt>
+template <int kIpt, int kMd>
 cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem, int* ctas) {
   static size_t attr = 0;
   if (smem > attr) {
     cudaError_t e =
-        cudaFuncSetAttribute(phi_tc_u8_kernel<kIpt>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(phi_tc_u8_kernel<kIpt, kMd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = smem;
   }
@@ -527,15 +543,22 @@ cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
   const int64_t ntiles = (a.n + kTileM - 1) / kTileM;
-  const int ky = (a.r + kModes - 1) / kModes;
+  const int ky = (a.r + kMd - 1) / kMd;
   int64_t bx = ((int64_t)sms + ky - 1) / ky;
   if (bx > ntiles) bx = ntiles;
   if (bx < 1) bx = 1;
   if (a.fuse && bx > kFusedMaxCtas) bx = kFusedMaxCtas;
   const int threads = 32 * (kConvWarp0 + kpad / (4 * kIpt));
-  phi_tc_u8_kernel<kIpt><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
+  phi_tc_u8_kernel<kIpt, kMd><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
   if (ctas) *ctas = (int)bx;
   return cudaGetLastError();
+}
+
+// one pass of 10 modes when r <= 10 (N = 64), else passes of 16 (N = 96)
+template <int kIpt>
+cudaError_t launch_modes(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem, int* ctas) {
+  if (a.fit_modes && a.r <= 10) return launch_cfg<kIpt, 10>(a, st, kpad, n_a, stages, smem, ctas);
+  return launch_cfg<kIpt, 16>(a, st, kpad, n_a, stages, smem, ctas);
 }
 
 // G's new row and column from the per-CTA sums (exact int64): one block per
@@ -583,9 +606,9 @@ cudaError_t launch_phi_tc_impl(const PhiArgs& a, cudaStream_t st, int* ctas) {
     // at least 116 KiB: one of these CTAs per SM, so its 512 tensor-memory
     // columns are always free
     const size_t smem = L.total < 116 * 1024 ? 116 * 1024 : (size_t)L.total;
-    if (ipt == 4) return launch_cfg<4>(a, st, kpad, cf[0], cf[1], smem, ctas);
-    if (ipt == 8) return launch_cfg<8>(a, st, kpad, cf[0], cf[1], smem, ctas);
-    return launch_cfg<16>(a, st, kpad, cf[0], cf[1], smem, ctas);
+    if (ipt == 4) return launch_modes<4>(a, st, kpad, cf[0], cf[1], smem, ctas);
+    if (ipt == 8) return launch_modes<8>(a, st, kpad, cf[0], cf[1], smem, ctas);
+    return launch_modes<16>(a, st, kpad, cf[0], cf[1], smem, ctas);
   }
   return cudaErrorNotSupported;
 }

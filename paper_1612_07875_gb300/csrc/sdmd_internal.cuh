@@ -193,6 +193,9 @@ struct PhiArgs {
   int32_t fuse = 0;
   int32_t ktot = 0, g0 = 0;
   long long* gpart = nullptr;
+  // 1: modes per tensor-core pass fitted to r (10 when r <= 10: N = 64),
+  // 0: always 16 modes per pass (N = 96); both give the same values
+  int32_t fit_modes = 1;
 };
 // Per-CTA partial capacity of the fused Gram row (CTAs x window slots).
 constexpr int kFusedMaxCtas = 160;

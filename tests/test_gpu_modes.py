@@ -262,7 +262,7 @@ def test_phi_tensor_core_matches_cuda_core_and_oracle(cuda_device, n, m, r):
         for f in frames:
             S.sdmd_push(h, torch.from_numpy(f).to(cuda_device))
         outs = {}
-        for tensor in (1, 0):
+        for tensor in (1, 2, 0):                # tensor cores (modes per pass fitted to r, 16 per pass), CUDA cores
             S.sdmd_set_option(h, S.SDMD_OPT_PHI_TENSOR, tensor)
             phi = torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device)
             lam = np.zeros(2 * r)
@@ -271,6 +271,7 @@ def test_phi_tensor_core_matches_cuda_core_and_oracle(cuda_device, n, m, r):
             P = phi.cpu().numpy()
             outs[tensor] = P[..., 0] + 1j * P[..., 1]
         assert S.sdmd_status(h) == S.SDMD_OK
+        assert np.array_equal(outs[1], outs[2])     # both tensor-core pass shapes: same arithmetic, same bits
         scale = np.abs(outs[0]).max(axis=1, keepdims=True) + 1e-30
         assert (np.abs(outs[1] - outs[0]) <= 2e-5 * scale).all()
         # against the oracle product with the oracle's M on the same window

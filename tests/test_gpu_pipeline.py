@@ -40,6 +40,9 @@ def test_pipelined_step_equals_serial(cuda_device, kind, depth, m, r):
     check = set(range(2, T)) if m < 200 else set(range(6, T, 7)) | {T - 1}
     hp = S.sdmd_create_ex(n, m, dt, depth)
     hs = S.sdmd_create(n, m, dt)
+    # the serial handle's Phi in tensor-core passes of 16 modes: the
+    # pipelined one (one pass of 10 modes where r <= 10) must give the same bits
+    S.sdmd_set_option(hs, S.SDMD_OPT_PHI_TENSOR, 2)
     nb = max(depth, 1)
     phis = [torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device) for _ in range(nb)]
     lam_p = torch.zeros(T, 2 * r, dtype=torch.float64, device=cuda_device)

@@ -77,7 +77,7 @@ def test_static_row_matches_push_row_on_two_calls_in_a_row(cuda_device, kind):
 def test_static_row_tail_only(cuda_device, kind, n):
     # fewer than 16 bytes past the last whole vector: one CTA whose lane 0
     # adds the scalar tail (for n = 1 and 3 with uint8, all of the row)
-    c, ld = 9, 16
+    c, ld = 9, (n + 15) // 16 * 16
     X = _snapshots(kind, c, n, ld, cuda_device, seed=21 + n)
     G = _reference_gram(kind, X, n, cuda_device)
     d = np.diag(G).astype(np.float64)
