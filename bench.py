@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--scpu-seconds", type=float, default=3.0,
                     help="seconds of the streaming CPU Gram update (host cores)")
-    ap.add_argument("--case", choices=["bf16x3_catchup", "batched_rows"], default=None,
+    ap.add_argument("--case", choices=["bf16x3_catchup", "batched_rows", "fused_pass"], default=None,
                     help="run one small fixed workload (for a profiler capture of its kernel) and exit")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served Poisson-arrival run (0 skips the serving measurement)")
@@ -1169,7 +1169,11 @@ def run_case(name):
       then three sdmd_push_batch calls of k = 8 under SDMD_OPT_F32_BF16X3 = 1
       (gram_f32_tc launches);
     batched_rows: 24 streams of the serving mix (each window at most 200 MB)
-      take 260 frames each through sdmd_push_many (gram_rows_batched launches)."""
+      take 260 frames each through sdmd_push_many (gram_rows_batched launches);
+    fused_pass: the HD video stream (n = 1920 x 1080 x 3 uint8, m = 100,
+      r = 10) fills its window, then 24 sdmd_step calls at depth 8: the fused
+      Phi + Gram-row launches of the bench's pipeline (phi_tc_u8 launches;
+      the first ones are the steady-state fused passes)."""
     import torch
 
     from paper_1612_07875_gb300 import sdmd as S
@@ -1190,6 +1194,25 @@ def run_case(name):
         ok = S.sdmd_status(h) == S.SDMD_OK
         S.sdmd_destroy(h)
         info = {"n": n, "m": m, "k": k, "launches": 3}
+    elif name == "fused_pass":
+        vs = synth.VideoStream(seed=synth.config_seed(2))
+        n, D, T = vs.n, 8, M_WIN + 24
+        frames = torch.empty(T, n, dtype=torch.uint8, device=dev)
+        for t in range(T):
+            frames[t].copy_(torch.from_numpy(vs.frame(t)))
+        h = S.sdmd_create_ex(n, M_WIN, S.SDMD_U8, D)
+        phis = [torch.empty(R_MODES, n, 2, dtype=torch.float32, device=dev) for _ in range(D)]
+        lam = torch.empty(T, 2 * R_MODES, dtype=torch.float64, device=dev)
+        rk = torch.empty(T, dtype=torch.int32, device=dev)
+        for t in range(M_WIN):
+            S.sdmd_push(h, frames[t])
+        for t in range(M_WIN, T):
+            S.sdmd_step(h, frames[t], R_MODES, phis[t % D], lam[t], rk[t:t + 1])
+        S.sdmd_sync(h)
+        torch.cuda.synchronize()
+        ok = S.sdmd_status(h) == S.SDMD_OK
+        S.sdmd_destroy(h)
+        info = {"n": n, "m": M_WIN, "r": R_MODES, "depth": D, "steps": T - M_WIN}
     else:
         mix = synth.ServingMix()
         specs = [sp for sp in mix.specs if sp[2] * sp[1] * (1 if sp[0] == "u8" else 4) <= 200e6][:24]

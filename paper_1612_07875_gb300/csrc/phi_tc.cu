@@ -124,18 +124,20 @@ struct TcLayout {
 
 constexpr int kMaxConvWarps = 7;
 
-// fuse: add a private copy of the new snapshot's tile per converter warp and
-// stage (128 bytes each) and the CTA's Gram sums
-__host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages, int fuse = 0) {
+// kb: 128-position MMA blocks per tile (a tile is what one iteration of the
+// roles hands on: its A buffer holds kb blocks, its staging rows kb x 128
+// bytes). fuse: add a private copy of the new snapshot's tile per converter
+// warp and stage and the CTA's Gram sums
+__host__ __device__ inline TcLayout tc_layout(int kpad, int n_a, int stages, int fuse = 0, int kb = 1) {
   TcLayout L;
-  L.a_bytes = kTileM * kpad * 2;                 // multiple of 4096
+  L.a_bytes = kb * kTileM * kpad * 2;            // multiple of 4096
   L.b_off = n_a * L.a_bytes;
   L.b_bytes = kMaxN * kpad * 2;                  // multiple of 3072 (room for 16 modes)
   L.st_off = L.b_off + L.b_bytes;                // 16-byte aligned (cp.async destination)
-  L.st_bytes = kpad * kTileM;
+  L.st_bytes = kpad * kTileM * kb;
   L.tab_off = L.st_off + stages * L.st_bytes;    // window slot offsets (int64)
   L.xn_off = L.tab_off + kMaxRows * 8;
-  L.gs_off = L.xn_off + (fuse ? stages * kMaxConvWarps * kTileM : 0);
+  L.gs_off = L.xn_off + (fuse ? stages * kMaxConvWarps * kTileM * kb : 0);
   L.sh_off = L.gs_off + (fuse ? kMaxRows * 8 : 0);
   L.total = L.sh_off + (int)sizeof(TcShared);
   return L;
@@ -158,13 +160,18 @@ __device__ __forceinline__ void raise_timeout(const PhiArgs& a, volatile int* st
   *stop = 1;
 }
 
-template <int kIpt, int kMd>
+template <int kIpt, int kMd, int kB>
 __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, int kpad, int n_a, int stages) {
-  constexpr int kU = kTileM;             // staging row bytes
+  constexpr int kT = kB * kTileM;        // positions per tile (kB MMA blocks)
+  constexpr int kU = kT;                 // staging row bytes
+  constexpr int kSeg = 2 * kB;           // 64-position segments per tile
   constexpr int kCols = PassShape<kMd>::kCols;
   constexpr int kN = PassShape<kMd>::kN;
+  constexpr int kAccT = (kB * kN * 4 <= kTmemCols) ? 4 : 2;   // accumulator sets (kB x kN columns each)
+  constexpr int kChunkT = kChunk / kB;   // tiles per scheduling grab (1024 positions)
   extern __shared__ __align__(1024) uint8_t smem[];
-  const TcLayout L = tc_layout(kpad, n_a, stages, a.fuse);
+  const TcLayout L = tc_layout(kpad, n_a, stages, a.fuse, kB);
+  const int a_blk = kTileM * kpad * 2;   // one block of an A buffer
   // fused Gram row: only the first mode pass computes it
   const bool dots = a.fuse && blockIdx.y == 0;
   const int krows = dots ? a.ktot : a.p;  // staged rows
@@ -177,10 +184,10 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   volatile int* stop = &sh.stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nthreads = blockDim.x;
-  const int conv_warps = (nthreads >> 5) - kConvWarp0;   // = kpad / (4 kIpt)
+  const int conv_warps = (nthreads >> 5) - kConvWarp0;   // = kpad kB / (4 kIpt)
   const int k0 = blockIdx.y * kMd;
   const int nks = kpad / 16;
-  const int ntiles = (int)((a.n + kTileM - 1) / kTileM);
+  const int ntiles = (int)((a.n + kT - 1) / kT);
 
   if (tid == 0) {
     for (int b = 0; b < kMaxA; ++b) {
@@ -188,7 +195,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       mbar_init(smem_u32(&sh.a_free[b]), 1);
     }
     for (int b = 0; b < 2; ++b) mbar_init(smem_u32(&sh.chunk_bar[b]), 1);
-    for (int b = 0; b < kAcc; ++b) {
+    for (int b = 0; b < kAccT; ++b) {
       mbar_init(smem_u32(&sh.acc_full[b]), 2);
       mbar_init(smem_u32(&sh.acc_empty[b]), kEpiWarps);
     }
@@ -252,8 +259,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   if (warp >= kConvWarp0) {
     // ---------------- load + convert ----------------
     // step j of converter warp cw covers u = cw + conv_warps j: slot group
-    // kg = u / 2 (slots 8 kg .. 8 kg + 7) and positions 64 h .. 64 h + 63
-    // (h = u % 2) of a tile; every (kg, h) is covered exactly once
+    // kg = u / kSeg (slots 8 kg .. 8 kg + 7) and positions 64 h .. 64 h + 63
+    // (h = u % kSeg) of a tile; every (kg, h) is covered exactly once.
+    // Staging rows hold the tile's kU bytes of a slot in 16-byte chunks;
+    // within each 128-byte half the chunk index is XORed with the slot's low
+    // three bits (conflict-free copies and reads)
     const int cw = warp - kConvWarp0;
     int64_t src[kIpt];                      // copy source in the ring (without tile)
     unsigned ldo[kIpt];                     // copy destination in a stage (first tile's segment)
@@ -261,7 +271,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
       const int u = cw + conv_warps * j;
-      const int kg = u >> 1, h = u & 1;
+      const int kg = u / kSeg, h = u % kSeg;
       // copy: lane -> slot 8 kg + lr, chunk pl (a quarter warp: slots r and r + 4, 4 chunks each)
       const int lr = (lane >> 3) + 4 * ((lane >> 2) & 1), pl = 4 * h + (lane & 3);
       const int ql = 8 * kg + lr;
@@ -270,11 +280,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       // the same copies with no branch; B is zero on those rows and their
       // dots are dropped
       src[j] = tab[(ql < krows) ? ql : krows - 1] + 16 * pl;
-      ldo[j] = (unsigned)(ql * kU + 16 * (pl ^ lr));
+      ldo[j] = (unsigned)(ql * kU + 16 * ((pl & ~7) | ((pl & 7) ^ lr)));
       // conversion: lane -> slot 8 kg + kr, chunk pc (a quarter warp: 8 slots, one chunk)
       const int kr = lane & 7, pc = 4 * h + (lane >> 3);
-      sto[j] = (unsigned)((8 * kg + kr) * kU + 16 * (pc ^ kr));
-      ao[j] = (unsigned)((kg * 16 + 2 * pc) * 128 + kr * 16);   // core (2 pc, kg), row kr
+      sto[j] = (unsigned)((8 * kg + kr) * kU + 16 * ((pc & ~7) | ((pc & 7) ^ kr)));
+      // block pc / 8 of the A buffer, core (2 (pc % 8), kg), row kr
+      ao[j] = (unsigned)((pc >> 3) * a_blk + (kg * 16 + 2 * (pc & 7)) * 128 + kr * 16);
     }
     // tile sequence: chunk c (iterations 8 c .. 8 c + 7 of this CTA) starts
     // at the tile index the leader grabbed and published through chunk_bar
@@ -290,11 +301,11 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     auto fix_next = [&]() -> int {           // all converter threads, in step
       int t = -1;
       if (!ended) {
-        const int c = ld_count / kChunk, o = ld_count % kChunk;
+        const int c = ld_count / kChunkT, o = ld_count % kChunkT;
         if (o == 0) {
           const unsigned bar = smem_u32(&sh.chunk_bar[c & 1]);
           if (ct == 0) {
-            sh.chunk[c & 1] = (int)atomicAdd(&a.sched[blockIdx.y], (unsigned)kChunk);
+            sh.chunk[c & 1] = (int)atomicAdd(&a.sched[blockIdx.y], (unsigned)kChunkT);
             mbar_arrive(bar);
           }
           int ok = 1;
@@ -321,19 +332,19 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
     };
     const unsigned stg0 = smem_u32(stg);
     // fused Gram row: this warp's private copy of the new snapshot's tile
-    // (lanes 0..7, 16 bytes each) per stage, and per step j the exact sum of
+    // (lanes 0 .. 8 kB - 1, 16 bytes each) per stage, and per step j the exact sum of
     // <x_slot, x_new> over this lane's 16 positions (computed for every lane,
     // branch-free, in two independent DP4A chains; lanes whose slot is not in
     // the new window drop their sums at the end)
-    uint8_t* xnw = smem + L.xn_off + cw * kTileM;       // stage s at + s * kMaxConvWarps * kTileM
-    const int64_t xsrc = dots ? tab[a.ktot - 1] + 16 * (lane & 7) : 0;
+    uint8_t* xnw = smem + L.xn_off + cw * kT;           // stage s at + s * kMaxConvWarps * kT
+    const int64_t xsrc = dots ? tab[a.ktot - 1] + 16 * (lane & (8 * kB - 1)) : 0;
     unsigned long long gacc[kIpt];
     bool gslot[kIpt];
 #pragma unroll
     for (int j = 0; j < kIpt; ++j) {
       gacc[j] = 0ull;
       const int u = cw + conv_warps * j;
-      const int sl = 8 * (u >> 1) + (lane & 7);
+      const int sl = 8 * (u / kSeg) + (lane & 7);
       gslot[j] = dots && sl >= a.g0 && sl < a.ktot;
     }
     int ld_stage = 0;
@@ -341,12 +352,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       const int t = fix_next();
       if (t >= 0) {
         const unsigned dst = stg0 + (unsigned)(ld_stage * L.st_bytes);
-        const uint8_t* tsrc = a.ring + (int64_t)t * kTileM;
+        const uint8_t* tsrc = a.ring + (int64_t)t * kT;
 #pragma unroll
         for (int j = 0; j < kIpt; ++j)
           cp_async16(dst + ldo[j], tsrc + src[j]);
-        if (dots && lane < 8)
-          cp_async16(smem_u32(xnw + ld_stage * kMaxConvWarps * kTileM + 16 * lane), tsrc + xsrc);
+        if (dots && lane < 8 * kB)
+          cp_async16(smem_u32(xnw + ld_stage * kMaxConvWarps * kT + 16 * lane), tsrc + xsrc);
       }
       ld_stage = (ld_stage + 1 == stages) ? 0 : ld_stage + 1;
     };
@@ -363,7 +374,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       cp_async_wait_pending(stages - 1);     // this lane's copies of tile `it` have landed
       __syncwarp();                          // ... and those of the other lanes of the warp
       const uint8_t* sb = stg + stage * L.st_bytes;
-      const uint8_t* xb = xnw + stage * kMaxConvWarps * kTileM;
+      const uint8_t* xb = xnw + stage * kMaxConvWarps * kT;
       stage = (stage + 1 == stages) ? 0 : stage + 1;
       {
         int ok = 1;
@@ -386,7 +397,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
           const uint8_t* xl = xb + 16 * (lane >> 3);
 #pragma unroll
           for (int j = 0; j < kIpt; ++j) {
-            const uint4 xv = *reinterpret_cast<const uint4*>(xl + 64 * ((cw + conv_warps * j) & 1));
+            const uint4 xv = *reinterpret_cast<const uint4*>(xl + 64 * ((cw + conv_warps * j) % kSeg));
             unsigned d0 = __dp4a(w[j].x, xv.x, 0u);
             unsigned d1 = __dp4a(w[j].y, xv.y, 0u);
             d0 = __dp4a(w[j].z, xv.z, d0);
@@ -421,7 +432,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
         unsigned long long v = gacc[j];
         v += __shfl_xor_sync(0xffffffffu, v, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 16);
-        if (lane < 8 && gslot[j]) atomicAdd(&gsum[8 * ((cw + conv_warps * j) >> 1) + lane], v);
+        if (lane < 8 && gslot[j]) atomicAdd(&gsum[8 * ((cw + conv_warps * j) / kSeg) + lane], v);
       }
     }
   } else if (warp == kMmaWarp) {
@@ -437,7 +448,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       for (int it = 0;; ++it) {
         if (*stop) break;
         bool ok = mbar_wait(smem_u32(&sh.a_full[ab.idx]), ab.phase);
-        if (ok && it >= kAcc) ok = mbar_wait(smem_u32(&sh.acc_empty[acc.idx]), acc.phase ^ 1u);
+        if (ok && it >= kAccT) ok = mbar_wait(smem_u32(&sh.acc_empty[acc.idx]), acc.phase ^ 1u);
         if (!ok) {
           raise_timeout(a, stop);
           break;
@@ -447,17 +458,21 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
           break;
         }
         fence_after();
-        const uint64_t ad0 = smem_desc(smem_u32(abuf + (size_t)ab.idx * L.a_bytes), 2048u, 128u);
-        const unsigned dt = tbase + (unsigned)(acc.idx * kN);
-        mma_f16(dt, ad0, bd0, idesc, 0u);
-        for (int ks = 1; ks < nks; ++ks) mma_f16(dt, ad0 + 256u * ks, bd0 + kBStep * ks, idesc, 1u);
+        const unsigned abase = smem_u32(abuf + (size_t)ab.idx * L.a_bytes);
+#pragma unroll
+        for (int blk = 0; blk < kB; ++blk) {   // block blk of the tile into accumulator columns (acc, blk)
+          const uint64_t ad0 = smem_desc(abase + (unsigned)(blk * a_blk), 2048u, 128u);
+          const unsigned dt = tbase + (unsigned)((acc.idx * kB + blk) * kN);
+          mma_f16(dt, ad0, bd0, idesc, 0u);
+          for (int ks = 1; ks < nks; ++ks) mma_f16(dt, ad0 + 256u * ks, bd0 + kBStep * ks, idesc, 1u);
+        }
         mma_commit(smem_u32(&sh.a_free[ab.idx]));
         mma_commit(smem_u32(&sh.acc_full[acc.idx]));
         mbar_arrive(smem_u32(&sh.acc_full[acc.idx]));   // release: the epilogue sees tix[]
         issued = it + 1;
         last = acc;
         ab.next(n_a);
-        acc.next(kAcc);
+        acc.next(kAccT);
       }
       // no MMA may still write tensor memory when it is freed
       if (issued > 0) mbar_wait(smem_u32(&sh.acc_full[last.idx]), last.phase);
@@ -481,32 +496,37 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
       }
       const int t = sh.tix[it % kTix];
       if (t < 0) break;                      // no more tiles
-      const int64_t i = (int64_t)t * kTileM + 32 * warp + lane;
       fence_after();
-      unsigned v[PassShape<kMd>::kLoad];
-      const unsigned taddr = tbase + ((unsigned)(32 * warp) << 16) + (unsigned)(acc.idx * kN);
-      if constexpr (PassShape<kMd>::kLoad == 64)
-        tmem_ld64_wait(taddr, v);
-      else
-        tmem_ld96_wait(taddr, v);
-      fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&sh.acc_empty[acc.idx]));
-      acc.next(kAcc);
-      if (i < a.n) {
-        float2* o = out + i;
+#pragma unroll 1
+      for (int blk = 0; blk < kB; ++blk) {   // the tile's blocks one after the other
+        const int64_t i = (int64_t)t * kT + blk * kTileM + 32 * warp + lane;
+        unsigned v[PassShape<kMd>::kLoad];
+        const unsigned taddr = tbase + ((unsigned)(32 * warp) << 16) + (unsigned)((acc.idx * kB + blk) * kN);
+        if constexpr (PassShape<kMd>::kLoad == 64)
+          tmem_ld64_wait(taddr, v);
+        else
+          tmem_ld96_wait(taddr, v);
+        if (blk + 1 == kB) {                 // every block of the set read: hand it back
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&sh.acc_empty[acc.idx]));
+        }
+        if (i < a.n) {
+          float2* o = out + i;
 #pragma unroll
-        for (int q = 0; q < kMd; ++q) {
-          if (nq == kMd || q < nq) {
-            const float re = (__uint_as_float(v[2 * q]) + __uint_as_float(v[kCols + 2 * q])) +
-                             __uint_as_float(v[2 * kCols + 2 * q]);
-            const float im = (__uint_as_float(v[2 * q + 1]) + __uint_as_float(v[kCols + 2 * q + 1])) +
-                             __uint_as_float(v[2 * kCols + 2 * q + 1]);
-            *o = make_float2(re * sc[2 * q], im * sc[2 * q + 1]);
+          for (int q = 0; q < kMd; ++q) {
+            if (nq == kMd || q < nq) {
+              const float re = (__uint_as_float(v[2 * q]) + __uint_as_float(v[kCols + 2 * q])) +
+                               __uint_as_float(v[2 * kCols + 2 * q]);
+              const float im = (__uint_as_float(v[2 * q + 1]) + __uint_as_float(v[kCols + 2 * q + 1])) +
+                               __uint_as_float(v[2 * kCols + 2 * q + 1]);
+              *o = make_float2(re * sc[2 * q], im * sc[2 * q + 1]);
+            }
+            o += a.n;
           }
-          o += a.n;
         }
       }
+      acc.next(kAccT);
     }
   }
   __syncthreads();
@@ -529,12 +549,12 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
   }
 }
 
-template <int kIpt, int kMd>
+template <int kIpt, int kMd, int kB>
 cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem, int* ctas) {
   static size_t attr = 0;
   if (smem > attr) {
     cudaError_t e =
-        cudaFuncSetAttribute(phi_tc_u8_kernel<kIpt, kMd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(phi_tc_u8_kernel<kIpt, kMd, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr = smem;
   }
@@ -542,23 +562,23 @@ cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
-  const int64_t ntiles = (a.n + kTileM - 1) / kTileM;
+  const int64_t ntiles = (a.n + kB * kTileM - 1) / (kB * kTileM);
   const int ky = (a.r + kMd - 1) / kMd;
   int64_t bx = ((int64_t)sms + ky - 1) / ky;
   if (bx > ntiles) bx = ntiles;
   if (bx < 1) bx = 1;
   if (a.fuse && bx > kFusedMaxCtas) bx = kFusedMaxCtas;
-  const int threads = 32 * (kConvWarp0 + kpad / (4 * kIpt));
-  phi_tc_u8_kernel<kIpt, kMd><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
+  const int threads = 32 * (kConvWarp0 + kpad * kB / (4 * kIpt));
+  phi_tc_u8_kernel<kIpt, kMd, kB><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
   if (ctas) *ctas = (int)bx;
   return cudaGetLastError();
 }
 
 // one pass of 10 modes when r <= 10 (N = 64), else passes of 16 (N = 96)
-template <int kIpt>
+template <int kIpt, int kB>
 cudaError_t launch_modes(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem, int* ctas) {
-  if (a.fit_modes && a.r <= 10) return launch_cfg<kIpt, 10>(a, st, kpad, n_a, stages, smem, ctas);
-  return launch_cfg<kIpt, 16>(a, st, kpad, n_a, stages, smem, ctas);
+  if (a.fit_modes && a.r <= 10) return launch_cfg<kIpt, 10, kB>(a, st, kpad, n_a, stages, smem, ctas);
+  return launch_cfg<kIpt, 16, kB>(a, st, kpad, n_a, stages, smem, ctas);
 }
 
 // G's new row and column from the per-CTA sums (exact int64): one block per
@@ -597,18 +617,29 @@ cudaError_t launch_phi_tc_impl(const PhiArgs& a, cudaStream_t st, int* ctas) {
       ipt = 16;
     }
   }
+  const int kLimit = 227 * 1024;
+  // at least 116 KiB of shared memory: one of these CTAs per SM, so its 512
+  // tensor-memory columns are always free
+  auto smem_of = [](const TcLayout& L) { return L.total < 116 * 1024 ? (size_t)116 * 1024 : (size_t)L.total; };
+  // K <= 112 with fitted shapes: tiles of two 128-position blocks (every
+  // role hands on 256 positions at a time, eight units per converter lane,
+  // the same converter warps), when two A buffers and three stages fit
+  if (ipt == 4 && a.fit_modes) {
+    static const int kConfigs2[][2] = {{2, 4}, {2, 3}};
+    for (const auto& cf : kConfigs2) {
+      const TcLayout L = tc_layout(kpad, cf[0], cf[1], a.fuse, 2);
+      if (L.total > kLimit) continue;
+      return launch_modes<8, 2>(a, st, kpad, cf[0], cf[1], smem_of(L), ctas);
+    }
+  }
   // deepest A ring first, then the deepest staging ring, within 227 KiB
   static const int kConfigs[][2] = {{4, 6}, {4, 5}, {4, 4}, {3, 5}, {3, 4}, {2, 6}, {2, 4}, {2, 3}, {1, 4}, {1, 3}};
-  const int kLimit = 227 * 1024;
   for (const auto& cf : kConfigs) {
     const TcLayout L = tc_layout(kpad, cf[0], cf[1], a.fuse);
     if (L.total > kLimit) continue;
-    // at least 116 KiB: one of these CTAs per SM, so its 512 tensor-memory
-    // columns are always free
-    const size_t smem = L.total < 116 * 1024 ? 116 * 1024 : (size_t)L.total;
-    if (ipt == 4) return launch_modes<4>(a, st, kpad, cf[0], cf[1], smem, ctas);
-    if (ipt == 8) return launch_modes<8>(a, st, kpad, cf[0], cf[1], smem, ctas);
-    return launch_modes<16>(a, st, kpad, cf[0], cf[1], smem, ctas);
+    if (ipt == 4) return launch_modes<4, 1>(a, st, kpad, cf[0], cf[1], smem_of(L), ctas);
+    if (ipt == 8) return launch_modes<8, 1>(a, st, kpad, cf[0], cf[1], smem_of(L), ctas);
+    return launch_modes<16, 1>(a, st, kpad, cf[0], cf[1], smem_of(L), ctas);
   }
   return cudaErrorNotSupported;
 }
