@@ -508,6 +508,26 @@ SDMD_API int sdmd_trace_times(sdmd_t h, int32_t kernel, double *ms, int32_t cap,
 SDMD_API int sdmd_modes_phase_cycles(sdmd_t h, int64_t *cycles, int32_t count, void *stream);
 
 /*
+ * sdmd_modes_many -- the small algebra of exact DMD (as sdmd_modes, Sec. 2.2,
+ * Eqs. 7-8; Algorithm 2: eig of G_X, rank, sigma, V, A~, eig(A~), the
+ * amplitudes) for `count` <= 64 real dense handles in one launch, one CTA per
+ * handle, each on its own G and workspace: the eigenvalues, rank and every
+ * later sdmd_svd / sdmd_amplitudes / sdmd_reconstruct of a handle are the
+ * same bits as after sdmd_modes(hs[i], r[i], NULL, ...). Serves many streams
+ * whose frames arrive together (the serving loop), where one-CTA launches
+ * per stream would queue behind each other.
+ *   hs      count handles (distinct, one device, >= 3 snapshots each)
+ *   r       count requested ranks, 1 <= r[i] <= m_i - 1 (host)
+ *   lambda  NULL, or count pointers (host array) to r[i] complex128 each,
+ *           device or pinned host memory (an entry may be NULL)
+ *   r_out   NULL, or count int32 kept ranks (device or pinned host)
+ * No Phi: use sdmd_pod_modes / sdmd_reconstruct, or sdmd_modes per handle.
+ * Errors as sdmd_modes; SDMD_ERR_UNSUPPORTED for complex handles.
+ */
+SDMD_API int sdmd_modes_many(const sdmd_t *hs, int32_t count, const int32_t *r, void *const *lambda,
+                             int32_t *r_out, void *stream);
+
+/*
  * sdmd_newest_row / sdmd_set_newest_row -- read or overwrite the newest
  * snapshot's row of the window's G (and, for the set, its column: the
  * conjugate), in time order: entry q is <x_q, x_new> for the q-th oldest

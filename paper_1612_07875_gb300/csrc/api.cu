@@ -994,6 +994,63 @@ int sdmd_gram(sdmd_t h, void* G, void* stream) {
   return SDMD_OK;
 }
 
+int sdmd_modes_many(const sdmd_t* hs, int32_t count, const int32_t* r, void* const* lambda, int32_t* r_out,
+                    void* stream) {
+  if (!hs || !r || count < 1 || count > kMaxModesJobs)
+    return fail(SDMD_ERR_ARG, "sdmd_modes_many: count=%d not in [1, %d] or NULL arrays", count, kMaxModesJobs);
+  for (int i = 0; i < count; ++i) {
+    const sdmd_s* h = hs[i];
+    if (!h) return fail(SDMD_ERR_ARG, "sdmd_modes_many: NULL handle %d", i);
+    if (h->dtype != SDMD_F32 && h->dtype != SDMD_U8)
+      return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes_many: handle %d is not a real dense handle", i);
+    if (h->device != hs[0]->device) return fail(SDMD_ERR_ARG, "sdmd_modes_many: handles on different devices");
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == h) return fail(SDMD_ERR_ARG, "sdmd_modes_many: handle %d appears twice", i);
+    const int c = resident(h);
+    if (c < 3) return fail(SDMD_ERR_NOT_READY, "sdmd_modes_many: handle %d has %d snapshots, need >= 3", i, c);
+    if (r[i] < 1 || r[i] > h->m - 1)
+      return fail(SDMD_ERR_ARG, "sdmd_modes_many: r[%d]=%d not in [1, %d]", i, r[i], h->m - 1);
+    if (lambda && lambda[i] && ptr_kind(lambda[i]) == kPageable)
+      return fail(SDMD_ERR_ARG, "sdmd_modes_many: lambda[%d] must be device or pinned host memory", i);
+  }
+  if (r_out && ptr_kind(r_out) == kPageable)
+    return fail(SDMD_ERR_ARG, "sdmd_modes_many: r_out must be device or pinned host memory");
+  DeviceScope ds(hs[0]->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ModesBatch b;
+  b.count = count;
+  for (int i = 0; i < count; ++i) {
+    sdmd_s* h = hs[i];
+    const int rc = flush_pending(h, st);
+    if (rc != SDMD_OK) return rc;
+    ModesArgs& a = b.job[i];
+    a.G = h->G;
+    a.g_is_int = (h->dtype == SDMD_U8) ? 1 : 0;
+    a.m = h->cap;
+    a.ws_m = h->m;
+    a.c = resident(h);
+    a.start = oldest_slot(h);
+    a.r_req = r[i];
+    a.ws = h->ws;
+    a.status = h->status;
+    a.r_dev = h->r_dev;
+  }
+  {
+    TraceScope ts(hs[0], SDMD_K_MODES, st);
+    CK(launch_modes_batch(b, st));
+  }
+  for (int i = 0; i < count; ++i) {
+    sdmd_s* h = hs[i];
+    const ModesLayout L = modes_layout(h->m);
+    if (lambda && lambda[i]) CK(cudaMemcpyAsync(lambda[i], h->ws + L.lamout, (size_t)r[i] * 16, cudaMemcpyDefault, st));
+    if (r_out) CK(cudaMemcpyAsync(r_out + i, h->r_dev, sizeof(int32_t), cudaMemcpyDefault, st));
+    h->last_r = r[i];
+    h->last_p = resident(h) - 1;
+    h->modes_count = h->count;
+  }
+  return SDMD_OK;
+}
+
 int sdmd_newest_row(sdmd_t h, void* row, void* stream) {
   if (!h || !row) return fail(SDMD_ERR_ARG, "sdmd_newest_row: NULL argument");
   DeviceScope ds(h->device);

@@ -738,7 +738,7 @@ __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   return s;
 }
 
-__global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, ModesLayout L) {
+__device__ __forceinline__ void modes_small_body(const ModesArgs& a, const ModesLayout& L) {
   extern __shared__ double smem_d[];
   __shared__ dd red[kWarps];
   __shared__ float cs[SDMD_MAX_M];
@@ -1123,6 +1123,15 @@ __global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, M
   }
 }
 
+__global__ void __launch_bounds__(kThreads, 1) modes_small_kernel(ModesArgs a, ModesLayout L) { modes_small_body(a, L); }
+
+// One CTA per job: the eigensolvers of up to kMaxModesJobs windows (of any
+// length) in one launch, each CTA on its own handle's G and workspace.
+__global__ void __launch_bounds__(kThreads, 1) modes_batch_kernel(ModesBatch b) {
+  const ModesArgs a = b.job[blockIdx.x];
+  modes_small_body(a, modes_layout(a.ws_m));
+}
+
 
 // ------------------------------------------------------- complex windows --
 // The small-matrix part of exact DMD for complex snapshots (dense complex64
@@ -1467,7 +1476,7 @@ __global__ void __launch_bounds__(kCThreads, 1) modes_complex_kernel(ModesArgs a
 
 }  // namespace
 
-ModesLayout modes_layout(int m) {
+__host__ __device__ ModesLayout modes_layout(int m) {
   const int64_t p = m - 1 > 1 ? m - 1 : 1;
   const int64_t p2 = p * p;
   ModesLayout L;
@@ -1518,6 +1527,24 @@ cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
     attr_bytes = bytes;
   }
   modes_small_kernel<<<1, kThreads, bytes, st>>>(a, modes_layout(a.ws_m));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_modes_batch(const ModesBatch& b, cudaStream_t st) {
+  if (b.count < 1 || b.count > kMaxModesJobs) return cudaErrorInvalidValue;
+  static size_t attr_bytes = 0;
+  size_t bytes = 0;
+  for (int i = 0; i < b.count; ++i) {
+    const SmemPlan plan = smem_plan(b.job[i].c - 1, b.job[i].r_req);
+    const size_t jb = (size_t)(plan.vec_units + plan.rr_units + plan.big_units + plan.inv_units) * 8;
+    if (jb > bytes) bytes = jb;
+  }
+  if (bytes > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(modes_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    attr_bytes = bytes;
+  }
+  modes_batch_kernel<<<b.count, kThreads, bytes, st>>>(b);
   return cudaGetLastError();
 }
 

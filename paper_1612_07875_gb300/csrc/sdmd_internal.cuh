@@ -162,9 +162,17 @@ struct ModesLayout {
   int64_t cx;     // complex windows: six p x p complex128 arrays (V of sdmd_svd at the sixth)
   int64_t total;
 };
-ModesLayout modes_layout(int m);
+__host__ __device__ ModesLayout modes_layout(int m);
 
 cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st);
+// The real-window eigensolvers of several handles in one launch (one CTA per
+// job; each job exactly as launch_modes_small would run it alone).
+constexpr int kMaxModesJobs = 64;
+struct ModesBatch {
+  ModesArgs job[kMaxModesJobs];
+  int32_t count;
+};
+cudaError_t launch_modes_batch(const ModesBatch& b, cudaStream_t st);
 // The same outputs for complex windows (G complex128 Hermitian): FP64 Jacobi
 // for G_X, complex A~, W, M and amplitudes.
 cudaError_t launch_modes_complex(const ModesArgs& a, cudaStream_t st);

@@ -72,6 +72,7 @@ _SIGNATURES = {
     "sdmd_rebuild": [_VP, _VP],
     "sdmd_gram": [_VP, _VP, _VP],
     "sdmd_newest_row": [_VP, _VP, _VP],
+    "sdmd_modes_many": [ctypes.POINTER(_VP), _I32, ctypes.POINTER(_I32), ctypes.POINTER(_VP), _VP, _VP],
     "sdmd_set_newest_row": [_VP, _VP, _VP],
     "sdmd_modes": [_VP, _I32, _VP, _VP, _VP, _VP],
     "sdmd_svd": [_VP, _I32, _VP, _VP, _VP],
@@ -217,6 +218,17 @@ def sdmd_count(h):
 
 def sdmd_gram(h, G, stream=None):
     _check(lib().sdmd_gram(h, ptr(G), stream_handle(stream)), "sdmd_gram")
+
+
+def sdmd_modes_many(hs, r, lambdas=None, r_out=None, stream=None):
+    """Eigensolvers of several handles in one launch (see sdmd.h); r is one
+    int or a list, lambdas a list of per-handle buffers (or None)."""
+    count = len(hs)
+    rr = [int(r)] * count if isinstance(r, int) else [int(x) for x in r]
+    harr = (_VP * count)(*hs)
+    rarr = (_I32 * count)(*rr)
+    larr = (_VP * count)(*[ptr(x) for x in lambdas]) if lambdas is not None else None
+    _check(lib().sdmd_modes_many(harr, count, rarr, larr, ptr(r_out), stream_handle(stream)), "sdmd_modes_many")
 
 
 def sdmd_newest_row(h, row, stream=None):

@@ -240,3 +240,49 @@ def test_autotune_keeps_the_gram_exact(cuda_device):
             assert S.sdmd_status(h) == S.SDMD_OK
         finally:
             S.sdmd_destroy(h)
+
+
+def test_modes_many_equals_one_handle_at_a_time(cuda_device):
+    # sdmd_modes_many: the eigensolvers of several windows (uneven n, window
+    # length, element type, rank) in one launch give, bit for bit, the
+    # eigenvalues, rank and singular values of sdmd_modes on each handle
+    specs = [("u8", 100003, 16, 5), ("f32", (1 << 16) + 7, 32, 10), ("u8", 6000, 127, 20), ("f32", 777, 5, 4),
+             ("u8", 4096 * 3, 64, 63), ("f32", 3000, 100, 10), ("u8", 50000, 256, 10)]
+    rng = np.random.default_rng(12)
+    hs = []
+    try:
+        for kind, n, m, _ in specs:
+            h = S.sdmd_create(n, m, DT[kind])
+            hs.append(h)
+            base = _frame(kind, n, rng)
+            for t in range(m + 3):
+                # slowly drifting frames, so the windows have structure
+                f = base if kind == "u8" and t % 3 else _frame(kind, n, rng)
+                S.sdmd_push(h, torch.from_numpy(f).to(cuda_device))
+        rs = [r for *_, r in specs]
+        lams = [torch.full((2 * r,), -1.0, dtype=torch.float64, device=cuda_device) for r in rs]
+        rk = torch.full((len(hs),), -1, dtype=torch.int32, device=cuda_device)
+        S.sdmd_modes_many(hs, rs, lams, rk)
+        sig_b = []
+        for h, r in zip(hs, rs):
+            sg = torch.zeros(r, dtype=torch.float64, device=cuda_device)
+            S.sdmd_svd(h, r, sg, None)
+            sig_b.append(sg)
+        torch.cuda.synchronize()
+        for i, (h, r) in enumerate(zip(hs, rs)):
+            lam1 = torch.full((2 * r,), -1.0, dtype=torch.float64, device=cuda_device)
+            rk1 = torch.full((1,), -1, dtype=torch.int32, device=cuda_device)
+            S.sdmd_modes(h, r, None, lam1, rk1)
+            sg = torch.zeros(r, dtype=torch.float64, device=cuda_device)
+            S.sdmd_svd(h, r, sg, None)
+            torch.cuda.synchronize()
+            assert torch.equal(lam1, lams[i]), i
+            assert int(rk1.item()) == int(rk[i].item()) >= 1, i
+            assert torch.equal(sg, sig_b[i]), i
+            assert S.sdmd_status(h) == S.SDMD_OK
+        with pytest.raises(S.SdmdError) as ei:
+            S.sdmd_modes_many([hs[0], hs[0]], 3)
+        assert ei.value.code == S.SDMD_ERR_ARG
+    finally:
+        for h in hs:
+            S.sdmd_destroy(h)
