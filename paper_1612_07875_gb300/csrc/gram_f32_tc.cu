@@ -67,14 +67,17 @@ constexpr int kRowsM = 128;          // MMA M
 constexpr int kKst = 64;             // positions per K-step (= accumulation period)
 constexpr int kStepsPerChunk = 16;   // scheduling unit: 1024 positions, 4 KiB per row
 constexpr int kStages = 4;           // staging ring (fp32): three K-steps in flight
+constexpr int kStagesStk = 3;        // ... with the stacked B tiles (two K-steps in flight)
+constexpr int kStkMaxT = 32;         // targets (rounded to 16) for the stacked B tiles
 constexpr int kTiles = 2;            // ring of term tiles
 constexpr int kRowBytes = kKst * 4;                        // 256 B of a row per K-step
 constexpr int kTermBytes = kRowsM * kKst * 2;              // 16384
 constexpr int kTileBytes = 3 * kTermBytes;                 // 49152
 constexpr int kStageBytes = kRowsM * kRowBytes;            // 32768
 constexpr int kAcc = 4;              // TMEM accumulators
-constexpr int kAccCols = kGramF32MaxTargets;               // 64
-constexpr int kTmemCols = kAcc * kAccCols;                 // 256
+constexpr int kAccCols = kGramF32MaxTargets;               // 64 (the partials' row stride)
+constexpr int kAccColsStk = 3 * kStkMaxT;                  // 96: three column groups
+constexpr int kStkBytes = 3 * kStkMaxT * 128;              // stacked B tile: three terms' target rows
 
 struct F32Shared {
   unsigned long long tile_full[kTiles];   // tile split (converter warps)
@@ -86,7 +89,16 @@ struct F32Shared {
   int64_t tab[kRowsM];                    // ring byte offset of tile row i
 };
 
-constexpr int kSmemBytes = kTiles * kTileBytes + kStages * kStageBytes + (int)sizeof(F32Shared);
+template <bool kStk>
+struct F32Layout {
+  static constexpr int kSt = kStk ? kStagesStk : kStages;
+  static constexpr int kStkOff = kTiles * kTileBytes;                  // 1024-aligned
+  static constexpr int kStgOff = kStkOff + (kStk ? kTiles * kStkBytes : 0);
+  static constexpr int kShOff = kStgOff + kSt * kStageBytes;
+  static constexpr int kBytes = kShOff + (int)sizeof(F32Shared);
+  static constexpr int kAccStride = kStk ? kAccColsStk : kAccCols;  // TMEM columns per accumulator
+  static constexpr int kTmem = kStk ? 512 : 256;
+};
 
 __device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
@@ -124,11 +136,22 @@ __device__ __forceinline__ void two_sum_add(float& hi, float& lo, float v) {
   lo = __fadd_rn(lo, e);
 }
 
+// kStk (targets rounded to 16 at most 32): the target rows of the three
+// terms are also written, stacked, into a small B tile, so that one MMA per
+// A term and K-slice covers all its B terms (N = 3, 2, 1 x npad): 12 MMAs per
+// K-step instead of 24. The products b_i c_j then land in column group j;
+// every group starts from zero (the drain writes zeros back after reading),
+// takes its small terms first, and the drain adds the groups.
+template <bool kStk>
 __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a) {
+  using Lay = F32Layout<kStk>;
+  constexpr int kSt = Lay::kSt;
+  constexpr int kAccStride = Lay::kAccStride;
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t* tiles = smem;
-  uint8_t* stg = smem + kTiles * kTileBytes;
-  F32Shared& sh = *reinterpret_cast<F32Shared*>(smem + kTiles * kTileBytes + kStages * kStageBytes);
+  uint8_t* stk = smem + Lay::kStkOff;
+  uint8_t* stg = smem + Lay::kStgOff;
+  F32Shared& sh = *reinterpret_cast<F32Shared*>(smem + Lay::kShOff);
   volatile int* stop = &sh.stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int kt = a.k;                          // targets: tile rows 0 .. kt - 1
@@ -150,13 +173,16 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
     sh.stop = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
-  if (warp == kMmaWarp) tmem_alloc(smem_u32(&sh.tmem_base), kTmemCols);
+  if (warp == kMmaWarp) tmem_alloc(smem_u32(&sh.tmem_base), Lay::kTmem);
   for (int r = tid; r < rows; r += kThreads) {
     const int t = (r < kt) ? a.t_tgt + r : a.t_old + (r - kt);   // window time index of tile row r
     sh.tab[r] = (int64_t)((a.start + t) % a.m) * a.slot_bytes;
   }
-  for (int idx = tid; idx < kStages * kStageBytes / 16; idx += kThreads)
+  for (int idx = tid; idx < kSt * kStageBytes / 16; idx += kThreads)
     reinterpret_cast<uint4*>(stg)[idx] = make_uint4(0u, 0u, 0u, 0u);
+  if (kStk)   // stacked B rows past the targets stay zero
+    for (int idx = tid; idx < kTiles * kStkBytes / 16; idx += kThreads)
+      reinterpret_cast<uint4*>(stk)[idx] = make_uint4(0u, 0u, 0u, 0u);
   // rows beyond `rows` stay zero in every term of both tiles
   for (int idx = tid; idx < kTiles * 3 * kRowsM * (kKst / 8); idx += kThreads) {
     const int tt = idx / (kRowsM * (kKst / 8)), rem = idx - tt * (kRowsM * (kKst / 8));
@@ -169,6 +195,18 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
   __syncthreads();
   fence_after();
   const unsigned tbase = sh.tmem_base;
+  if (kStk) {   // every accumulator starts at zero (the MMAs only accumulate)
+    if (warp < kDrainWarps) {
+      const int lq = warp & 3, half = warp >> 2;
+      constexpr int kHalfCols = kAcc * kAccStride / 2;
+      for (int c = 0; c < kHalfCols; c += 8)
+        tmem_st8_zero(tbase + ((unsigned)(32 * lq) << 16) + (unsigned)(half * kHalfCols + c));
+      tmem_st_wait();
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+  }
 
   if (warp >= kConvWarp0) {
     // ---------------- load + split ----------------
@@ -208,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
     auto load = [&](int64_t s) {
       if (s < nsteps) {
         const int64_t off = step_pos(s) * 4;
-        const unsigned dst = stg0 + (unsigned)((s % kStages) * kStageBytes);
+        const unsigned dst = stg0 + (unsigned)((s % kSt) * kStageBytes);
 #pragma unroll
         for (int gi = 0; gi < kGroupsPerWarp; ++gi)
 #pragma unroll
@@ -218,11 +256,11 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
       cp_async_commit();                       // one group per K-step, empty past the end
     };
     prefetch_half(0);
-    for (int s = 0; s < kStages - 1; ++s) load(s);
+    for (int s = 0; s < kSt - 1; ++s) load(s);
     for (int64_t s = 0; s < nsteps && !*stop; ++s) {
       if (s % 8 == 0) prefetch_half(s + 8);
-      load(s + kStages - 1);
-      cp_async_wait<kStages - 1>();            // this lane's copies of K-step s have landed
+      load(s + kSt - 1);
+      cp_async_wait<kSt - 1>();                // this lane's copies of K-step s have landed
       __syncwarp();                            // ... and those of the other lanes
       const int tb = (int)(s % kTiles);
       const bool ok = s < kTiles || mbar_wait(smem_u32(&sh.tile_free[tb]), (unsigned)(((s / kTiles) & 1) ^ 1));
@@ -232,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
       }
       const int64_t p0 = step_pos(s);
       const bool tail = p0 + kKst > a.n;       // positions past n contribute nothing
-      const uint8_t* sb = stg + (s % kStages) * kStageBytes;
+      const uint8_t* sb = stg + (s % kSt) * kStageBytes;
       uint8_t* tile = tiles + tb * kTileBytes;
 #pragma unroll
       for (int gi = 0; gi < kGroupsPerWarp; ++gi) {
@@ -265,6 +303,13 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
           *reinterpret_cast<uint4*>(cp) = t0;
           *reinterpret_cast<uint4*>(cp + kTermBytes) = t1;
           *reinterpret_cast<uint4*>(cp + 2 * kTermBytes) = t2;
+          if (kStk && 8 * g < kt) {            // a target row: also into the stacked B tile
+            // term t's target rows at t * npad * 128 (1024-aligned: the same swizzle phase)
+            uint8_t* bp = stk + tb * kStkBytes + (8 * g + rsub) * 128 + 16 * ((kq + 4 * h) ^ rsub);
+            *reinterpret_cast<uint4*>(bp) = t0;
+            *reinterpret_cast<uint4*>(bp + npad * 128) = t1;
+            *reinterpret_cast<uint4*>(bp + 2 * npad * 128) = t2;
+          }
         }
       }
       fence_proxy_async();
@@ -301,17 +346,35 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
         }
         fence_after();
         const unsigned base = smem_u32(tiles + tb * kTileBytes);
-        const unsigned dt = tbase + (unsigned)(ac * kAccCols);
-        int first = 1;
+        const unsigned dt = tbase + (unsigned)(ac * kAccStride);
+        if (kStk) {
+          // A term i against the stacked B terms 0 .. G - 1 - i (G = split):
+          // smallest products first; every MMA accumulates onto the zeroed groups
+          const unsigned sbase = smem_u32(stk + tb * kStkBytes);
+          const int G = (a.split == 2) ? 2 : 3;
+          for (int i = G - 1; i >= 0; --i) {
+            const int nb = G - i;                      // B terms 0 .. nb - 1
+            const uint32_t idn = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)((nb * npad) >> 3) << 17) |
+                                 ((uint32_t)(kRowsM >> 4) << 24);
 #pragma unroll
-        for (int pr = 0; pr < kPairs; ++pr) {
-          if (pr < pr0) continue;
+            for (int ks = 0; ks < kKst / 16; ++ks) {
+              const uint64_t da = smem_desc_sw128(base + (unsigned)(i * kTermBytes + ks * 32));
+              const uint64_t db = smem_desc_sw128(sbase + (unsigned)(ks * 32));
+              mma_f16(dt, da, db, idn, 1u);
+            }
+          }
+        } else {
+          int first = 1;
 #pragma unroll
-          for (int ks = 0; ks < kKst / 16; ++ks) {
-            const uint64_t da = smem_desc_sw128(base + (unsigned)(pa[pr] * kTermBytes + ks * 32));
-            const uint64_t db = smem_desc_sw128(base + (unsigned)(pb[pr] * kTermBytes + ks * 32));
-            mma_f16(dt, da, db, idesc, first ? 0u : 1u);
-            first = 0;
+          for (int pr = 0; pr < kPairs; ++pr) {
+            if (pr < pr0) continue;
+#pragma unroll
+            for (int ks = 0; ks < kKst / 16; ++ks) {
+              const uint64_t da = smem_desc_sw128(base + (unsigned)(pa[pr] * kTermBytes + ks * 32));
+              const uint64_t db = smem_desc_sw128(base + (unsigned)(pb[pr] * kTermBytes + ks * 32));
+              mma_f16(dt, da, db, idesc, first ? 0u : 1u);
+              first = 0;
+            }
           }
         }
         mma_commit(smem_u32(&sh.tile_free[tb]));
@@ -326,9 +389,10 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
     const int lq = warp & 3, half = warp >> 2;
     const int cols = npad / 2;                         // multiple of 8, <= 32
     const int col0 = half * cols;
-    float hi[32], lo[32];
+    constexpr int kDc = kStk ? kStkMaxT / 2 : 32;       // target columns per drain warp, at most
+    float hi[kDc], lo[kDc];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) hi[i] = lo[i] = 0.f;
+    for (int i = 0; i < kDc; ++i) hi[i] = lo[i] = 0.f;
     for (int64_t s = 0; s < nsteps; ++s) {
       if (*stop) break;
       const int ac = (int)(s % kAcc);
@@ -338,17 +402,35 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
         break;
       }
       fence_after();
-      const unsigned taddr = tbase + ((unsigned)(32 * lq) << 16) + (unsigned)(ac * kAccCols + col0);
+      const unsigned taddr = tbase + ((unsigned)(32 * lq) << 16) + (unsigned)(ac * kAccStride + col0);
 #pragma unroll
-      for (int pc = 0; pc < 4; ++pc) {
+      for (int pc = 0; pc < kDc / 8; ++pc) {
         if (8 * pc < cols) {
           unsigned v[8];
           tmem_ld8_nowait(taddr + 8 * pc, v);
           tmem_ld_wait();
+          if (kStk) {
+            // column groups 1 and 2 (B terms 1, 2) of the same targets; then
+            // all three back to zero for the accumulator's next use
+            unsigned v1[8], v2[8];
+            tmem_ld8_nowait(taddr + npad + 8 * pc, v1);
+            if (a.split != 2) tmem_ld8_nowait(taddr + 2 * npad + 8 * pc, v2);
+            tmem_ld_wait();
 #pragma unroll
-          for (int i = 0; i < 8; ++i) two_sum_add(hi[8 * pc + i], lo[8 * pc + i], __uint_as_float(v[i]));
+            for (int i = 0; i < 8; ++i) {
+              const float g12 = (a.split != 2) ? __uint_as_float(v1[i]) + __uint_as_float(v2[i]) : __uint_as_float(v1[i]);
+              two_sum_add(hi[8 * pc + i], lo[8 * pc + i], __uint_as_float(v[i]) + g12);
+            }
+            tmem_st8_zero(taddr + 8 * pc);
+            tmem_st8_zero(taddr + npad + 8 * pc);
+            if (a.split != 2) tmem_st8_zero(taddr + 2 * npad + 8 * pc);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) two_sum_add(hi[8 * pc + i], lo[8 * pc + i], __uint_as_float(v[i]));
+          }
         }
       }
+      if (kStk) tmem_st_wait();
       fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&sh.acc_empty[ac]));
@@ -357,7 +439,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
     const int row = 32 * lq + lane;
     float2* P = a.partials + (int64_t)blockIdx.x * kRowsM * kAccCols;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < kDc; ++i) {
       const int col = col0 + i;
       if (i < cols && row < rows && col < kt) P[(int64_t)row * kAccCols + col] = make_float2(hi[i], lo[i]);
     }
@@ -365,7 +447,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_f32_tc_kernel(GramF32Args a)
   __syncthreads();
   fence_after();
   __syncwarp();
-  if (warp == kMmaWarp) tmem_dealloc(tbase, kTmemCols);
+  if (warp == kMmaWarp) tmem_dealloc(tbase, Lay::kTmem);
 }
 
 // G for every tile row i (one block each) and target j (threads): the sum of
@@ -389,7 +471,10 @@ __global__ void gram_f32_finish_kernel(GramF32Args a, int ctas) {
 }
 
 cudaError_t launch_one(const GramF32Args& a, int ctas, cudaStream_t st) {
-  gram_f32_tc_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
+  if (((a.k + 15) / 16) * 16 <= kStkMaxT)
+    gram_f32_tc_kernel<true><<<ctas, kThreads, F32Layout<true>::kBytes, st>>>(a);
+  else
+    gram_f32_tc_kernel<false><<<ctas, kThreads, F32Layout<false>::kBytes, st>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gram_f32_finish_kernel<<<a.k + a.nold, 64, 0, st>>>(a, ctas);
@@ -415,7 +500,11 @@ cudaError_t launch_gram_f32_tc(const GramF32Args& base, int c, int k, int num_sm
   if (c < 1 || k < 1 || k > c) return cudaErrorNotSupported;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_f32_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    cudaError_t e = cudaFuncSetAttribute(gram_f32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         F32Layout<false>::kBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gram_f32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               F32Layout<true>::kBytes);
     if (e != cudaSuccess) return e;
     attr = true;
   }

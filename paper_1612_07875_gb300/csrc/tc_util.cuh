@@ -128,6 +128,13 @@ __device__ __forceinline__ void tmem_ld8_nowait(unsigned taddr, unsigned (&r)[8]
                : "r"(taddr));
 }
 
+// zeros into 8 consecutive tensor-memory columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_st8_zero(unsigned taddr) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1};\n" ::"r"(taddr), "r"(0u)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
 __device__ __forceinline__ void tmem_alloc(unsigned dst_smem, unsigned cols) {
   asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(dst_smem), "r"(cols)
                : "memory");

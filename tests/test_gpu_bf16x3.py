@@ -107,7 +107,7 @@ def test_push_batch_bf16x3_within_bound(cuda_device, n, m, pre, k):
         S.sdmd_destroy(h)
 
 
-@pytest.mark.parametrize("n,m,data", [(70001, 40, "normal"), ((1 << 18) + 1, 100, "offset")])
+@pytest.mark.parametrize("n,m,data", [(70001, 40, "normal"), ((1 << 18) + 1, 100, "offset"), (70001, 16, "normal")])
 def test_rebuild_two_term_split_within_its_bound(cuda_device, n, m, data):
     # two bf16 terms, three products: dropped b1 c1 and remainders about
     # 2^-16 |x y| per product; bound used: 3e-5 sum_p |x_ip x_jp|
