@@ -272,9 +272,11 @@ SDMD_API int sdmd_gram(sdmd_t h, void *G, void *stream);
  * phi must be device memory (SDMD_ERR_ARG otherwise); lambda and r_out may
  * be device or host memory. Complex handles (SDMD_C64, SDMD_C64_SPARSE):
  * the same small algebra with complex V (FP64 Jacobi for the Hermitian G_X,
- * A~ = vsi^H G_XY vsi), lambda / sigma / amplitudes as above; phi must be
- * NULL (SDMD_ERR_UNSUPPORTED otherwise) -- Fourier-sparse handles form their
- * modes in coefficient space with sdmd_fourier_modes. Needs c >= 3
+ * A~ = vsi^H G_XY vsi), lambda / sigma / amplitudes as above; dense complex
+ * handles form Phi = X' M with complex X' (CUDA cores, FP32 complex
+ * products); Fourier-sparse handles take phi = NULL (SDMD_ERR_UNSUPPORTED
+ * otherwise) and form their modes in coefficient space with
+ * sdmd_fourier_modes. Needs c >= 3
  * snapshots (else SDMD_ERR_NOT_READY). The eigensolvers have iteration caps; if one is
  * reached the call still completes and sdmd_status reports SDMD_ERR_RANK.
  */

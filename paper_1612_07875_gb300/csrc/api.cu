@@ -1097,8 +1097,8 @@ int sdmd_set_newest_row(sdmd_t h, const void* row, void* stream) {
 int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, void* stream) {
   if (!h) return fail(SDMD_ERR_ARG, "sdmd_modes: NULL handle");
   const bool cplx = (h->dtype == SDMD_C64 || h->dtype == SDMD_C64_SPARSE);
-  if (cplx && phi)
-    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes: complex handles return no dense Phi (Fourier-sparse handles: "
+  if (h->dtype == SDMD_C64_SPARSE && phi)
+    return fail(SDMD_ERR_UNSUPPORTED, "sdmd_modes: Fourier-sparse handles return no dense Phi (use "
                                       "sdmd_fourier_modes after this call)");
   const int c = resident(h);
   if (c < 3) return fail(SDMD_ERR_NOT_READY, "sdmd_modes: %d snapshots resident, need >= 3", c);

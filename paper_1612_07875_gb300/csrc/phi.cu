@@ -13,7 +13,8 @@
 //
 // The same kernel with a real p x r matrix and real output, reading X
 // (columns 0..c-2) instead of X', gives the POD modes U = X V Sigma^-1
-// (Sec. 2.1, Eq. 4) for sdmd_pod_modes.
+// (Sec. 2.1, Eq. 4) for sdmd_pod_modes. Complex64 windows (dense complex
+// handles) take the complex product X' M (four FMAs per position and mode).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,17 +25,23 @@ namespace sdmd {
 namespace {
 
 constexpr int kPhiThreads = 256;
-constexpr int kSlots = 32;          // slots per staged chunk
 
 template <typename T>
 struct PhiTraits;
 template <>
 struct PhiTraits<uint8_t> {
   static constexpr int kPos = 512;  // positions per tile (2 per thread)
+  static constexpr int kSlots = 32; // slots per staged chunk
 };
 template <>
 struct PhiTraits<float> {
   static constexpr int kPos = 256;  // positions per tile (1 per thread)
+  static constexpr int kSlots = 32;
+};
+template <>
+struct PhiTraits<float2> {          // complex64 (re, im)
+  static constexpr int kPos = 256;
+  static constexpr int kSlots = 16; // 2 x 16 x 2 KB staged: two CTAs per SM
 };
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -65,6 +72,7 @@ __global__ void __launch_bounds__(kPhiThreads, 2) phi_tile_kernel(PhiArgs a) {
   constexpr int kPer = kPos / kPhiThreads;               // positions per thread
   constexpr int kRowBytes = kPos * (int)sizeof(T);
   constexpr int kW = kReal ? KT : 2 * KT;                // sums per position
+  constexpr int kSlots = PhiTraits<T>::kSlots;
   extern __shared__ __align__(16) uint8_t smem[];
   uint8_t* buf0 = smem;
   uint8_t* buf1 = smem + kSlots * kRowBytes;
@@ -104,6 +112,19 @@ __global__ void __launch_bounds__(kPhiThreads, 2) phi_tile_kernel(PhiArgs a) {
       }
       __syncthreads();
       for (int s = 0; s < ns; ++s) {
+        if constexpr (sizeof(T) == 8) {   // complex64: phi += x m, 4 FMAs per mode
+          const float2 xc = *reinterpret_cast<const float2*>(cur + s * kRowBytes + 8 * threadIdx.x);
+          const float4* mrow = reinterpret_cast<const float4*>(Ms + (a0 + s) * kW);
+#pragma unroll
+          for (int q2 = 0; q2 < KT / 2; ++q2) {
+            const float4 mv = mrow[q2];            // modes 2 q2 and 2 q2 + 1: (re, im, re, im)
+            acc[0][4 * q2 + 0] = fmaf(-xc.y, mv.y, fmaf(xc.x, mv.x, acc[0][4 * q2 + 0]));
+            acc[0][4 * q2 + 1] = fmaf(xc.y, mv.x, fmaf(xc.x, mv.y, acc[0][4 * q2 + 1]));
+            acc[0][4 * q2 + 2] = fmaf(-xc.y, mv.w, fmaf(xc.x, mv.z, acc[0][4 * q2 + 2]));
+            acc[0][4 * q2 + 3] = fmaf(xc.y, mv.z, fmaf(xc.x, mv.w, acc[0][4 * q2 + 3]));
+          }
+          continue;
+        }
         float x[kPer];
         if constexpr (sizeof(T) == 1) {
           const unsigned short v = *reinterpret_cast<const unsigned short*>(cur + s * kRowBytes + 2 * threadIdx.x);
@@ -164,6 +185,7 @@ __global__ void __launch_bounds__(kPhiThreads, 2) phi_tile_kernel(PhiArgs a) {
 template <typename T, int KT, bool kReal>
 cudaError_t launch_t(const PhiArgs& a, cudaStream_t st, int sms) {
   constexpr int kPos = PhiTraits<T>::kPos;
+  constexpr int kSlots = PhiTraits<T>::kSlots;
   const size_t smem = 2 * kSlots * kPos * sizeof(T) + (size_t)a.p * (kReal ? KT : 2 * KT) * sizeof(float);
   static size_t attr = 0;
   if (smem > attr) {
@@ -225,6 +247,7 @@ cudaError_t launch_phi(const PhiArgs& a, cudaStream_t st) {
     return launch_for_type<float, true>(a, st, sms > 0 ? sms : 1);
   }
   if (a.dtype == SDMD_U8) return launch_for_type<uint8_t, false>(a, st, sms > 0 ? sms : 1);
+  if (a.dtype == SDMD_C64) return launch_for_type<float2, false>(a, st, sms > 0 ? sms : 1);
   return launch_for_type<float, false>(a, st, sms > 0 ? sms : 1);
 }
 

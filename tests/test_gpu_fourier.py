@@ -18,7 +18,7 @@ import oracle
 from paper_1612_07875_gb300 import sdmd as S
 from paper_1612_07875_gb300 import synth
 
-from helpers import match_eigs
+from helpers import match_eigs, normalize_cols, rel_fro
 
 pytestmark = pytest.mark.gpu
 
@@ -128,8 +128,17 @@ def test_dense_complex_window_equals_its_coefficients(cuda_device):
             v, w = Vc[q], ref.V[:, q]
             ph = np.vdot(v, w) / abs(np.vdot(v, w))
             assert np.linalg.norm(v * ph - w) <= 1e-5, q
-        with pytest.raises(S.SdmdError) as ei:                    # no dense complex Phi
-            S.sdmd_modes(hd, r, torch.empty(r, fs.N, 2, device=cuda_device), None)
+        # dense complex Phi = X' M of the physical window against the oracle's
+        phi = torch.zeros(r, fs.N, 2, dtype=torch.float32, device=cuda_device)
+        lam = np.zeros(2 * r)
+        S.sdmd_modes(hd, r, phi, lam)
+        torch.cuda.synchronize()
+        P = phi.cpu().numpy()
+        got = (P[..., 0] + 1j * P[..., 1]).T[:, :kd]
+        err, perm = match_eigs((lam[0::2] + 1j * lam[1::2])[:kd], ref.lam)
+        assert rel_fro(normalize_cols(got), normalize_cols(ref.Phi[:, perm])) <= 1e-4
+        with pytest.raises(S.SdmdError) as ei:                    # Fourier-sparse: no dense Phi
+            S.sdmd_modes(hs, r, torch.empty(r, fs.N, 2, device=cuda_device), None)
         assert ei.value.code == S.SDMD_ERR_UNSUPPORTED
         assert S.sdmd_status(hd) == S.SDMD_OK and S.sdmd_status(hs) == S.SDMD_OK
     finally:
@@ -163,3 +172,52 @@ def test_fourier_modes_error_paths(cuda_device):
     finally:
         S.sdmd_destroy(h)
         S.sdmd_destroy(hd)
+
+
+@pytest.mark.parametrize("n,m,r", [(40000 + 37, 20, 7), (3 * 65536 + 5, 40, 18)])
+def test_dense_complex_phi_matches_oracle(cuda_device, n, m, r):
+    # complex64 windows of planted rotating modes plus noise: Phi = X' M on
+    # the CUDA cores (several position tiles, a ragged tail, one or two mode
+    # passes) against the oracle's DMD from the same Gram and its product
+    # X' M; columns compared after normalisation (unit norm, phase of the
+    # largest entry)
+    rng = np.random.default_rng(n + m)
+    k = 5
+    F = rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))
+    lam_p = 0.98 * np.exp(1j * rng.uniform(-np.pi, np.pi, k))
+    c0 = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+    T = m + 3
+    frames = [(F @ (c0 * lam_p ** t) + 1e-3 * (rng.standard_normal(n) + 1j * rng.standard_normal(n)))
+              .astype(np.complex64) for t in range(T)]
+    h = S.sdmd_create(n, m, S.SDMD_C64)
+    try:
+        for x in frames:
+            S.sdmd_push(h, torch.from_numpy(x.view(np.float32)).to(cuda_device))
+        phi = torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device)
+        lam = np.zeros(2 * r)
+        rk = np.zeros(1, dtype=np.int32)
+        S.sdmd_modes(h, r, phi, lam, rk)
+        torch.cuda.synchronize()
+        # the oracle's algebra on the device's own Gram (same-input parity: the
+        # FP32-product Gram's rounding is not Phi's), Phi = X' M by the oracle
+        G = np.zeros((m, m, 2))
+        S.sdmd_gram(h, G)
+        Gc = G[..., 0] + 1j * G[..., 1]
+        ref = oracle.dmd_from_gram(Gc[:-1, :-1], Gc[:-1, 1:], r)
+        kept = int(rk[0])
+        assert kept == ref.r
+        lg = (lam[0::2] + 1j * lam[1::2])[:kept]
+        err, perm = match_eigs(lg, ref.lam)
+        assert err <= 1e-6                       # the eigenvalue tolerance (FP32 Schur + FP64 refinement)
+        Xp = np.stack(frames[-(m - 1):], axis=1).astype(np.complex128)
+        Pref = Xp @ ref.M[:, perm]
+        P = phi.cpu().numpy()
+        got = (P[..., 0] + 1j * P[..., 1]).T
+        # the planted modes are well separated from the noise ones: their columns
+        big = [q for q in range(kept) if abs(lg[q]) > 0.9]
+        assert len(big) >= k - 1
+        assert rel_fro(normalize_cols(got[:, big]), normalize_cols(Pref[:, big])) <= 1e-4
+        assert np.all(got[:, kept:] == 0)
+        assert S.sdmd_status(h) == S.SDMD_OK
+    finally:
+        S.sdmd_destroy(h)
