@@ -153,9 +153,10 @@ SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const v
  * sdmd_rebuild -- recompute the whole Gram of the resident window from the
  * ring buffer (Algorithm 1's first-step branch, G = X^T X; Sec. 2.1 Eq. 3),
  * e.g. to resynchronise G after the ring was modified outside the library.
- * uint8 windows of at most 127 snapshots (with SDMD_OPT_REBUILD_TENSOR, the
- * default): one pass over the window on the tensor cores, exact int64, so
- * equal to the streamed G. FP32 windows with SDMD_OPT_F32_BF16X3 = 1: the
+ * uint8 windows (with SDMD_OPT_REBUILD_TENSOR, the default): on the tensor
+ * cores, exact int64, so equal to the streamed G -- one pass over the window
+ * up to 127 snapshots; larger windows in groups of 64 target snapshots, each
+ * paired with the older ones in blocks of up to 127 - 64 rows. FP32 windows with SDMD_OPT_F32_BF16X3 = 1: the
  * tensor cores in BF16x3 split precision, one pass per block of 64 target
  * columns (|G_ij - <x_i, x_j>| <= 1e-6 sum_p |x_ip x_jp|). Otherwise one
  * Gram-row pass per resident snapshot, in time order, so every entry is
@@ -169,9 +170,10 @@ SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
  * multi-column catch-up of a stream that fell behind. Snapshot j is at
  * X + j * ld elements (ld >= n), host or device memory; each must stay valid
  * until the stream reaches the call. The resulting G equals that of k
- * sdmd_push calls. uint8 windows of at most 127 snapshots (with
- * SDMD_OPT_REBUILD_TENSOR): the k new rows and columns of G in one pass over
- * the window on the tensor cores (exact int64) instead of k passes; FP32
+ * sdmd_push calls. uint8 windows (with SDMD_OPT_REBUILD_TENSOR): the k new
+ * rows and columns of G on the tensor cores (exact int64; one pass over a
+ * window of up to 127 snapshots, else per group of 64 new snapshots about
+ * one pass per 127 - (group size) older ones) instead of k passes; FP32
  * windows with SDMD_OPT_F32_BF16X3 = 1 and k >= 2: the k new rows and columns
  * in BF16x3 on the tensor cores, one pass over the window per 64 new
  * snapshots (equal to k pushes within the BF16x3 bound given at
@@ -423,11 +425,11 @@ enum {
                                identical); 0: CUDA-core FP32 kernel */
     ,
     SDMD_OPT_REBUILD_TENSOR = 2 /* 1 (default): sdmd_rebuild and sdmd_push_batch
-                                   of uint8 windows of at most 127 snapshots
-                                   in one pass on the tensor cores (centred
-                                   fp16 pixels, exact int64 G); 0: one
-                                   Gram-row pass per snapshot (bit-identical
-                                   to streaming for every dtype) */
+                                   of uint8 windows on the tensor cores
+                                   (centred fp16 pixels, exact int64 G); 0:
+                                   one Gram-row pass per snapshot
+                                   (bit-identical to streaming for every
+                                   dtype) */
     ,
     SDMD_OPT_F32_BF16X3 = 3 /* 0 (default): FP32 windows keep FP32 products
                                with FP64 sums everywhere; 1: sdmd_rebuild and

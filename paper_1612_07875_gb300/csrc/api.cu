@@ -724,7 +724,7 @@ int sdmd_push_batch(sdmd_t h, int32_t k, const void* X, int64_t ld, void* stream
   const int c_after = (int)(h->count + k < h->m ? h->count + k : h->m);
   const size_t elem_bytes = (size_t)h->elem;
   const uint8_t* src = static_cast<const uint8_t*>(X);
-  const bool u8_tc = h->dtype == SDMD_U8 && h->rebuild_tensor && c_after <= 127;
+  const bool u8_tc = h->dtype == SDMD_U8 && h->rebuild_tensor;
   const bool f32_tc = h->dtype == SDMD_F32 && h->f32_bf16x3 && k >= 2;
   if (!u8_tc && !f32_tc) {
     // k ordinary pushes (one Gram-row pass each)
@@ -900,7 +900,7 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   const int c = resident(h);
   const int first = oldest_slot(h);
   if (h->dtype == SDMD_F32 && h->f32_bf16x3 && c >= 1) return gram_f32_tensor(h, c, c, st);
-  if (h->dtype == SDMD_U8 && h->rebuild_tensor && c >= 1 && c <= 127) {
+  if (h->dtype == SDMD_U8 && h->rebuild_tensor && c >= 1) {
     // one pass over the window on the tensor cores, exact int64
     const int rc0 = ensure_gram_full_scratch(h);
     if (rc0 != SDMD_OK) return rc0;

@@ -11,14 +11,18 @@
 // same MMAs give the column sums s_i = sum_k x'_ik and the count n, and
 //   G_ij = G'_ij + 128 (s_i + s_j) + 128^2 n        (exact int64).
 //
-// GEMM. The c snapshots (c <= 127) plus the ones row are the rows of one
-// K-major fp16 tile T (128 rows x 256 positions, zero rows beyond c + 1):
-// first the k target snapshots (the k newest; k = c for a full rebuild), then
-// the ones row, then the older ones. D[128 x N] += T T_B^T, where T_B is the
-// first N = k + 1 (rounded up to 16) rows of the same tile, so A and B share
-// one shared-memory descriptor and D holds every <x_i, x_j> with x_j a target
-// (the k new rows and columns of G: a multi-column catch-up reads the window
-// once for all k). Core matrix (rg, kg) = rows 8 rg .. 8 rg + 7
+// GEMM. One launch: the rows of one K-major fp16 tile T (128 rows x 256
+// positions, zero rows past the used ones) are a group of k <= 64 target
+// snapshots, the ones row, then a block of older snapshots. D[128 x N] +=
+// T T_B^T, where T_B is the first N = k + 1 (rounded up to 16) rows of the
+// same tile, so A and B share one shared-memory descriptor and D holds every
+// <x_i, x_j> with x_j a target. The host call covers the k newest snapshots
+// of a window of c (k = c: a full rebuild) with groups of at most 64 targets,
+// newest first, each paired with every older snapshot in blocks of
+// 127 - (group size) rows (a group with nothing older: one launch of its
+// own); a window of at most 127 snapshots is one launch whatever k. Pairs
+// inside a group are recomputed by each of its launches, with the same
+// (exact) result. Core matrix (rg, kg) = rows 8 rg .. 8 rg + 7
 // x positions 8 kg .. 8 kg + 7 at (kg * 16 + rg) * 128 bytes: LBO 2048 B
 // between K neighbours, SBO 128 B between row groups.
 //
@@ -118,8 +122,8 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
   FullShared& sh = *reinterpret_cast<FullShared*>(smem + kTiles * kTileBytes + kStages * kStageBytes);
   volatile int* stop = &sh.stop;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c = a.c;                     // snapshots (tile rows 0 .. c except the ones row)
   const int kt = a.k;                    // targets: tile rows 0 .. kt - 1; row kt is the ones row
+  const int c = kt + a.nold;             // last tile row in use (the older block ends there)
   const int npad = ((kt + 1 + 15) / 16) * 16;
   const int64_t nchunks = (a.n + (int64_t)kKst * kStepsPerChunk - 1) / ((int64_t)kKst * kStepsPerChunk);
 
@@ -140,7 +144,7 @@ __global__ void __launch_bounds__(kThreads, 1) gram_full_tc_kernel(GramFullArgs 
   if (warp == kMmaWarp) tmem_alloc(smem_u32(&sh.tmem_base), kTmemCols);
   for (int r = tid; r <= c; r += kThreads) {
     if (r == kt) continue;
-    const int t = (r < kt) ? c - kt + r : r - kt - 1;      // window time index of tile row r
+    const int t = (r < kt) ? a.t_tgt + r : a.t_old + (r - kt - 1);   // window time index of tile row r
     sh.tab[r] = (int64_t)((a.start + t) % a.m) * a.slot_bytes;
   }
   // rows beyond the ones row stay zero in both tiles
@@ -416,7 +420,7 @@ __global__ void reset_sched_kernel(unsigned* sched) { sched[0] = 0u; }   // read
 
 __global__ void gram_full_finish_kernel(GramFullArgs a, int ctas) {
   __shared__ long long si_n[2];
-  const int i = blockIdx.x, c = a.c, kt = a.k;
+  const int i = blockIdx.x, kt = a.k;
   if (i == kt) return;                   // the ones row
   if (threadIdx.x < 2) {                 // s_i = G'_i,kt and n = G'_kt,kt
     const int rw = (threadIdx.x == 0) ? i : kt;
@@ -426,7 +430,7 @@ __global__ void gram_full_finish_kernel(GramFullArgs a, int ctas) {
   }
   __syncthreads();
   const long long si = si_n[0], n = si_n[1];
-  const int ti = (i < kt) ? c - kt + i : i - kt - 1;
+  const int ti = (i < kt) ? a.t_tgt + i : a.t_old + (i - kt - 1);
   const int pi = (a.start + ti) % a.m;
   for (int j = threadIdx.x; j < kt; j += blockDim.x) {
     long long g = 0, sj = 0;
@@ -436,17 +440,17 @@ __global__ void gram_full_finish_kernel(GramFullArgs a, int ctas) {
       sj += P[(int64_t)j * kRowsM + kt];
     }
     const long long v = g + 128LL * (si + sj) + 16384LL * n;
-    const int pj = (a.start + c - kt + j) % a.m;
+    const int pj = (a.start + a.t_tgt + j) % a.m;
     a.G[(int64_t)pi * a.m + pj] = v;
     a.G[(int64_t)pj * a.m + pi] = v;
   }
-  (void)c;
 }
 
 }  // namespace
 
-cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream_t st) {
-  if (a.c < 1 || a.c > kRowsM - 1 || a.k < 1 || a.k > a.c) return cudaErrorNotSupported;
+cudaError_t launch_gram_full_tc(const GramFullArgs& base, int* ctas_out, cudaStream_t st) {
+  const int c = base.c, k = base.k;
+  if (c < 1 || c > SDMD_MAX_M || k < 1 || k > c) return cudaErrorNotSupported;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(gram_full_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
@@ -458,15 +462,37 @@ cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (sms < 1) sms = 1;
   const int ctas = sms < kGramFullMaxCtas ? sms : kGramFullMaxCtas;
-  gram_full_tc_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  gram_full_finish_kernel<<<a.c + 1, 128, 0, st>>>(a, ctas);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  reset_sched_kernel<<<1, 1, 0, st>>>(a.sched);
+  // targets = window time indices c - k .. c - 1 in groups of at most 64,
+  // newest first; each group against the older snapshots 0 .. lo - 1 in
+  // blocks of 127 - kg rows. A window of at most 127 fits one tile: one
+  // launch whatever k.
+  const int gmax = (c + 1 <= kRowsM) ? k : kGramFullMaxTargets;
+  for (int hi = c; hi > c - k;) {
+    const int lo = (hi - gmax > c - k) ? hi - gmax : c - k;
+    const int kg = hi - lo;
+    const int blk = kRowsM - 1 - kg;
+    int o = 0;
+    do {
+      GramFullArgs a = base;
+      a.t_tgt = lo;
+      a.k = kg;
+      a.t_old = o;
+      a.nold = (lo - o < blk) ? lo - o : blk;
+      gram_full_tc_kernel<<<ctas, kThreads, kSmemBytes, st>>>(a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      gram_full_finish_kernel<<<a.k + 1 + a.nold, 128, 0, st>>>(a, ctas);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      reset_sched_kernel<<<1, 1, 0, st>>>(a.sched);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      o += a.nold;
+    } while (o < lo);
+    hi = lo;
+  }
   if (ctas_out) *ctas_out = ctas;
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace sdmd

@@ -39,7 +39,9 @@ struct GramRowArgs {
 };
 
 // Gram rows/columns of the k newest uint8 snapshots against the window
-// (k = c: the full Gram) on the tensor cores, exact (c <= 127).
+// (k = c: the full Gram) on the tensor cores, exact. The host call splits
+// the targets into groups of at most 64 and pairs each group with blocks of
+// older snapshots; one kernel launch covers one (group, block) pair.
 struct GramFullArgs {
   const uint8_t* ring;
   int64_t slot_bytes;
@@ -52,9 +54,15 @@ struct GramFullArgs {
   unsigned* sched;       // chunk counter, zero between launches
   long long* G;
   int* status;
+  // one launch (set by launch_gram_full_tc): tile rows = targets (window time
+  // indices t_tgt .. t_tgt + k - 1), the ones row, then nold older snapshots
+  // (t_old .. t_old + nold - 1); k + 1 + nold <= 128
+  int32_t t_tgt = 0, t_old = 0, nold = 0;
 };
 constexpr int kGramFullMaxCtas = 160;
-// Launches the two kernels on `st`; cudaErrorNotSupported outside c <= 127.
+constexpr int kGramFullMaxTargets = 64;
+// Launches the kernels of every (target group, older block) pair on `st`;
+// cudaErrorNotSupported outside 1 <= k <= c <= SDMD_MAX_M.
 cudaError_t launch_gram_full_tc(const GramFullArgs& a, int* ctas_out, cudaStream_t st);
 
 // Gram rows/columns of FP32 snapshots on the tensor cores in BF16x3 split

@@ -230,7 +230,9 @@ def test_full_window_rebuild_equals_streamed_gram_bitwise(cuda_device, kind):
     (4096 * 3 + 17, 127, 130, "random"),   # the largest window on the tensor path
     (100003, 100, 40, "extreme"),     # ramp-up (40 of 100), pixels 0 / 255 only
     (1, 3, 5, "random"),              # a single position
-    (5000, 128, 128, "random"),       # beyond the tensor path: row kernels
+    (5000, 128, 128, "random"),       # past one tile: groups of 64 targets with older blocks
+    (70001, 256, 260, "random"),      # the largest window: 4 groups, 10 launches
+    (9000, 200, 230, "extreme"),      # uneven groups (64, 64, 64, 8), pixels 0 / 255 only
 ])
 def test_tensor_core_rebuild_exact(cuda_device, n, m, pushes, pattern):
     # Algorithm 1's first step on the tensor cores (centred fp16 pixels,
@@ -271,8 +273,10 @@ def test_tensor_core_rebuild_exact(cuda_device, n, m, pushes, pattern):
     (4096 * 3 + 17, 100, 120, 8, "u8", False),   # host source
     (100003, 20, 5, 10, "u8", True),        # ramp-up: 5 resident, 10 new
     (5000, 16, 3, 16, "u8", True),          # k = m: every resident snapshot is new
-    (6000, 127, 130, 127, "u8", True),      # the largest window on the tensor path
-    (5000, 128, 130, 3, "u8", True),        # beyond it: k ordinary pushes
+    (6000, 127, 130, 127, "u8", True),      # the largest window in one tile
+    (5000, 128, 130, 3, "u8", True),        # past one tile: 3 targets, older in blocks of 124
+    (70001, 256, 256, 8, "u8", True),       # the largest window, the bench's catch-up size
+    (9000, 200, 150, 100, "u8", False),     # ramp-up into a wrapped window: groups of 64 and 36
     (3001, 12, 15, 5, "f32", True),         # float: k ordinary pushes
 ])
 def test_push_batch_equals_sequential_pushes(cuda_device, n, m, pre, k, dtype, device_src):
