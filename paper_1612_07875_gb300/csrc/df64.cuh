@@ -10,7 +10,7 @@
 //   two_prod(a, b)      = (p, e) with p + e == a * b          (FMA)
 // The compound operations renormalise their result; relative errors are a
 // few units of 2^-48 (division and square root one Newton-type correction
-// each). No operation relies on reassociation, so the code must be built
+// each; the reciprocal one Newton step). No operation relies on reassociation, so the code must be built
 // without fast-math flags (it is: see build.py).
 #pragma once
 
@@ -25,7 +25,7 @@
 
 namespace sdmd {
 
-struct dd {
+struct alignas(8) dd {   // 8-byte aligned: one 64-bit load or store per value
   float hi, lo;
 };
 
@@ -91,6 +91,16 @@ DF_HD dd dd_div(dd a, dd b) {
   const float q3 = r.hi / b.hi;
   const dd q = quick_two_sum(q1, q2);
   return dd_add(q, dd_make(q3));
+}
+
+// 1 / b: the FP32 reciprocal r0 refined by one Newton step r0 + r0 (1 - b r0),
+// with the residual formed exactly (two_prod; 1 - p is exact for p near 1).
+// r0 is correctly rounded, so the step leaves about 2^-47 relative error.
+DF_HD dd dd_recip(dd b) {
+  const float r0 = 1.f / b.hi;
+  const dd pr = two_prod(b.hi, r0);
+  const float res = fmaf(-b.lo, r0, (1.f - pr.hi) - pr.lo);
+  return quick_two_sum(r0, r0 * res);
 }
 
 DF_HD dd dd_sqrt(dd a) {

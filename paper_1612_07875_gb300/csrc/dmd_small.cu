@@ -13,7 +13,8 @@
 //     ring-indexed physical G (p = c-1), converted to df64 and scaled by an
 //     exact power of two so that the largest diagonal entry is in [0.5, 1).
 //  1. Householder tridiagonalisation of G_X in df64: Q^T G_X Q = T (d, e),
-//     reflectors kept in the rows of G_X's storage.
+//     reflectors kept down the columns of G_X's storage, one block barrier
+//     per Householder step (the rank-2 update deferred into the next step).
 //  2. the r largest eigenvalues of T by Sturm-count multisection in FP32
 //     (one warp per eigenvalue, 32 points per round): shifts accurate to
 //     ~eps32 * |T|.
@@ -75,6 +76,8 @@ __device__ __forceinline__ float warp_max_f(float v) {
   return v;
 }
 
+__device__ __forceinline__ dd dd_sel(bool c, dd a, dd b) { return {c ? a.hi : b.hi, c ? a.lo : b.lo}; }
+
 struct CF {
   float re, im;
 };
@@ -100,14 +103,6 @@ __device__ __forceinline__ CF csqrt(CF z) {
   const float im = z.im / (2.f * re);
   if (z.re >= 0.f) return {re, im};
   return {fabsf(im), copysignf(re, z.im)};
-}
-
-// Row of the lower-triangle element with flat index f (row-major, j <= i).
-__device__ __forceinline__ int tri_row(int f) {
-  int i = (int)((sqrtf(8.f * (float)f + 1.f) - 1.f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= f) ++i;
-  while (i * (i + 1) / 2 > f) --i;
-  return i;
 }
 
 struct WS {
@@ -136,93 +131,240 @@ __device__ WS carve(double* base, const ModesLayout& L) {
 // ---------------------------------------------------------------- phase 1 --
 // df64 Householder reduction of the symmetric p x p matrix A (row-major,
 // full storage) to tridiagonal form (d, e). Reflector k is I - 2 v v^T on
-// indices k+1..p-1 with v unit (zero if column k is already reduced), stored
-// over row k, A[k][k+1..p-1]. Scalars are formed by one lane and shared.
-__device__ void tridiagonalize(dd* A, int p, dd* d, dd* e, dd* vs, dd* pv, dd* wv, dd* part, dd* sc) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+// indices k+1..p-1 with v unit (zero if column k is already reduced); it is
+// stored down column k, A[k+1..p-1][k].
+//
+// One block barrier per step. Step k's rank-2 update A -= v w^T + w v^T
+// (w = 2 (A v - (v^T A v) v)) is not applied in step k: step k+1 applies it
+// while it reads the trailing block for its own product A u, so the block is
+// read and written once per step. Warp w owns trailing rows w, w + 8, ...
+// and lane l columns l, l + 32, ...; as the block is symmetric, the row sums
+// of A u are also its column sums, so each lane sums its columns over its
+// warp's rows, and u^T A u comes from the same column sums. After the
+// barrier every warp adds the eight warps' parts for its lanes' columns and
+// forms v, A v and w itself, then the next pivot row, its norm and the
+// reflector's scalars: the same operations in the same order in every warp,
+// so all warps hold the same bits without a second barrier. The block stays
+// exactly symmetric: the update term of (i, j) is formed from the same
+// products, added in an order-free way, as that of (j, i).
+//
+// Workspace tw (8-byte units): part[2][kWarps][P] (per-warp column sums by
+// step parity), u, v, w [kWarps][P] (each warp's copy, indexed by row, of
+// the current reflector's u and of the pending reflector's v and w),
+// dot[2][kWarps] (per-warp parts of u^T A_sub u).
+constexpr int kTriCols = 8;   // columns per lane: p <= 8 * 32
+constexpr int kTriUnitsPerP = 5 * kWarps;
+
+// a*b as an unevaluated (hi, lo) pair whose bits do not depend on the operand order
+__device__ __forceinline__ dd dd_mul_sym(dd a, dd b) {
+  const float ph = a.hi * b.hi;
+  const float pe = fmaf(a.hi, b.hi, -ph);
+  return {ph, pe + __fadd_rn(__fmul_rn(a.hi, b.lo), __fmul_rn(a.lo, b.hi))};   // no fma contraction
+}
+// a - (v_i w_j + w_i v_j); the same bits for (i, j) and (j, i)
+__device__ __forceinline__ dd dd_rank2_sub(dd a, dd vi, dd wi, dd vj, dd wj) {
+  const dd p1 = dd_mul_sym(vi, wj), p2 = dd_mul_sym(wi, vj);
+  const dd s = two_sum(p1.hi, p2.hi);
+  const float c = (p1.lo + p2.lo) + s.lo;
+  const dd r = two_sum(a.hi, -s.hi);
+  return quick_two_sum(r.hi, (a.lo - c) + r.lo);
+}
+// running sum (s, c) += a * b, c collecting the rounding errors (Dot2-style)
+__device__ __forceinline__ void dot2_acc(float& s, float& c, dd a, dd b) {
+  const float ph = a.hi * b.hi;
+  float pe = fmaf(a.hi, b.hi, -ph);
+  pe = fmaf(a.hi, b.lo, pe);
+  pe = fmaf(a.lo, b.hi, pe);
+  const dd t = two_sum(s, ph);
+  s = t.hi;
+  c += t.lo + pe;
+}
+// (hi, lo) pairs added without renormalising the tail (Dot2-style): the
+// exact error of the leading parts is kept, the tails are added in FP32
+__device__ __forceinline__ dd pair_add(dd a, dd b) {
+  const dd t = two_sum(a.hi, b.hi);
+  return {t.hi, (a.lo + b.lo) + t.lo};
+}
+// the eight per-warp parts x[0], x[st], ..., x[7 st] summed as a fixed tree
+__device__ __forceinline__ dd dd_sum8(const dd* x, int64_t st) {
+  const dd a = pair_add(x[0], x[st]), b = pair_add(x[2 * st], x[3 * st]);
+  const dd c = pair_add(x[4 * st], x[5 * st]), f = pair_add(x[6 * st], x[7 * st]);
+  const dd r = pair_add(pair_add(a, b), pair_add(c, f));
+  return quick_two_sum(r.hi, r.lo);
+}
+static_assert(kWarps == 8, "dd_sum8 adds one part per warp");
+
+__device__ void tridiagonalize(dd* A, int p, dd* d, dd* e, dd* tw, int64_t P) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  dd* part = tw;                                            // [2][kWarps][P]
+  dd* uw = tw + (2 * kWarps + warp) * P;                    // this warp's u, v, w by row
+  dd* vw = tw + (3 * kWarps + warp) * P;
+  dd* ww = tw + (4 * kWarps + warp) * P;
+  dd* dotp = tw + (int64_t)kTriUnitsPerP * P;               // [2][kWarps]
+  // pending reflector's v, w at g = k + lane + 32c (from the previous step's combine)
+  dd vr[kTriCols], wr[kTriCols];
+#pragma unroll
+  for (int c = 0; c < kTriCols; ++c) {
+    vr[c] = {0.f, 0.f};
+    wr[c] = {0.f, 0.f};
+  }
   for (int k = 0; k + 2 < p; ++k) {
     const int L = p - k - 1;
-    dd* rowk = A + (int64_t)k * p + (k + 1);
-    if (warp == 0) {
-      dd t = {0.f, 0.f};
-      for (int i = 1 + lane; i < L; i += 32) t = dd_fma(rowk[i], rowk[i], t);
-      t = warp_sum_dd(t);
-      if (lane == 0) {
-        const dd x0 = rowk[0];
-        d[k] = A[(int64_t)k * p + k];
-        if (t.hi == 0.f) {
-          sc[0] = {0.f, 0.f};
-          e[k] = x0;
-        } else {
-          const dd nrm = dd_sqrt(dd_fma(x0, x0, t));
-          const dd alpha = (x0.hi >= 0.f) ? dd_neg(nrm) : nrm;
-          const dd v0 = dd_sub(x0, alpha);                 // same sign as x0: no cancellation
-          sc[0] = dd_div(dd_make(1.f), dd_sqrt(dd_fma(v0, v0, t)));
-          sc[1] = v0;
-          e[k] = alpha;
+    const int par = k & 1;
+    const bool pend = (k > 0);
+    // pivot row k of the updated matrix, x_g for g = k..p-1 (lane g - k + 32c)
+    const dd vk = {__shfl_sync(0xffffffffu, vr[0].hi, 0), __shfl_sync(0xffffffffu, vr[0].lo, 0)};
+    const dd wk = {__shfl_sync(0xffffffffu, wr[0].hi, 0), __shfl_sync(0xffffffffu, wr[0].lo, 0)};
+    float ts = 0.f, tc = 0.f;
+    dd xk[kTriCols];
+#pragma unroll
+    for (int c = 0; c < kTriCols; ++c) {
+      xk[c] = {0.f, 0.f};
+      if (32 * c > L) break;             // warp-uniform: no slot beyond the row
+      const int g = k + lane + 32 * c;
+      dd x = {0.f, 0.f};
+      if (g < p) {
+        x = A[(int64_t)k * p + g];
+        if (pend) x = dd_rank2_sub(x, vk, wk, vr[c], wr[c]);
+        if (g >= k + 2) dot2_acc(ts, tc, x, x);
+      }
+      xk[c] = x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {   // xor butterfly: all lanes end with the same bits
+      const float so = __shfl_xor_sync(0xffffffffu, ts, o), co = __shfl_xor_sync(0xffffffffu, tc, o);
+      const dd q = two_sum(ts, so);
+      ts = q.hi;
+      tc = (tc + co) + q.lo;
+    }
+    const dd t = quick_two_sum(ts, tc);
+    const dd x0 = {__shfl_sync(0xffffffffu, xk[0].hi, 1), __shfl_sync(0xffffffffu, xk[0].lo, 1)};
+    dd inv = {0.f, 0.f}, u0 = x0, ek = x0;
+    if (t.hi != 0.f) {
+      const dd nrm = dd_sqrt(dd_fma(x0, x0, t));
+      const dd alpha = (x0.hi >= 0.f) ? dd_neg(nrm) : nrm;
+      u0 = dd_sub(x0, alpha);                       // same sign as x0: no cancellation
+      inv = dd_recip(dd_sqrt(dd_fma(u0, u0, t)));
+      ek = alpha;
+    }
+    // this warp's copy of u (u_{k+1} = x0 - alpha, u_g = x_g beyond)
+#pragma unroll
+    for (int c = 0; c < kTriCols; ++c) {
+      if (32 * c > L) break;
+      const int g = k + lane + 32 * c;
+      if (g > k && g < p) uw[g] = (g == k + 1) ? u0 : xk[c];
+    }
+    if (warp == 0 && lane == 0) {
+      d[k] = xk[0];
+      e[k] = ek;
+    }
+    __syncwarp();
+    // trailing block rows/cols k+1..p-1: apply the pending update, store, and
+    // sum a_ij u_i down this lane's columns j over this warp's rows i
+    dd vc[kTriCols], wc[kTriCols];
+    float cs[kTriCols], cc[kTriCols];
+#pragma unroll
+    for (int c = 0; c < kTriCols; ++c) {
+      const int gj = k + 1 + lane + 32 * c;
+      vc[c] = {0.f, 0.f};
+      wc[c] = {0.f, 0.f};
+      cs[c] = 0.f;
+      cc[c] = 0.f;
+      if (32 * c >= L) continue;
+      if (pend && gj < p) {
+        vc[c] = vw[gj];
+        wc[c] = ww[gj];
+      }
+    }
+    // four rows per iteration: their loads, updates and sums interleave
+    for (int i0 = warp; i0 < L; i0 += 4 * kWarps) {
+      dd ui[4], vi[4], wi[4];
+      dd* rp[4];
+      bool ok[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + q * kWarps;
+        ok[q] = i < L;
+        const int gi = ok[q] ? k + 1 + i : k + 1;
+        ui[q] = ok[q] ? uw[gi] : dd{0.f, 0.f};
+        vi[q] = (pend && ok[q]) ? vw[gi] : dd{0.f, 0.f};
+        wi[q] = (pend && ok[q]) ? ww[gi] : dd{0.f, 0.f};
+        rp[q] = A + (int64_t)gi * p + (k + 1);
+      }
+#pragma unroll
+      for (int c = 0; c < kTriCols; ++c) {
+        if (32 * c >= L) break;
+        const int j = lane + 32 * c;
+        if (j < L) {
+          dd av[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) av[q] = ok[q] ? rp[q][j] : dd{0.f, 0.f};
+          if (pend) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[q] = dd_rank2_sub(av[q], vi[q], wi[q], vc[c], wc[c]);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              if (ok[q]) rp[q][j] = av[q];
+          }
+#pragma unroll
+          for (int q = 0; q < 4; ++q)   // rows past L add zero products
+            dot2_acc(cs[c], cc[c], av[q], ui[q]);
         }
       }
     }
-    __syncthreads();
-    const dd inv = sc[0];
-    if (inv.hi == 0.f) {
-      for (int i = tid; i < L; i += kThreads) rowk[i] = {0.f, 0.f};
-      __syncthreads();
-      continue;
-    }
-    const dd v0 = sc[1];
-    for (int i = tid; i < L; i += kThreads) vs[i] = dd_mul(i == 0 ? v0 : rowk[i], inv);
-    __syncthreads();
-    // pv = A_sub v, each row split into np parts (np * L <= kThreads)
-    dd* As = A + (int64_t)(k + 1) * p + (k + 1);
-    int np = kThreads / L;
-    np = np >= 8 ? 8 : (np >= 4 ? 4 : (np >= 2 ? 2 : 1));
-    const int seg = (L + np - 1) / np;
-    for (int idx = tid; idx < L * np; idx += kThreads) {
-      const int q = idx / L, i = idx - q * L;
-      const int j0 = q * seg, j1 = min(L, j0 + seg);
-      dd s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
-      int j = j0;
-      for (; j + 1 < j1; j += 2) {
-        s0 = dd_fma(As[(int64_t)j * p + i], vs[j], s0);
-        s1 = dd_fma(As[(int64_t)(j + 1) * p + i], vs[j + 1], s1);
+    // column parts, and this warp's part of u^T A_sub u
+    dd* pp = part + (int64_t)par * kWarps * P;
+    float us = 0.f, uc = 0.f;
+#pragma unroll
+    for (int c = 0; c < kTriCols; ++c) {
+      if (32 * c >= L) break;
+      const int gj = k + 1 + lane + 32 * c;
+      if (gj < p) {
+        const dd T = quick_two_sum(cs[c], cc[c]);
+        pp[(int64_t)warp * P + gj] = T;
+        dot2_acc(us, uc, uw[gj], T);
       }
-      if (j < j1) s0 = dd_fma(As[(int64_t)j * p + i], vs[j], s0);
-      part[q * L + i] = dd_add(s0, s1);
     }
-    for (int i = tid; i < L; i += kThreads) rowk[i] = vs[i];
-    __syncthreads();
-    for (int i = tid; i < L; i += kThreads) {
-      dd s = part[i];
-      for (int q = 1; q < np; ++q) s = dd_add(s, part[q * L + i]);
-      pv[i] = s;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float so = __shfl_xor_sync(0xffffffffu, us, o), co = __shfl_xor_sync(0xffffffffu, uc, o);
+      const dd q = two_sum(us, so);
+      us = q.hi;
+      uc = (uc + co) + q.lo;
     }
+    if (lane == 0) dotp[par * kWarps + warp] = quick_two_sum(us, uc);
     __syncthreads();
-    if (warp == 0) {
-      dd t = {0.f, 0.f};
-      for (int i = lane; i < L; i += 32) t = dd_fma(vs[i], pv[i], t);
-      t = warp_sum_dd(t);
-      if (lane == 0) sc[2] = t;
+    // every warp: A_sub u for its lanes' rows, v = u inv, pv = A_sub v,
+    // K = v^T pv = inv^2 u^T A_sub u, w = 2 (pv - K v); reflector k down column k
+    const dd kv = dd_mul(dd_mul(dd_sum8(dotp + par * kWarps, 1), inv), inv);
+#pragma unroll
+    for (int c = 0; c < kTriCols; ++c) {
+      if (32 * c >= L) break;
+      const int g = k + 1 + lane + 32 * c;
+      if (g < p) {
+        const dd pvg = dd_mul(dd_sum8(pp + g, P), inv);
+        const dd vg = dd_mul(uw[g], inv);
+        const dd wg = dd_scale(dd_sub(pvg, dd_mul(kv, vg)), 2.f);
+        vw[g] = vg;
+        ww[g] = wg;
+        vr[c] = vg;
+        wr[c] = wg;
+        if (warp == 0) A[(int64_t)g * p + k] = vg;
+      }
     }
-    __syncthreads();
-    const dd kv = sc[2];
-    for (int i = tid; i < L; i += kThreads) wv[i] = dd_scale(dd_sub(pv[i], dd_mul(kv, vs[i])), 2.f);
-    __syncthreads();
-    // A_sub -= v w^T + w v^T on the lower triangle (flat index), mirrored
-    const int ne = L * (L + 1) / 2;
-    for (int f = tid; f < ne; f += kThreads) {
-      const int i = tri_row(f), j = f - i * (i + 1) / 2;
-      const dd val = dd_sub(dd_sub(As[(int64_t)i * p + j], dd_mul(vs[i], wv[j])), dd_mul(wv[i], vs[j]));
-      As[(int64_t)i * p + j] = val;
-      As[(int64_t)j * p + i] = val;
-    }
-    __syncthreads();
+    __syncwarp();
   }
-  if (tid == 0) {
-    if (p >= 2) {
-      d[p - 2] = A[(int64_t)(p - 2) * p + (p - 2)];
-      d[p - 1] = A[(int64_t)(p - 1) * p + (p - 1)];
-      e[p - 2] = A[(int64_t)(p - 2) * p + (p - 1)];
+  if (threadIdx.x == 0) {
+    if (p >= 3) {   // the last reflector's update of the final 2 x 2 block
+      const int k = p - 2;
+      const dd v0 = vw[k], v1 = vw[k + 1], w0 = ww[k], w1 = ww[k + 1];
+      d[k] = dd_rank2_sub(A[(int64_t)k * p + k], v0, w0, v0, w0);
+      d[k + 1] = dd_rank2_sub(A[(int64_t)(k + 1) * p + k + 1], v1, w1, v1, w1);
+      e[k] = dd_rank2_sub(A[(int64_t)k * p + k + 1], v0, w0, v1, w1);
+    } else if (p == 2) {
+      d[0] = A[0];
+      d[1] = A[3];
+      e[0] = A[1];
     } else {
       d[0] = A[0];
     }
@@ -231,13 +373,15 @@ __device__ void tridiagonalize(dd* A, int p, dd* d, dd* e, dd* vs, dd* pv, dd* w
 }
 
 // ---------------------------------------------------------------- phase 2 --
-// Number of eigenvalues of the FP32 tridiagonal (d, e^2) below x.
+// Number of eigenvalues of the FP32 tridiagonal (d, e^2) below x. The
+// divisions use the fast reciprocal (about 2 ulp): the counts only place
+// FP32 shifts, which the df64 inverse iteration refines.
 __device__ int sturm32(const float* d, const float* e2, int p, float x, float pivmin) {
   float q = d[0] - x;
   if (fabsf(q) < pivmin) q = -pivmin;
   int cnt = (q < 0.f);
   for (int i = 1; i < p; ++i) {
-    q = (d[i] - x) - e2[i - 1] / q;
+    q = (d[i] - x) - __fdividef(e2[i - 1], q);   // |q| >= pivmin keeps e2 / q below 2^126
     if (fabsf(q) < pivmin) q = -pivmin;
     cnt += (q < 0.f);
   }
@@ -248,60 +392,56 @@ __device__ int sturm32(const float* d, const float* e2, int p, float x, float pi
 // LU with partial pivoting of the df64 tridiagonal T - mu I. Row i of U has
 // (1/u0, u1, u2) on columns (i, i+1, i+2) (diagonal stored as reciprocal);
 // mult / piv (0 or 1) describe L. Pivots below `tiny` are raised to it.
+// Branch-free (selects), so the lanes of a warp that factor different shifts
+// never diverge.
 __device__ void tri_lu_dd(const dd* d, const dd* e, int p, dd mu, float tiny, dd* u0, dd* u1, dd* u2,
                           dd* mult, dd* piv) {
-  dd cd = dd_sub(d[0], mu), c1 = (p > 1) ? e[0] : dd{0.f, 0.f}, c2 = {0.f, 0.f};
+  dd cd = dd_sub(d[0], mu), c1 = (p > 1) ? e[0] : dd{0.f, 0.f};
   for (int i = 0; i + 1 < p; ++i) {
     const dd sub = e[i];
     const dd nd = dd_sub(d[i + 1], mu);
     const dd n1 = (i + 2 < p) ? e[i + 1] : dd{0.f, 0.f};
-    dd piv_val;
-    if (fabsf(cd.hi) >= fabsf(sub.hi)) {
-      const dd m = (cd.hi != 0.f) ? dd_div(sub, cd) : dd{0.f, 0.f};
-      piv_val = cd;
-      u1[i] = c1;
-      u2[i] = c2;
-      piv[i] = {0.f, 0.f};
-      mult[i] = m;
-      cd = dd_sub(nd, dd_mul(m, c1));
-      c1 = dd_sub(n1, dd_mul(m, c2));
-      c2 = {0.f, 0.f};
-    } else {
-      const dd m = dd_div(cd, sub);
-      piv_val = sub;
-      u1[i] = nd;
-      u2[i] = n1;
-      piv[i] = {1.f, 0.f};
-      mult[i] = m;
-      cd = dd_sub(c1, dd_mul(m, nd));
-      c1 = dd_sub(c2, dd_mul(m, n1));
-      c2 = {0.f, 0.f};
-    }
-    if (fabsf(piv_val.hi) < tiny) piv_val = {copysignf(tiny, piv_val.hi), 0.f};
-    u0[i] = dd_div(dd_make(1.f), piv_val);
+    const bool sw = fabsf(cd.hi) < fabsf(sub.hi);   // row i+1 becomes the pivot row
+    dd pv = dd_sel(sw, sub, cd);
+    const dd num = dd_sel(sw, cd, sub);
+    if (fabsf(pv.hi) < tiny) pv = {copysignf(tiny, pv.hi), 0.f};
+    const dd rp = dd_recip(pv);
+    const dd m = (pv.hi != 0.f) ? dd_mul(num, rp) : dd{0.f, 0.f};
+    u0[i] = rp;
+    u1[i] = dd_sel(sw, nd, c1);
+    u2[i] = dd_sel(sw, n1, dd{0.f, 0.f});
+    piv[i] = {sw ? 1.f : 0.f, 0.f};
+    mult[i] = m;
+    // no swap: row i+1 - m row i = (nd - m c1, n1); swap: row i - m row i+1 = (c1 - m nd, -m n1)
+    cd = dd_sub(dd_sel(sw, c1, nd), dd_mul(m, dd_sel(sw, nd, c1)));
+    c1 = sw ? dd_neg(dd_mul(m, n1)) : n1;
   }
-  const dd last = (fabsf(cd.hi) < tiny) ? dd{copysignf(tiny, cd.hi), 0.f} : cd;
-  u0[p - 1] = dd_div(dd_make(1.f), last);
+  dd last = cd;
+  if (fabsf(last.hi) < tiny) last = {copysignf(tiny, last.hi), 0.f};
+  u0[p - 1] = dd_recip(last);
   u1[p - 1] = {0.f, 0.f};
   u2[p - 1] = {0.f, 0.f};
 }
 
 __device__ void tri_solve_dd(int p, const dd* u0inv, const dd* u1, const dd* u2, const dd* mult, const dd* piv,
                              dd* b) {
-  for (int i = 0; i + 1 < p; ++i) {
-    if (piv[i].hi != 0.f) {
-      const dd bi = b[i], bn = b[i + 1];
-      b[i] = bn;
-      b[i + 1] = dd_sub(bi, dd_mul(mult[i], bn));
-    } else {
-      b[i + 1] = dd_sub(b[i + 1], dd_mul(mult[i], b[i]));
-    }
+  dd bi = b[0];
+  for (int i = 0; i + 1 < p; ++i) {   // forward, branch-free: b_i is carried in registers
+    const bool sw = piv[i].hi != 0.f;
+    const dd bn = b[i + 1];
+    const dd keep = dd_sel(sw, bn, bi), elim = dd_sel(sw, bi, bn);
+    b[i] = keep;
+    bi = dd_sub(elim, dd_mul(mult[i], keep));
   }
+  b[p - 1] = bi;
+  dd x1 = {0.f, 0.f}, x2 = {0.f, 0.f};   // x_{i+1}, x_{i+2}
   for (int i = p - 1; i >= 0; --i) {
-    dd s = b[i];
-    if (i + 1 < p) s = dd_sub(s, dd_mul(u1[i], b[i + 1]));
-    if (i + 2 < p) s = dd_sub(s, dd_mul(u2[i], b[i + 2]));
-    b[i] = dd_mul(s, u0inv[i]);
+    dd s = dd_sub(b[i], dd_mul(u2[i], x2));
+    s = dd_sub(s, dd_mul(u1[i], x1));
+    const dd x = dd_mul(s, u0inv[i]);
+    b[i] = x;
+    x2 = x1;
+    x1 = x;
   }
 }
 
@@ -724,7 +864,10 @@ __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   s.rr_dim = (r + kClusterExt < p) ? r + kClusterExt : p;
   s.rr_in_smem = (s.rr_dim <= kRRMax);
   s.rr_units = s.rr_in_smem ? 2 * (int64_t)s.rr_dim * s.rr_dim : 0;
-  s.a_in_smem = (p <= kSmemMaxP);
+  // the tridiagonalisation's workspace (phase 1 only) shares its region with
+  // the inverse iteration's working set (phase 3 on)
+  const int64_t tri = (int64_t)kTriUnitsPerP * s.P + 2 * kWarps;
+  s.a_in_smem = (p <= kSmemMaxP) && (s.vec_units + s.rr_units + (int64_t)p * p + tri <= kSmemDynUnits);
   s.eig_in_smem = (r <= kEigMaxR);
   const int64_t a = s.a_in_smem ? (int64_t)p * p : 0;
   const int64_t g = s.eig_in_smem ? (int64_t)5 * r * r : 0;   // H, Q, W, U, y (complex float)
@@ -733,8 +876,8 @@ __host__ __device__ inline SmemPlan smem_plan(int p, int r) {
   // the vector p) on chip when it fits: its tridiagonal recurrences are
   // chains of dependent loads and stores
   const int64_t inv = (int64_t)s.rr_dim * 7 * p;
-  s.inv_in_smem = (s.vec_units + s.rr_units + s.big_units + inv <= kSmemDynUnits);
-  s.inv_units = s.inv_in_smem ? inv : 0;
+  s.inv_in_smem = (s.vec_units + s.rr_units + s.big_units + (inv > tri ? inv : tri) <= kSmemDynUnits);
+  s.inv_units = s.inv_in_smem ? (inv > tri ? inv : tri) : tri;
   return s;
 }
 
@@ -817,7 +960,7 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   if (tid == 0) w.clk[1] = clock64();
 
   // ---- 1. tridiagonalise G_X (df64)
-  tridiagonalize(A, p, d, e, vs, pv, wv, part, sc);
+  tridiagonalize(A, p, d, e, inv_base, P);
   if (tid == 0) w.clk[2] = clock64();
 
   // ---- 2. FP32 multisection for the rw largest eigenvalues of T
@@ -859,7 +1002,10 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
     }
     return 0.5f * (lo + hi);
   };
-  for (int i = warp; i < rw; i += kWarps) {
+  // the last pass's idle warps take the eigenvalues after the rw-th (the
+  // cluster test below reads them instead of running more multisections)
+  const int npre = min(p, ((rw + kWarps - 1) / kWarps) * kWarps);
+  for (int i = warp; i < npre; i += kWarps) {
     const float v = multisect(i);
     if (lane == 0) lam[i] = dd_make(v);
   }
@@ -876,7 +1022,7 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
     while (rwe < cap) {
       const float last = lam[rwe - 1].hi;
       if (!(last > floor_v)) break;
-      const float v = multisect(rwe);
+      const float v = (rwe < npre) ? lam[rwe].hi : multisect(rwe);
       if (fabsf(v - last) > 8.f * kEps32 * tnorm) break;
       if (lane == 0) lam[rwe] = dd_make(v);
       __syncwarp();
@@ -895,21 +1041,24 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   const float tiny = fmaxf(1e-13f * tnorm, FLT_MIN);
   for (int round = 0; round < 2; ++round) {
     const float sep = (round == 0) ? 2.f * kEps32 * tnorm : 1e-12f * tnorm;
-    for (int i = tid; i < rwe; i += kThreads) {
+    // vector i on lane i / 8 of warp i % 8: the factorisations and solves are
+    // serial recurrences, so they are spread over all warps' issue slots
+    for (int i = warp + kWarps * lane; i < rwe; i += kThreads) {
       dd* u0 = LU + (int64_t)i * 5 * p;
       dd shift = lam[i];
       for (int q = 0; q < i; ++q)    // (numerically) equal shifts: separate them slightly
         if (fabsf(lam[q].hi - shift.hi) <= sep) shift = dd_sub(shift, dd_make(sep));
       tri_lu_dd(d, e, p, shift, tiny, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p);
-      if (round == 0) {
-        dd* z = Z + (int64_t)i * p;
-        for (int j = 0; j < p; ++j)
-          z[j] = dd_make(1.f + 0.1f * (float)(((j + 1) * 7919 + (i + 1) * 104729) % 97) / 97.f);
+    }
+    if (round == 0) {
+      for (int idx = tid; idx < rwe * p; idx += kThreads) {
+        const int i = idx / p, j = idx - i * p;
+        Z[idx] = dd_make(1.f + 0.1f * (float)(((j + 1) * 7919 + (i + 1) * 104729) % 97) / 97.f);
       }
     }
     __syncthreads();
     for (int it = 0; it < kInvIters; ++it) {
-      for (int i = tid; i < rwe; i += kThreads) {
+      for (int i = warp + kWarps * lane; i < rwe; i += kThreads) {
         dd* u0 = LU + (int64_t)i * 5 * p;
         tri_solve_dd(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, Z + (int64_t)i * p);
       }
@@ -920,16 +1069,27 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   }
   if (tid == 0) w.clk[4] = clock64();
 
-  // ---- 4. back-transform: v = H_0 H_1 ... H_{p-3} z  (warp per vector)
-  for (int i = warp; i < rw; i += kWarps) {
-    dd* z = Z + (int64_t)i * p;
+  // ---- 4. back-transform: v = H_0 H_1 ... H_{p-3} z  (half a warp per vector)
+  for (int i0 = 2 * warp; i0 < rw; i0 += 2 * kWarps) {
+    const int i = i0 + (lane >> 4), hl = lane & 15;
+    const bool live = i < rw;
+    dd* z = Z + (int64_t)(live ? i : i0) * p;
     for (int k = p - 3; k >= 0; --k) {
       const int Lk = p - k - 1;
-      const dd* v = A + (int64_t)k * p + (k + 1);
-      dd s = {0.f, 0.f};
-      for (int j = lane; j < Lk; j += 32) s = dd_fma(v[j], z[k + 1 + j], s);
-      s = dd_scale(warp_sum_dd(s), -2.f);
-      for (int j = lane; j < Lk; j += 32) z[k + 1 + j] = dd_fma(s, v[j], z[k + 1 + j]);
+      const dd* v = A + (int64_t)(k + 1) * p + k;   // down column k
+      float ss = 0.f, sc2 = 0.f;
+      if (live)
+        for (int j = hl; j < Lk; j += 16) dot2_acc(ss, sc2, v[(int64_t)j * p], z[k + 1 + j]);
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) {   // within each half warp
+        const float so = __shfl_xor_sync(0xffffffffu, ss, o), co = __shfl_xor_sync(0xffffffffu, sc2, o);
+        const dd q = two_sum(ss, so);
+        ss = q.hi;
+        sc2 = (sc2 + co) + q.lo;
+      }
+      const dd s = dd_scale(quick_two_sum(ss, sc2), -2.f);
+      if (live)
+        for (int j = hl; j < Lk; j += 16) z[k + 1 + j] = dd_fma(s, v[(int64_t)j * p], z[k + 1 + j]);
       __syncwarp();
     }
   }
@@ -964,10 +1124,20 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   }
   __syncthreads();
 
-  // ---- 6. A~ = vsi^T G_XY vsi (df64; independent of the scaling)
+  // ---- 6. A~ = vsi^T G_XY vsi (df64; independent of the scaling). G_XY is
+  //         staged into A's region (free after the back-transform) and Y, A~
+  //         into the inverse iteration's (free after phase 3) when on chip.
+  const dd* GXY = w.GXYd;
+  if (plan.a_in_smem) {
+    for (int idx = tid; idx < p * p; idx += kThreads) big[idx] = w.GXYd[idx];
+    GXY = big;
+    __syncthreads();
+  }
+  dd* Yb = plan.inv_in_smem ? LU : w.Y;
+  dd* At = plan.inv_in_smem ? LU + (int64_t)re * p : w.lu;   // re x re df64
   for (int idx = tid; idx < re * p; idx += kThreads) {
     const int k = idx / p, row = idx - k * p;
-    const dd* g = w.GXYd + (int64_t)row * p;
+    const dd* g = GXY + (int64_t)row * p;
     const dd* v = Z + (int64_t)k * p;
     dd s0 = {0.f, 0.f}, s1 = {0.f, 0.f};
     int b = 0;
@@ -976,10 +1146,9 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
       s1 = dd_fma(g[b + 1], v[b + 1], s1);
     }
     if (b < p) s0 = dd_fma(g[b], v[b], s0);
-    w.Y[idx] = dd_add(s0, s1);
+    Yb[idx] = dd_add(s0, s1);
   }
   __syncthreads();
-  dd* At = w.lu;                       // re x re df64 (the LU scratch is free again)
   CF* Hc = plan.eig_in_smem ? reinterpret_cast<CF*>(big) : reinterpret_cast<CF*>(w.lu + (int64_t)re * re);
   CF* Qc = Hc + re * re;
   CF* Wc = Qc + re * re;
@@ -988,7 +1157,7 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   for (int idx = tid; idx < re * re; idx += kThreads) {
     const int k = idx / re, l = idx - k * re;
     const dd* v = Z + (int64_t)k * p;
-    const dd* y = w.Y + (int64_t)l * p;
+    const dd* y = Yb + (int64_t)l * p;
     dd s = {0.f, 0.f};
     for (int b = 0; b < p; ++b) s = dd_fma(v[b], y[b], s);
     At[idx] = s;

@@ -32,6 +32,7 @@ int main() {
     pr("sub", a, b, dd_sub(a, b));
     pr("mul", a, b, dd_mul(a, b));
     if (b.hi != 0.f) pr("div", a, b, dd_div(a, b));
+    if (b.hi != 0.f) pr("recip", b, b, dd_recip(b));
     const dd aa = dd_abs(a);
     pr("sqrt", aa, aa, dd_sqrt(aa));
     const dd c = dd_from_double(rnd());

@@ -53,7 +53,8 @@ def test_conversion_from_int64_exact_below_2_48(lines):
 
 
 @pytest.mark.parametrize("op,bound", [("add", 2 ** -46), ("sub", 2 ** -46), ("mul", 2 ** -45),
-                                      ("div", 2 ** -44), ("sqrt", 2 ** -44), ("fma", 2 ** -45)])
+                                      ("div", 2 ** -44), ("sqrt", 2 ** -44), ("fma", 2 ** -45),
+                                      ("recip", 2 ** -45)])
 def test_operations_against_exact_rationals(lines, op, bound):
     worst = Fraction(0)
     cnt = 0
@@ -76,6 +77,8 @@ def test_operations_against_exact_rationals(lines, op, bound):
                 exact = a * b
             elif op == "div":
                 exact = a / b
+            elif op == "recip":
+                exact = 1 / b
             else:
                 # compare r^2 with a: relative error of sqrt is half that of r^2
                 e = _rel(r * r, a) / 2
