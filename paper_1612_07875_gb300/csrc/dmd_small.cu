@@ -88,6 +88,7 @@ __device__ __forceinline__ CF cconj(CF a) { return {a.re, -a.im}; }
 __device__ __forceinline__ CF cscale(CF a, float s) { return {a.re * s, a.im * s}; }
 __device__ __forceinline__ float cabs2(CF a) { return a.re * a.re + a.im * a.im; }
 __device__ __forceinline__ float cabs(CF a) { return hypotf(a.re, a.im); }
+// a / b by Smith's method (no overflow or underflow of |b|^2)
 __device__ __forceinline__ CF cdiv(CF a, CF b) {
   if (fabsf(b.re) >= fabsf(b.im)) {
     const float r = b.im / b.re, den = b.re + b.im * r;
@@ -394,8 +395,9 @@ __device__ int sturm32(const float* d, const float* e2, int p, float x, float pi
 // mult / piv (0 or 1) describe L. Pivots below `tiny` are raised to it.
 // Branch-free (selects), so the lanes of a warp that factor different shifts
 // never diverge.
-__device__ void tri_lu_dd(const dd* d, const dd* e, int p, dd mu, float tiny, dd* u0, dd* u1, dd* u2,
-                          dd* mult, dd* piv) {
+__device__ void tri_lu_dd(const dd* __restrict__ d, const dd* __restrict__ e, int p, dd mu, float tiny,
+                          dd* __restrict__ u0, dd* __restrict__ u1, dd* __restrict__ u2, dd* __restrict__ mult,
+                          dd* __restrict__ piv) {
   dd cd = dd_sub(d[0], mu), c1 = (p > 1) ? e[0] : dd{0.f, 0.f};
   for (int i = 0; i + 1 < p; ++i) {
     const dd sub = e[i];
@@ -423,8 +425,9 @@ __device__ void tri_lu_dd(const dd* d, const dd* e, int p, dd mu, float tiny, dd
   u2[p - 1] = {0.f, 0.f};
 }
 
-__device__ void tri_solve_dd(int p, const dd* u0inv, const dd* u1, const dd* u2, const dd* mult, const dd* piv,
-                             dd* b) {
+__device__ void tri_solve_dd(int p, const dd* __restrict__ u0inv, const dd* __restrict__ u1,
+                             const dd* __restrict__ u2, const dd* __restrict__ mult, const dd* __restrict__ piv,
+                             dd* __restrict__ b) {
   dd bi = b[0];
   for (int i = 0; i + 1 < p; ++i) {   // forward, branch-free: b_i is carried in registers
     const bool sw = piv[i].hi != 0.f;
@@ -446,17 +449,20 @@ __device__ void tri_solve_dd(int p, const dd* u0inv, const dd* u1, const dd* u2,
 }
 
 // Orthonormalise vectors Z[i*p ..], i < rw, in order (classical Gram-Schmidt,
-// `passes` times), vectors over warps and rows over threads.
-// A vector that lies (to working precision) in the span of the earlier ones
-// -- inverse iteration with shifts inside a cluster closer than the shifts'
-// resolution -- is replaced by a fixed pseudo-random vector and
-// orthogonalised again, so the set stays a basis of the cluster's subspace.
-__device__ dd norm2_dd(const dd* z, int p, dd* red) {
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  dd nn = {0.f, 0.f};
-  for (int q = tid; q < p; q += kThreads) nn = dd_fma(z[q], z[q], nn);
-  nn = warp_sum_dd(nn);
-  if (lane == 0) red[warp] = nn;
+// `passes` times). The vectors stay unnormalised until the end: vector i is
+// projected with coefficients ((z_j . z_i) / |z_j|) / |z_j|, the dots of one pass
+// (and the vector's own norm) taken together, one vector per warp and the
+// positions over its lanes; one final pass scales every vector. A vector that
+// lies (to working precision) in the span of the earlier ones -- inverse
+// iteration with shifts inside a cluster closer than the shifts' resolution --
+// is replaced by a fixed pseudo-random vector and projected twice, so the set
+// stays a basis of the cluster's subspace. rn: rw reciprocal norms 1 / |z_j|
+// (not 1 / |z_j|^2: after a solve |z|^2 reaches ~1e30, and the low word of
+// its reciprocal would sit in FP32's denormal range).
+__device__ dd block_sum_dd(dd v, dd* red) {   // every thread gets the same sum
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  v = warp_sum_dd(v);
+  if (lane == 0) red[warp] = v;
   __syncthreads();
   dd t = red[0];
   for (int w = 1; w < kWarps; ++w) t = dd_add(t, red[w]);
@@ -464,58 +470,59 @@ __device__ dd norm2_dd(const dd* z, int p, dd* red) {
   return t;
 }
 
-__device__ void cgs_dd(dd* Z, int rw, int p, int passes, dd* coef, dd* red, dd* sc) {
+// one projection pass of z_i against z_0..z_{i-1}; with `self` also z_i . z_i
+// (before the projection) into *self_out
+__device__ void cgs_pass(dd* Z, int i, int p, const dd* rn, dd* coef, dd* self_out) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const dd* zi = Z + (int64_t)i * p;
+  const int nj = self_out ? i + 1 : i;
+  for (int j = warp; j < nj; j += kWarps) {
+    const dd* zj = Z + (int64_t)j * p;
+    dd acc = {0.f, 0.f};   // full df64 sums: the basis must be orthonormal to df64 resolution
+    for (int q = lane; q < p; q += 32) acc = dd_fma(zj[q], zi[q], acc);
+    acc = warp_sum_dd(acc);
+    if (lane == 0) {
+      const dd dt = acc;
+      if (j < i)
+        coef[j] = dd_mul(dd_mul(dt, rn[j]), rn[j]);
+      else
+        *self_out = dt;
+    }
+  }
+  __syncthreads();
+  dd* zw = Z + (int64_t)i * p;
+  for (int q = tid; q < p; q += kThreads) {
+    dd s = zw[q];
+    for (int j = 0; j < i; ++j) s = dd_sub(s, dd_mul(coef[j], Z[(int64_t)j * p + q]));
+    zw[q] = s;
+  }
+  __syncthreads();
+}
+
+__device__ void cgs_dd(dd* Z, int rw, int p, int passes, dd* coef, dd* rn, dd* red, dd* sc) {
+  const int tid = threadIdx.x;
   for (int i = 0; i < rw; ++i) {
     dd* zi = Z + (int64_t)i * p;
-    const dd t0 = norm2_dd(zi, p, red);
-    for (int pass = 0; pass < passes && i > 0; ++pass) {
-      for (int j = warp; j < i; j += kWarps) {
-        const dd* zj = Z + (int64_t)j * p;
-        dd s = {0.f, 0.f};
-        for (int q = lane; q < p; q += 32) s = dd_fma(zj[q], zi[q], s);
-        s = warp_sum_dd(s);
-        if (lane == 0) coef[j] = s;
-      }
-      __syncthreads();
-      for (int q = tid; q < p; q += kThreads) {
-        dd s = zi[q];
-        for (int j = 0; j < i; ++j) s = dd_sub(s, dd_mul(coef[j], Z[(int64_t)j * p + q]));
-        zi[q] = s;
-      }
-      __syncthreads();
-    }
-    dd t = norm2_dd(zi, p, red);
-    if (i > 0 && !(t.hi > 1e-20f * t0.hi)) {   // collapsed: reseed and orthogonalise twice
+    for (int pass = 0; pass < passes && i > 0; ++pass) cgs_pass(Z, i, p, rn, coef, pass == 0 ? &sc[3] : nullptr);
+    dd nn = {0.f, 0.f};
+    for (int q = tid; q < p; q += kThreads) nn = dd_fma(zi[q], zi[q], nn);
+    dd t = block_sum_dd(nn, red);
+    if (i > 0 && !(t.hi > 1e-20f * sc[3].hi)) {   // collapsed: reseed and project twice
       for (int q = tid; q < p; q += kThreads) {
         const unsigned hsh = (unsigned)(q + 1) * 2654435761u ^ (unsigned)(i + 1) * 40503u;
         zi[q] = dd_make((float)((hsh >> 8) & 0xFFFFu) / 65536.f - 0.5f);
       }
       __syncthreads();
-      for (int pass = 0; pass < 2; ++pass) {
-        for (int j = warp; j < i; j += kWarps) {
-          const dd* zj = Z + (int64_t)j * p;
-          dd s = {0.f, 0.f};
-          for (int q = lane; q < p; q += 32) s = dd_fma(zj[q], zi[q], s);
-          s = warp_sum_dd(s);
-          if (lane == 0) coef[j] = s;
-        }
-        __syncthreads();
-        for (int q = tid; q < p; q += kThreads) {
-          dd s = zi[q];
-          for (int j = 0; j < i; ++j) s = dd_sub(s, dd_mul(coef[j], Z[(int64_t)j * p + q]));
-          zi[q] = s;
-        }
-        __syncthreads();
-      }
-      t = norm2_dd(zi, p, red);
+      for (int pass = 0; pass < 2; ++pass) cgs_pass(Z, i, p, rn, coef, nullptr);
+      nn = {0.f, 0.f};
+      for (int q = tid; q < p; q += kThreads) nn = dd_fma(zi[q], zi[q], nn);
+      t = block_sum_dd(nn, red);
     }
-    if (tid == 0) sc[3] = (t.hi > 0.f) ? dd_div(dd_make(1.f), dd_sqrt(t)) : dd{0.f, 0.f};
-    __syncthreads();
-    const dd inv = sc[3];
-    for (int q = tid; q < p; q += kThreads) zi[q] = dd_mul(zi[q], inv);
+    if (tid == 0) rn[i] = (t.hi > 0.f) ? dd_recip(dd_sqrt(t)) : dd{0.f, 0.f};
     __syncthreads();
   }
+  for (int idx = tid; idx < rw * p; idx += kThreads) Z[idx] = dd_mul(Z[idx], rn[idx / p]);
+  __syncthreads();
 }
 
 // Rayleigh-Ritz on the orthonormal vectors Z (rw x p, vector-major):
@@ -549,17 +556,18 @@ __device__ void rayleigh_ritz(dd* Z, int rw, int p, const dd* d, const dd* e, dd
   __syncthreads();
   const int n2 = rw + (rw & 1);
   for (int sweep = 0; sweep < kJacobiSweeps && rw > 1; ++sweep) {
-    if (tid == 0) {    // converged when the off-diagonal is below df64 resolution
+    if (warp == 0) {    // converged when the off-diagonal is below df64 resolution
       float off = 0.f, dia = 0.f;
-      for (int a = 0; a < rw; ++a)
-        for (int b = 0; b < rw; ++b) {
-          const float v = fabsf(H[a * rw + b].hi);
-          if (a == b)
-            dia = fmaxf(dia, v);
-          else
-            off = fmaxf(off, v);
-        }
-      sc[4] = {(off <= 1e-15f * dia) ? 1.f : 0.f, 0.f};
+      for (int idx = lane; idx < rw * rw; idx += 32) {
+        const float v = fabsf(H[idx].hi);
+        if (idx / rw == idx % rw)
+          dia = fmaxf(dia, v);
+        else
+          off = fmaxf(off, v);
+      }
+      off = warp_max_f(off);
+      dia = warp_max_f(dia);
+      if (lane == 0) sc[4] = {(off <= 1e-15f * dia) ? 1.f : 0.f, 0.f};
     }
     __syncthreads();
     if (sc[4].hi != 0.f) break;
@@ -576,16 +584,16 @@ __device__ void rayleigh_ritz(dd* Z, int rw, int p, const dd* d, const dd* e, dd
         if (b < rw) {
           const dd hab = H[a * rw + b];
           if (hab.hi != 0.f) {
-            const dd tau = dd_div(dd_sub(H[b * rw + b], H[a * rw + a]), dd_scale(hab, 2.f));
+            const dd tau = dd_mul(dd_sub(H[b * rw + b], H[a * rw + a]), dd_recip(dd_scale(hab, 2.f)));
             // |tau| > 1e18 (or not finite: h_ab is a denormal): h_ab is below
             // 1e-18 of the diagonal gap, under df64 resolution, and the
             // rotation would be the identity to working precision; tau^2
             // would also leave the FP32 exponent range. Skip it.
             if (fabsf(tau.hi) <= 1e18f) {
               const dd root = dd_sqrt(dd_fma(tau, tau, dd_make(1.f)));
-              dd t = dd_div(dd_make(1.f), dd_add(dd_abs(tau), root));
+              dd t = dd_recip(dd_add(dd_abs(tau), root));
               if (tau.hi < 0.f) t = dd_neg(t);
-              c = dd_div(dd_make(1.f), dd_sqrt(dd_fma(t, t, dd_make(1.f))));
+              c = dd_recip(dd_sqrt(dd_fma(t, t, dd_make(1.f))));
               s = dd_mul(t, c);
             }
           }
@@ -702,11 +710,11 @@ __device__ bool warp_eig32(CF* H, CF* Q, CF* W, CF* U, CF* ycol, int r, float* c
   const int cap = 60 * r + 60;
   while (hi > 0) {
     int l = hi;
-    while (l > 0) {
-      const float sub = cabs(H[l * r + l - 1]);
-      float scale = cabs(H[l * r + l]) + cabs(H[(l - 1) * r + l - 1]);
-      if (scale == 0.f) scale = hnorm;
-      if (sub <= kEps32 * scale) break;
+    while (l > 0) {   // negligible subdiagonal: |h| <= eps32 (|a|^2 + |b|^2)^(1/2), in squares
+      const float sub2 = cabs2(H[l * r + l - 1]);
+      float scale2 = cabs2(H[l * r + l]) + cabs2(H[(l - 1) * r + l - 1]);
+      if (scale2 == 0.f) scale2 = hnorm * hnorm;
+      if (sub2 <= kEps32 * kEps32 * scale2) break;
       --l;
     }
     __syncwarp();
@@ -740,19 +748,34 @@ __device__ bool warp_eig32(CF* H, CF* Q, CF* W, CF* U, CF* ycol, int r, float* c
     for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = csub(H[q * r + q], mu);
     __syncwarp();
     for (int j = l; j < hi; ++j) {
-      const CF a = H[j * r + j], b = H[(j + 1) * r + j];
-      const float aa = cabs(a), rho = hypotf(aa, cabs(b));
+      CF a = H[j * r + j], b = H[(j + 1) * r + j];
+      // (a, b) scaled by a power of two to a largest component in [1, 2)
+      // (c and s do not change), so the squared moduli neither underflow nor
+      // overflow; then c, s from one reciprocal square root
+      const float mx = fmaxf(fmaxf(fabsf(a.re), fabsf(a.im)), fmaxf(fabsf(b.re), fabsf(b.im)));
       float c;
       CF s;
-      if (rho == 0.f) {
+      if (mx == 0.f) {
         c = 1.f;
         s = {0.f, 0.f};
-      } else if (aa == 0.f) {
-        c = 0.f;
-        s = {1.f, 0.f};
       } else {
-        c = aa / rho;
-        s = cscale(cmul(cscale(a, 1.f / aa), cconj(b)), 1.f / rho);
+        const int be = min((__float_as_int(mx) >> 23) & 0xff, 253);
+        const float sc = __int_as_float((254 - be) << 23);
+        a = cscale(a, sc);
+        b = cscale(b, sc);
+        const float aa2 = cabs2(a), rho2 = aa2 + cabs2(b);
+        if (aa2 < 1e-30f) {   // |a| negligible against |b| >= 1
+          c = 0.f;
+          s = {1.f, 0.f};
+        } else {
+          // k = 1 / (|a| rho): c = |a|^2 k, s = a conj(b) k; rsqrt plus one
+          // Newton step (about 1 ulp), so c^2 + |s|^2 = 1 to FP32 rounding
+          const float x = aa2 * rho2;
+          float k = rsqrtf(x);
+          k = k * fmaf(-0.5f * x * k, k, 1.5f);
+          c = aa2 * k;
+          s = cscale(cmul(a, cconj(b)), k);
+        }
       }
       __syncwarp();
       for (int q = j + lane; q < r; q += 32) {
@@ -1063,7 +1086,7 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
         tri_solve_dd(p, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p, Z + (int64_t)i * p);
       }
       __syncthreads();
-      cgs_dd(Z, rwe, p, (it + 1 == kInvIters) ? 2 : 1, coef, red, sc);
+      cgs_dd(Z, rwe, p, (it + 1 == kInvIters) ? 2 : 1, coef, vs, red, sc);
     }
     rayleigh_ritz(Z, rwe, p, d, e, rrH, rrR, LU + (int64_t)rwe * 5 * p, lam, sc, ord);
   }

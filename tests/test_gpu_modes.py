@@ -110,6 +110,24 @@ def test_u8_video_end_to_end_exact_gram(cuda_device):
         S.sdmd_destroy(h)
 
 
+@pytest.mark.parametrize("seed_off,T", [(0, 32), (0, 45), (3, 32), (5, 40), (11, 33)])
+def test_planted_fp32_noise_floor_cluster(cuda_device, seed_off, T):
+    # r = 10 on a window with 5 planted modes: the other 5 requested
+    # eigenvalues sit in the noise floor's cluster, where inverse iteration
+    # needs its Gram-Schmidt / Rayleigh-Ritz rounds to resolve the subspace.
+    ps = synth.PlantedStream(seed=synth.config_seed(1) + seed_off)
+    n, m, r = ps.n, 32, 10
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    so = oracle.StreamOracle(n, m, "f32")
+    try:
+        _stream(h, so, [ps.snapshot(t) for t in range(T)], cuda_device)
+        rk, lam, sig, V, _ = _modes(h, n, r, cuda_device, m)
+        G = _gram(h, m, cuda_device, False)
+        _compare_same_input(G, rk, lam, sig, V, r)
+    finally:
+        S.sdmd_destroy(h)
+
+
 def test_ramp_up_window_not_full(cuda_device):
     ps = synth.PlantedStream(side=24, noise_var=1e-4, seed=77)
     n, m = ps.n, 32
