@@ -659,6 +659,36 @@ __device__ void rayleigh_ritz(dd* Z, int rw, int p, const dd* d, const dd* e, dd
 // warp: Hessenberg reduction, shifted QR to Schur form with Q accumulated,
 // right eigenvectors W and left eigenvectors U (columns, unit norm).
 // Returns false if the QR iteration cap was reached.
+// Complex Givens rotation [c s; -conj(s) c] taking (a, b) to (rho, 0). (a, b)
+// are scaled by a power of two to a largest component in [1, 2) (c and s do
+// not change), so the squared moduli neither underflow nor overflow; then c,
+// s from one reciprocal square root.
+__device__ __forceinline__ void givens32(CF a, CF b, float& c, CF& s) {
+  const float mx = fmaxf(fmaxf(fabsf(a.re), fabsf(a.im)), fmaxf(fabsf(b.re), fabsf(b.im)));
+  if (mx == 0.f) {
+    c = 1.f;
+    s = {0.f, 0.f};
+    return;
+  }
+  const int be = min((__float_as_int(mx) >> 23) & 0xff, 253);
+  const float sc = __int_as_float((254 - be) << 23);
+  a = cscale(a, sc);
+  b = cscale(b, sc);
+  const float aa2 = cabs2(a), rho2 = aa2 + cabs2(b);
+  if (aa2 < 1e-30f) {   // |a| negligible against |b| >= 1
+    c = 0.f;
+    s = {1.f, 0.f};
+    return;
+  }
+  // k = 1 / (|a| rho): c = |a|^2 k, s = a conj(b) k; rsqrt plus one Newton
+  // step (about 1 ulp), so c^2 + |s|^2 = 1 to FP32 rounding
+  const float x = aa2 * rho2;
+  float k = rsqrtf(x);
+  k = k * fmaf(-0.5f * x * k, k, 1.5f);
+  c = aa2 * k;
+  s = cscale(cmul(a, cconj(b)), k);
+}
+
 __device__ bool warp_eig32(CF* H, CF* Q, CF* W, CF* U, CF* ycol, int r, float* cs, CF* sn) {
   const int lane = threadIdx.x & 31;
   for (int idx = lane; idx < r * r; idx += 32) {
@@ -709,13 +739,20 @@ __device__ bool warp_eig32(CF* H, CF* Q, CF* W, CF* U, CF* ycol, int r, float* c
   int hi = r - 1, its = 0, total = 0;
   const int cap = 60 * r + 60;
   while (hi > 0) {
-    int l = hi;
-    while (l > 0) {   // negligible subdiagonal: |h| <= eps32 (|a|^2 + |b|^2)^(1/2), in squares
-      const float sub2 = cabs2(H[l * r + l - 1]);
-      float scale2 = cabs2(H[l * r + l]) + cabs2(H[(l - 1) * r + l - 1]);
+    // l = the largest i <= hi whose subdiagonal H[i][i-1] is negligible
+    // (|h| <= eps32 (|a|^2 + |b|^2)^(1/2), in squares), else 0
+    auto negligible = [&](int i) {
+      const float sub2 = cabs2(H[i * r + i - 1]);
+      float scale2 = cabs2(H[i * r + i]) + cabs2(H[(i - 1) * r + i - 1]);
       if (scale2 == 0.f) scale2 = hnorm * hnorm;
-      if (sub2 <= kEps32 * kEps32 * scale2) break;
-      --l;
+      return sub2 <= kEps32 * kEps32 * scale2;
+    };
+    int l = hi;
+    if (r <= 32) {   // one subdiagonal per lane
+      const unsigned neg = __ballot_sync(0xffffffffu, lane >= 1 && lane <= hi && negligible(lane));
+      l = neg ? 31 - __clz(neg) : 0;
+    } else {
+      while (l > 0 && !negligible(l)) --l;
     }
     __syncwarp();
     if (l > 0 && lane == 0) H[l * r + l - 1] = {0.f, 0.f};
@@ -747,60 +784,84 @@ __device__ bool warp_eig32(CF* H, CF* Q, CF* W, CF* U, CF* ycol, int r, float* c
     }
     for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = csub(H[q * r + q], mu);
     __syncwarp();
-    for (int j = l; j < hi; ++j) {
-      CF a = H[j * r + j], b = H[(j + 1) * r + j];
-      // (a, b) scaled by a power of two to a largest component in [1, 2)
-      // (c and s do not change), so the squared moduli neither underflow nor
-      // overflow; then c, s from one reciprocal square root
-      const float mx = fmaxf(fmaxf(fabsf(a.re), fabsf(a.im)), fmaxf(fabsf(b.re), fabsf(b.im)));
-      float c;
-      CF s;
-      if (mx == 0.f) {
-        c = 1.f;
-        s = {0.f, 0.f};
-      } else {
-        const int be = min((__float_as_int(mx) >> 23) & 0xff, 253);
-        const float sc = __int_as_float((254 - be) << 23);
-        a = cscale(a, sc);
-        b = cscale(b, sc);
-        const float aa2 = cabs2(a), rho2 = aa2 + cabs2(b);
-        if (aa2 < 1e-30f) {   // |a| negligible against |b| >= 1
-          c = 0.f;
-          s = {1.f, 0.f};
-        } else {
-          // k = 1 / (|a| rho): c = |a|^2 k, s = a conj(b) k; rsqrt plus one
-          // Newton step (about 1 ulp), so c^2 + |s|^2 = 1 to FP32 rounding
-          const float x = aa2 * rho2;
-          float k = rsqrtf(x);
-          k = k * fmaf(-0.5f * x * k, k, 1.5f);
-          c = aa2 * k;
-          s = cscale(cmul(a, cconj(b)), k);
+    if (r <= 32) {
+      // row rotations: lane q carries H[j][q] through rotations j = l..min(q, hi-1)
+      // in registers; rotation j's pivot H[j][j] comes from lane j by shuffle
+      const int q = lane;
+      const bool col = q >= l && q < r;
+      CF cur = col ? H[l * r + q] : CF{0.f, 0.f};
+      for (int j = l; j < hi; ++j) {
+        const CF a = {__shfl_sync(0xffffffffu, cur.re, j), __shfl_sync(0xffffffffu, cur.im, j)};
+        const CF b = H[(j + 1) * r + j];   // row j+1 is untouched before rotation j
+        float c;
+        CF s;
+        givens32(a, b, c, s);
+        if (col && q >= j) {
+          const CF h2 = H[(j + 1) * r + q];
+          H[j * r + q] = cadd(cscale(cur, c), cmul(s, h2));
+          cur = csub(cscale(h2, c), cmul(cconj(s), cur));
+        }
+        if (lane == 0) {
+          cs[j] = c;
+          sn[j] = s;
         }
       }
+      if (col) H[(min(q, hi - 1) + 1) * r + q] = cur;
       __syncwarp();
-      for (int q = j + lane; q < r; q += 32) {
-        const CF h1 = H[j * r + q], h2 = H[(j + 1) * r + q];
-        H[j * r + q] = cadd(cscale(h1, c), cmul(s, h2));
-        H[(j + 1) * r + q] = csub(cscale(h2, c), cmul(cconj(s), h1));
-      }
-      if (lane == 0) {
-        cs[j] = c;
-        sn[j] = s;
+      // column rotations: lane q applies rotations j >= max(l, q-1) to H's row
+      // q (rows above j+1 only) and all of them to Q's row q, carrying column j
+      if (q < r) {
+        const int j0 = max(l, q - 1);
+        const bool hrow = q <= hi;
+        CF hc = hrow ? H[q * r + j0] : CF{0.f, 0.f};
+        CF qc = Q[q * r + l];
+        for (int j = l; j < hi; ++j) {
+          const float c = cs[j];
+          const CF s = sn[j];
+          if (hrow && j >= j0) {
+            const CF h2 = H[q * r + j + 1];
+            H[q * r + j] = cadd(cscale(hc, c), cmul(h2, cconj(s)));
+            hc = csub(cscale(h2, c), cmul(hc, s));
+          }
+          const CF q2 = Q[q * r + j + 1];
+          Q[q * r + j] = cadd(cscale(qc, c), cmul(q2, cconj(s)));
+          qc = csub(cscale(q2, c), cmul(qc, s));
+        }
+        if (hrow) H[q * r + hi] = hc;
+        Q[q * r + hi] = qc;
       }
       __syncwarp();
-    }
-    for (int j = l; j < hi; ++j) {
-      const float c = cs[j];
-      const CF s = sn[j];
-      for (int q = lane; q < r + (j + 2); q += 32) {
-        CF* M = (q < j + 2) ? H : Q;
-        const int row = (q < j + 2) ? q : q - (j + 2);
-        if (q >= j + 2 && row >= r) continue;
-        const CF h1 = M[row * r + j], h2 = M[row * r + j + 1];
-        M[row * r + j] = cadd(cscale(h1, c), cmul(h2, cconj(s)));
-        M[row * r + j + 1] = csub(cscale(h2, c), cmul(h1, s));
+    } else {
+      for (int j = l; j < hi; ++j) {
+        const CF a = H[j * r + j], b = H[(j + 1) * r + j];
+        float c;
+        CF s;
+        givens32(a, b, c, s);
+        __syncwarp();
+        for (int q = j + lane; q < r; q += 32) {
+          const CF h1 = H[j * r + q], h2 = H[(j + 1) * r + q];
+          H[j * r + q] = cadd(cscale(h1, c), cmul(s, h2));
+          H[(j + 1) * r + q] = csub(cscale(h2, c), cmul(cconj(s), h1));
+        }
+        if (lane == 0) {
+          cs[j] = c;
+          sn[j] = s;
+        }
+        __syncwarp();
       }
-      __syncwarp();
+      for (int j = l; j < hi; ++j) {
+        const float c = cs[j];
+        const CF s = sn[j];
+        for (int q = lane; q < r + (j + 2); q += 32) {
+          CF* M = (q < j + 2) ? H : Q;
+          const int row = (q < j + 2) ? q : q - (j + 2);
+          if (q >= j + 2 && row >= r) continue;
+          const CF h1 = M[row * r + j], h2 = M[row * r + j + 1];
+          M[row * r + j] = cadd(cscale(h1, c), cmul(h2, cconj(s)));
+          M[row * r + j + 1] = csub(cscale(h2, c), cmul(h1, s));
+        }
+        __syncwarp();
+      }
     }
     for (int q = l + lane; q <= hi; q += 32) H[q * r + q] = cadd(H[q * r + q], mu);
     __syncwarp();
