@@ -322,6 +322,8 @@ def measure_isolated(S, h, frames, t0, stream, phi, n, steps=8):
     out["gram_row"]["autotune_us"] = tuned_us
     out["gram_row"]["note"] = "each launch after a sdmd_modes (serial push + modes steps)"
     out["phi"]["GB/s"] = ((M_WIN - 1) * n + n * R_MODES * 8) / (out["phi"]["us"] * 1e-6) / 1e9
+    # the last eigensolver launch's phase clocks (SM cycles, in thousands)
+    out["modes_small_f64"]["phase_kcycles"] = {k: v // 1000 for k, v in S.sdmd_modes_phase_cycles(h, sh).items()}
     out["serial_step_us"] = sum(out[k]["us"] for k in ("gram_row", "phi", "modes_small_f64", "ingest_copy"))
     # streaming background subtraction of the newest frame (Algorithm 3):
     # background column and foreground x_t - background, one pass over X'
