@@ -430,8 +430,9 @@ def measure_catchup(S, h, frames, t0, stream, n, k=8, reps=3):
 
 def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
     """FP32 window shaped like the precision-sweep workload (n = 2^22, m = 256):
-    k frames appended with one BF16x3 tensor-core sdmd_push_batch against k
-    FP32 sdmd_push calls, the BF16x3 rebuild against the FP32 row passes, and
+    k frames appended with one sdmd_push_batch under SDMD_OPT_F32_BF16X3 (k <= 16:
+    one CUDA-core pass with FP32 products; larger k: BF16x3 on the tensor cores)
+    against k FP32 sdmd_push calls, the BF16x3 rebuild against the FP32 row passes, and
     the BF16x3 error of the k new rows on sampled entries against FP64 dot
     products of the same FP32 frames."""
     import torch
@@ -484,25 +485,28 @@ def measure_bf16x3(S, dev, stream, n=1 << 22, m=256, ks=(8, 64), reps=3):
                     src[0] += 1
                     S.sdmd_push_batch(h, k, frames[j:j + k], n, sh)
                 msb = timed(batch)
-                out["%s_push_batch_k%d" % (name, k)] = {"ms": msb, "snapshots_per_s": k / (msb * 1e-3),
-                                                         "window_GB/s": m * n * 4 / (msb * 1e-3) / 1e9,
-                                                         "vs_fp32_push": (k / msb) / (1.0 / ms1)}
-            # error of the newest k rows (last batch) on sampled entries
-            k = ks[-1]
-            stream.synchronize()
-            S.sdmd_gram(h, G, sh)
-            stream.synchronize()
-            j = m + ((src[0] - 1) * k) % (kmax * reps)   # the last batch: the k newest snapshots
-            Wh = frames[j:j + k][::4].cpu().numpy().astype(np.float64)   # exact FP32 values
-            ref = Wh @ Wh.T
-            bnd = np.abs(Wh) @ np.abs(Wh).T
-            sel = np.arange(m - k, m, 4)
-            got = G.cpu().numpy()[np.ix_(sel, sel)]
-            out["%s_sampled_error" % name] = {
-                "max_abs_err_over_sum_abs_products": float((np.abs(got - ref) / bnd).max()),
-                "rel_frobenius": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-                "entries": int(sel.size ** 2), "bound": bound,
-                "reference": "FP64 dot products of the same FP32 frames on the host (numpy)"}
+                ent = {"ms": msb, "snapshots_per_s": k / (msb * 1e-3),
+                       "window_GB/s": m * n * 4 / (msb * 1e-3) / 1e9, "vs_fp32_push": (k / msb) / (1.0 / ms1),
+                       "path": ("CUDA cores, FP32 products (k <= 16)" if k <= 16 else
+                                "tensor cores, %s split" % name)}
+                ent["frac_of_copy_peak"] = ent["window_GB/s"] / measured_peaks()[0]
+                # error of the k newest rows (the last batch) on sampled entries
+                stream.synchronize()
+                S.sdmd_gram(h, G, sh)
+                stream.synchronize()
+                j = m + ((src[0] - 1) * k) % (kmax * reps)
+                step = 4 if k > 16 else 1
+                Wh = frames[j:j + k][::step].cpu().numpy().astype(np.float64)   # exact FP32 values
+                ref = Wh @ Wh.T
+                bnd = np.abs(Wh) @ np.abs(Wh).T
+                sel = np.arange(m - k, m, step)
+                got = G.cpu().numpy()[np.ix_(sel, sel)]
+                ent["sampled_error"] = {
+                    "max_abs_err_over_sum_abs_products": float((np.abs(got - ref) / bnd).max()),
+                    "rel_frobenius": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+                    "entries": int(sel.size ** 2), "bound": bound,
+                    "reference": "FP64 dot products of the same FP32 frames on the host (numpy)"}
+                out["%s_push_batch_k%d" % (name, k)] = ent
         out["per_kappa"] = bf16x3_kappa_sweep(S, h, dev, stream, n, m)
         S.sdmd_set_option(h, S.SDMD_OPT_F32_BF16X3, 1)
         msr = timed(lambda: S.sdmd_rebuild(h, sh), r=2)

@@ -158,7 +158,9 @@ SDMD_API int sdmd_push_sparse(sdmd_t h, int32_t nnz, const int32_t *idx, const v
  * up to 127 snapshots; larger windows in groups of 64 target snapshots, each
  * paired with the older ones in blocks of up to 127 - 64 rows. FP32 windows with SDMD_OPT_F32_BF16X3 = 1: the
  * tensor cores in BF16x3 split precision, one pass per block of 64 target
- * columns (|G_ij - <x_i, x_j>| <= 1e-6 sum_p |x_ip x_jp|). Otherwise one
+ * columns (|G_ij - <x_i, x_j>| <= 1e-6 sum_p |x_ip x_jp|); windows of at
+ * most 16 snapshots in one CUDA-core pass with FP32 products (the same
+ * bound, as for sdmd_push_batch). Otherwise one
  * Gram-row pass per resident snapshot, in time order, so every entry is
  * computed with the same reduction as when it was streamed: the result
  * equals the streamed G bit for bit (c passes).
@@ -174,10 +176,13 @@ SDMD_API int sdmd_rebuild(sdmd_t h, void *stream);
  * rows and columns of G on the tensor cores (exact int64; one pass over a
  * window of up to 127 snapshots, else per group of 64 new snapshots about
  * one pass per 127 - (group size) older ones) instead of k passes; FP32
- * windows with SDMD_OPT_F32_BF16X3 = 1 and k >= 2: the k new rows and columns
- * in BF16x3 on the tensor cores, one pass over the window per 64 new
- * snapshots (equal to k pushes within the BF16x3 bound given at
- * sdmd_rebuild); other handles: k sdmd_push calls. SDMD_ERR_ARG for a bad k,
+ * windows with SDMD_OPT_F32_BF16X3 = 1 (or 2) and k >= 2: the k new rows and
+ * columns in one pass over the window -- for k <= 16 on the CUDA cores (FP32
+ * products accumulated in FP32 per 64 positions, compensated sums, FP64 over
+ * CTAs: the pass is bound by the window's reads), for larger k in BF16x3 on
+ * the tensor cores, one pass per 64 new snapshots -- equal to k pushes within
+ * the bound given at sdmd_rebuild; other handles: k sdmd_push calls.
+ * SDMD_ERR_ARG for a bad k,
  * ld or pointer.
  */
 SDMD_API int sdmd_push_batch(sdmd_t h, int32_t k, const void *X, int64_t ld, void *stream);
@@ -440,7 +445,11 @@ enum {
                                64 positions, compensated sums; bound
                                1e-6 sum_p |x_ip x_jp|); 2: the same with two
                                bf16 terms and the three products with
-                               i + j <= 1 (about 2^-16 per product) */
+                               i + j <= 1 (about 2^-16 per product). Either
+                               value runs catch-ups of at most 16 snapshots
+                               (and rebuilds of windows of at most 16) on the
+                               CUDA cores with FP32 products instead, within
+                               the three-term bound */
     ,
     SDMD_OPT_F32_FP64 = 4   /* 0 (default): Gram rows of FP32 windows with FP32
                                products and FP64 sums; 1: FP64 products (exact

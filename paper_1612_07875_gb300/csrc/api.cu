@@ -687,11 +687,28 @@ int ensure_gram_full_scratch(sdmd_s* h) {
   return SDMD_OK;
 }
 
-// The k newest of the c resident FP32 snapshots against the window, BF16x3
-// on the tensor cores (k = c: the whole Gram).
+// The k newest of the c resident FP32 snapshots against the window (k = c:
+// the whole Gram): up to 16 of them in one pass on the CUDA cores (FP32
+// products; the pass is bound by the window's reads), more in BF16x3 on the
+// tensor cores.
 int gram_f32_tensor(sdmd_s* h, int c, int k, cudaStream_t st) {
   const int rc0 = ensure_gram_full_scratch(h);
   if (rc0 != SDMD_OK) return rc0;
+  if (k <= kGramF32SimtMaxTargets && c <= SDMD_MAX_M) {
+    GramF32SimtArgs sa;
+    sa.ring = h->ring;
+    sa.slot_bytes = h->slot_bytes;
+    sa.n = h->n;
+    sa.m = h->cap;
+    sa.start = oldest_slot(h);
+    sa.c = c;
+    sa.k = k;
+    sa.partials = reinterpret_cast<float2*>(h->gf_partials);
+    sa.G = static_cast<double*>(h->G);
+    TraceScope ts(h, SDMD_K_GRAM_ROW, st);
+    CK(launch_gram_f32_simt(sa, h->num_sms, st));
+    return SDMD_OK;
+  }
   GramF32Args ga;
   ga.ring = h->ring;
   ga.slot_bytes = h->slot_bytes;

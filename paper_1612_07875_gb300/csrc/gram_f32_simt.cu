@@ -1,0 +1,189 @@
+// The multi-column catch-up of FP32 windows for a few new snapshots (Sec. 3.1,
+// Eq. 12a-b for k new columns at once; the paper's future-work multi-column
+// update): G[i][t] = <x_i, x_t> for the k <= 16 newest snapshots t against all
+// c <= 256 window snapshots i, in one pass over the window.
+//
+// Why CUDA cores. Per window element the pass does k multiply-adds (8 for the
+// usual catch-up of 8 frames) against 4 bytes read: 2 FMA per byte, about 14
+// TFMA/s at the copy bandwidth, a fraction of the FP32 rate. The work is
+// bound by the window's reads, not by arithmetic, so it stays a plain
+// tall-skinny product on the FP32 pipes; the tensor-core BF16x3 pass
+// (gram_f32_tc.cu) is kept for larger k and for the full rebuild.
+//
+// Precision: FP32 products, accumulated in FP32 over runs of 64 positions,
+// each run added to a compensated (hi, lo) pair per (row, target) with an
+// error-free two-sum; the per-CTA pairs are added in FP64 in CTA order. The
+// error is that of the BF16x3 pass or below: |G_ij - <x_i, x_j>| <= 1e-6
+// sum_p |x_ip x_jp|. Chunks go to CTAs statically (chunk b, b + grid, ...),
+// so the result is the same on every run.
+//
+// Layout. A CTA of 256 threads takes 64-position chunks b, b + grid, ... (at
+// any moment the CTAs read neighbouring pieces of every row, which HBM sees
+// as one stream per row); a chunk of every window row (256 bytes, in time
+// order) is copied with cp.async into one of three stages (rows padded to 272
+// bytes: thread r's 16-byte reads of row r fall in distinct banks). The k
+// targets are the last k rows of the same stage. Thread r owns window row r:
+// per 4 positions one 16-byte read of its row, k broadcast reads of the
+// target rows, 4k FMAs. A warp's copy instruction moves 512 contiguous bytes
+// (two rows). Measured and dropped: two threads per row (each half of the
+// targets: no faster at k = 8, slower at k = 16) and contiguous chunk runs per
+// CTA with L2 bulk prefetch (0.44 instead of 0.59 of the copy peak at k = 8).
+// The tail chunk (n not a multiple of 64) is summed with both factors masked,
+// since the ring's row padding past n holds no data.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "df64.cuh"
+#include "sdmd_internal.cuh"
+#include "tc_util.cuh"
+
+namespace sdmd {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kSRows = 256;                            // window rows (at most)
+constexpr int kSThreads = kSRows;                      // one window row per thread
+constexpr int kSPos = 64;                              // positions per chunk (= FP32 run)
+constexpr int kSStages = 3;
+constexpr int kSRowFloats = kSPos + 4;                 // 272-byte rows in a stage
+constexpr int kSStageFloats = kSRows * kSRowFloats;
+constexpr int kSSmem = kSStages * kSStageFloats * 4;   // 208,896 B
+constexpr int kSRowsPerPass = 2 * kSThreads / 32;      // rows copied per pass of all warps
+constexpr int kSPasses = kSRows / kSRowsPerPass;       // 16
+
+// kT: targets padded (8 or 16)
+template <int kT>
+__global__ void __launch_bounds__(kSThreads, 1) gram_f32_simt_kernel(GramF32SimtArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = a.c, k = a.k, t0 = c - k;
+  // this CTA's chunks: b, b + grid, ...
+  const int64_t nch = (a.n + kSPos - 1) / kSPos;
+  const int64_t mine = (nch > (int64_t)blockIdx.x) ? (nch - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  // the rows this thread copies: 2 warp + (lane >> 4) + 16 q, 16-byte piece lane & 15
+  const uint8_t* rowp[kSPasses];
+#pragma unroll
+  for (int q = 0; q < kSPasses; ++q) {
+    const int r = 2 * warp + (lane >> 4) + kSRowsPerPass * q;
+    rowp[q] = (r < c) ? a.ring + (int64_t)((a.start + r) % a.m) * a.slot_bytes + 16 * (lane & 15) : nullptr;
+  }
+  const unsigned sm0 = smem_u32(sm);
+  auto issue = [&](int64_t it) {
+    if (it < mine) {
+      const int64_t boff = (blockIdx.x + it * (int64_t)gridDim.x) * (kSPos * 4);
+      const unsigned st = sm0 + (unsigned)((it % kSStages) * kSStageFloats * 4);
+#pragma unroll
+      for (int q = 0; q < kSPasses; ++q) {
+        const int r = 2 * warp + (lane >> 4) + kSRowsPerPass * q;
+        if (r < c) cp_async16(st + (unsigned)((r * kSRowFloats + 4 * (lane & 15)) * 4), rowp[q] + boff);
+      }
+    }
+    cp_async_commit();   // one group per chunk, empty past the end
+  };
+
+  float hi[kT], lo[kT];
+#pragma unroll
+  for (int j = 0; j < kT; ++j) hi[j] = lo[j] = 0.f;
+  for (int s = 0; s < kSStages - 1; ++s) issue(s);
+  for (int64_t it = 0; it < mine; ++it) {
+    cp_async_wait<kSStages - 2>();   // this thread's copies of chunk `it` have landed
+    __syncthreads();                 // ... everyone's; and chunk it-1 is summed (its stage is free)
+    issue(it + kSStages - 1);
+    const float* st = sm + (it % kSStages) * kSStageFloats;
+    const int64_t p0 = (blockIdx.x + it * (int64_t)gridDim.x) * kSPos;
+    if (tid < c) {
+      const float* wr = st + tid * kSRowFloats;
+      const float* tr = st + t0 * kSRowFloats;
+      float acc[kT];
+#pragma unroll
+      for (int j = 0; j < kT; ++j) acc[j] = 0.f;
+      if (p0 + kSPos <= a.n) {
+#pragma unroll 4
+        for (int q = 0; q < kSPos; q += 4) {
+          const float4 w = *reinterpret_cast<const float4*>(wr + q);
+#pragma unroll
+          for (int j = 0; j < kT; ++j) {
+            if (j < k) {
+              const float4 t = *reinterpret_cast<const float4*>(tr + j * kSRowFloats + q);
+              acc[j] = fmaf(w.x, t.x, acc[j]);
+              acc[j] = fmaf(w.y, t.y, acc[j]);
+              acc[j] = fmaf(w.z, t.z, acc[j]);
+              acc[j] = fmaf(w.w, t.w, acc[j]);
+            }
+          }
+        }
+      } else {   // tail chunk: positions past n hold no data (mask both factors)
+        const int nv = (int)(a.n - p0);
+        for (int q = 0; q < nv; ++q) {
+          const float w = wr[q];
+#pragma unroll
+          for (int j = 0; j < kT; ++j)
+            if (j < k) acc[j] = fmaf(w, tr[j * kSRowFloats + q], acc[j]);
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kT; ++j) {   // error-free two-sum into the compensated pair
+        const dd sm2 = two_sum(hi[j], acc[j]);
+        hi[j] = sm2.hi;
+        lo[j] += sm2.lo;
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (tid < c) {
+#pragma unroll
+    for (int j = 0; j < kT; ++j)
+      if (j < k) a.partials[((int64_t)blockIdx.x * kSRows + tid) * kGramF32SimtMaxTargets + j] = {hi[j], lo[j]};
+  }
+}
+
+// G's entries from the per-CTA pairs, FP64 in CTA order: block i = window row
+// i, thread j = target j; a pair of targets is written once (from the row of
+// the later one), both G[i][t] and G[t][i] in physical slots.
+__global__ void gram_f32_simt_finish_kernel(GramF32SimtArgs a, int ctas) {
+  const int i = blockIdx.x, t0 = a.c - a.k;
+  const int pi = (a.start + i) % a.m;
+  for (int j = threadIdx.x; j < a.k; j += blockDim.x) {
+    if (i >= t0 && t0 + j > i) continue;
+    double g = 0.0;
+    for (int b = 0; b < ctas; ++b) {
+      const float2 v = a.partials[((int64_t)b * kSRows + i) * kGramF32SimtMaxTargets + j];
+      g += (double)v.x + (double)v.y;
+    }
+    const int pj = (a.start + t0 + j) % a.m;
+    a.G[(int64_t)pi * a.m + pj] = g;
+    a.G[(int64_t)pj * a.m + pi] = g;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_gram_f32_simt(const GramF32SimtArgs& a, int num_sms, cudaStream_t st) {
+  if (a.c < 1 || a.c > kSRows || a.k < 1 || a.k > kGramF32SimtMaxTargets || a.k > a.c || a.n < 1)
+    return cudaErrorNotSupported;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(gram_f32_simt_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gram_f32_simt_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int64_t nch = (a.n + kSPos - 1) / kSPos;
+  int64_t ctas = (num_sms < kGramF32MaxCtas) ? num_sms : kGramF32MaxCtas;
+  if (ctas > nch) ctas = nch;
+  if (ctas < 1) ctas = 1;
+  if (a.k <= 8)
+    gram_f32_simt_kernel<8><<<(unsigned)ctas, kSThreads, kSSmem, st>>>(a);
+  else
+    gram_f32_simt_kernel<16><<<(unsigned)ctas, kSThreads, kSSmem, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_f32_simt_finish_kernel<<<a.c, 32, 0, st>>>(a, (int)ctas);
+  return cudaGetLastError();
+}
+
+}  // namespace sdmd

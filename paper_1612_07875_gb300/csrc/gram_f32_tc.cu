@@ -100,9 +100,6 @@ struct F32Layout {
   static constexpr int kTmem = kStk ? 512 : 256;
 };
 
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
-}
 
 __device__ __forceinline__ void raise_timeout(int* status, volatile int* stop) {
   atomicOr(status, kDevTimeout);

@@ -87,9 +87,6 @@ struct FullShared {
 
 constexpr int kSmemBytes = kTiles * kTileBytes + kStages * kStageBytes + (int)sizeof(FullShared);
 
-__device__ __forceinline__ void bulk_prefetch_l2(const void* src, unsigned bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(bytes) : "memory");
-}
 
 // 16 pixels -> 2 x 8 centred fp16 (x - 128): fp16 0x64bb = 1024 + b, minus 1152
 __device__ __forceinline__ unsigned f16x2_centred(unsigned w, unsigned sel) {

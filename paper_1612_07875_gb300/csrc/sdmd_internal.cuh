@@ -88,6 +88,22 @@ constexpr int kGramF32MaxTargets = 64;
 cudaError_t launch_gram_f32_tc(const GramF32Args& base, int c, int k, int num_sms, int* launches, cudaStream_t st);
 int gram_f32_tc_ctas(int64_t n, int num_sms);
 
+// The k newest of c resident FP32 snapshots (k <= 16, c <= 256) against the
+// whole window on the CUDA cores: FP32 products, 64-position FP32 runs,
+// compensated sums, FP64 over CTAs (gram_f32_simt.cu).
+struct GramF32SimtArgs {
+  const uint8_t* ring;
+  int64_t slot_bytes;
+  int64_t n;
+  int32_t m;             // ring modulus (G is m x m doubles, physical slots)
+  int32_t start;         // physical slot of window time index 0 (the oldest)
+  int32_t c, k;          // rows: time indices 0..c-1; targets: the last k
+  float2* partials;      // [kGramF32MaxCtas][256][16] per-CTA (hi, lo) sums
+  double* G;
+};
+constexpr int kGramF32SimtMaxTargets = 16;
+cudaError_t launch_gram_f32_simt(const GramF32SimtArgs& a, int num_sms, cudaStream_t st);
+
 // One snapshot's Gram row inside a batched launch (fields as in GramRowArgs).
 struct RowJob {
   const uint8_t* ring;

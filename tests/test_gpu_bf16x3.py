@@ -1,6 +1,8 @@
 """BF16x3 split-precision Gram of FP32 windows on the tensor cores
 (SDMD_OPT_F32_BF16X3): sdmd_rebuild and the multi-column catch-up
 sdmd_push_batch, against the FP64 oracle Gram of the same FP32 snapshots.
+Catch-ups of at most 16 snapshots (and rebuilds of windows of at most 16)
+take the CUDA-core pass with FP32 products under the same option and bound.
 
 Bound (from the arithmetic: dropped split products and remainders below
 2^-22 |x y|, about four full-magnitude FP32 roundings of the accumulator per
@@ -79,7 +81,9 @@ def test_rebuild_bf16x3_within_bound(cuda_device, n, m, data):
 
 @pytest.mark.parametrize("n,m,pre,k", [(70001, 16, 0, 5), (70001, 16, 20, 2), ((1 << 19) + 5, 100, 100, 8),
                                        ((1 << 19) + 5, 100, 37, 64), ((1 << 18) + 3, 256, 256, 65),
-                                       ((1 << 18) + 3, 256, 10, 200), (3000, 128, 128, 128)])
+                                       ((1 << 18) + 3, 256, 10, 200), (3000, 128, 128, 128),
+                                       # k <= 16: one CUDA-core pass with FP32 products
+                                       (70001, 256, 256, 16), ((1 << 18) + 3, 200, 150, 9), (100, 40, 3, 16)])
 def test_push_batch_bf16x3_within_bound(cuda_device, n, m, pre, k):
     X = _frames(n, pre + k, seed=3 * n + k)
     h = S.sdmd_create(n, m, S.SDMD_F32)
