@@ -49,11 +49,11 @@ constexpr int kSPos = 64;                              // positions per chunk (=
 constexpr int kSStages = 3;
 constexpr int kSRowFloats = kSPos + 4;                 // 272-byte rows in a stage
 constexpr int kSStageFloats = kSRows * kSRowFloats;
-constexpr int kSSmem = kSStages * kSStageFloats * 4;   // 208,896 B
+constexpr int kSSmem = (kSStages * kSStageFloats + kSRowFloats) * 4;   // stages + a zero row: 209,168 B
 constexpr int kSRowsPerPass = 2 * kSThreads / 32;      // rows copied per pass of all warps
 constexpr int kSPasses = kSRows / kSRowsPerPass;       // 16
 
-// kT: targets padded (8 or 16)
+// kT: targets padded (4, 8 or 16)
 template <int kT>
 __global__ void __launch_bounds__(kSThreads, 1) gram_f32_simt_kernel(GramF32SimtArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -84,6 +84,9 @@ __global__ void __launch_bounds__(kSThreads, 1) gram_f32_simt_kernel(GramF32Simt
     cp_async_commit();   // one group per chunk, empty past the end
   };
 
+  // targets past k read a zero row (no per-target guards in the inner loop)
+  float* zrow = sm + kSStages * kSStageFloats;
+  for (int q = tid; q < kSRowFloats; q += kSThreads) zrow[q] = 0.f;   // visible after the loop's first barrier
   float hi[kT], lo[kT];
 #pragma unroll
   for (int j = 0; j < kT; ++j) hi[j] = lo[j] = 0.f;
@@ -96,7 +99,9 @@ __global__ void __launch_bounds__(kSThreads, 1) gram_f32_simt_kernel(GramF32Simt
     const int64_t p0 = (blockIdx.x + it * (int64_t)gridDim.x) * kSPos;
     if (tid < c) {
       const float* wr = st + tid * kSRowFloats;
-      const float* tr = st + t0 * kSRowFloats;
+      const float* tj[kT];
+#pragma unroll
+      for (int j = 0; j < kT; ++j) tj[j] = (j < k) ? st + (t0 + j) * kSRowFloats : zrow;
       float acc[kT];
 #pragma unroll
       for (int j = 0; j < kT; ++j) acc[j] = 0.f;
@@ -106,13 +111,11 @@ __global__ void __launch_bounds__(kSThreads, 1) gram_f32_simt_kernel(GramF32Simt
           const float4 w = *reinterpret_cast<const float4*>(wr + q);
 #pragma unroll
           for (int j = 0; j < kT; ++j) {
-            if (j < k) {
-              const float4 t = *reinterpret_cast<const float4*>(tr + j * kSRowFloats + q);
-              acc[j] = fmaf(w.x, t.x, acc[j]);
-              acc[j] = fmaf(w.y, t.y, acc[j]);
-              acc[j] = fmaf(w.z, t.z, acc[j]);
-              acc[j] = fmaf(w.w, t.w, acc[j]);
-            }
+            const float4 t = *reinterpret_cast<const float4*>(tj[j] + q);
+            acc[j] = fmaf(w.x, t.x, acc[j]);
+            acc[j] = fmaf(w.y, t.y, acc[j]);
+            acc[j] = fmaf(w.z, t.z, acc[j]);
+            acc[j] = fmaf(w.w, t.w, acc[j]);
           }
         }
       } else {   // tail chunk: positions past n hold no data (mask both factors)
@@ -120,8 +123,7 @@ __global__ void __launch_bounds__(kSThreads, 1) gram_f32_simt_kernel(GramF32Simt
         for (int q = 0; q < nv; ++q) {
           const float w = wr[q];
 #pragma unroll
-          for (int j = 0; j < kT; ++j)
-            if (j < k) acc[j] = fmaf(w, tr[j * kSRowFloats + q], acc[j]);
+          for (int j = 0; j < kT; ++j) acc[j] = fmaf(w, tj[j][q], acc[j]);
         }
       }
 #pragma unroll
@@ -166,7 +168,9 @@ cudaError_t launch_gram_f32_simt(const GramF32SimtArgs& a, int num_sms, cudaStre
     return cudaErrorNotSupported;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_f32_simt_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
+    cudaError_t e = cudaFuncSetAttribute(gram_f32_simt_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(gram_f32_simt_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(gram_f32_simt_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
     if (e != cudaSuccess) return e;
@@ -176,7 +180,9 @@ cudaError_t launch_gram_f32_simt(const GramF32SimtArgs& a, int num_sms, cudaStre
   int64_t ctas = (num_sms < kGramF32MaxCtas) ? num_sms : kGramF32MaxCtas;
   if (ctas > nch) ctas = nch;
   if (ctas < 1) ctas = 1;
-  if (a.k <= 8)
+  if (a.k <= 4)
+    gram_f32_simt_kernel<4><<<(unsigned)ctas, kSThreads, kSSmem, st>>>(a);
+  else if (a.k <= 8)
     gram_f32_simt_kernel<8><<<(unsigned)ctas, kSThreads, kSSmem, st>>>(a);
   else
     gram_f32_simt_kernel<16><<<(unsigned)ctas, kSThreads, kSSmem, st>>>(a);
