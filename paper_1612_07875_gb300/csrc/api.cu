@@ -1142,6 +1142,15 @@ int sdmd_modes(sdmd_t h, int32_t r, void* phi, void* lambda, int32_t* r_out, voi
   {
     TraceScope ts(h, SDMD_K_MODES, st);
     if (cplx) {
+      // eig of the Hermitian G_X by the real df64 solver on its 2p x 2p real
+      // embedding when that fits on chip, else the FP64 Jacobi sweeps
+      if (modes_embed_ok(c, r)) {
+        ModesArgs e = a;
+        e.embed_cx = 1;
+        e.r_req = 2 * ((r < c - 1) ? r : c - 1);
+        CK(launch_modes_small(e, st));
+        a.cx_pre = 1;
+      }
       CK(launch_modes_complex(a, st));
     } else {
       CK(launch_modes_small(a, st));

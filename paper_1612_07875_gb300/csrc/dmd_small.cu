@@ -976,7 +976,8 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   __shared__ float sh_f[4];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   WS w = carve(a.ws, L);
-  const int m = a.m, p = a.c - 1;
+  // embed_cx: the 2pc x 2pc real embedding of a complex pc x pc G_X
+  const int m = a.m, pc = a.c - 1, p = a.embed_cx ? 2 * pc : pc;
   const int rw = min(a.r_req, p);
   const SmemPlan plan = smem_plan(p, a.r_req);
   const int64_t P = plan.P;
@@ -1008,7 +1009,11 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
     for (int i = lane; i < p; i += 32) {
       const int si = (a.start + i) % m;
       int xe;
-      if (a.g_is_int) {
+      if (a.embed_cx) {   // complex G: the real diagonal (as the complex kernel scales)
+        const double g = static_cast<const double2*>(a.G)[(int64_t)((a.start + i % pc) % m) * m + (a.start + i % pc) % m].x;
+        const int bits = (__double2hiint(g) >> 20) & 0x7ff;
+        xe = (g > 0.0 && bits > 0) ? bits - 1023 : -1000;
+      } else if (a.g_is_int) {
         const long long g = static_cast<const long long*>(a.G)[(int64_t)si * m + si];
         xe = (g > 0) ? 63 - __clzll(g) : -1000;
       } else {
@@ -1024,7 +1029,17 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   }
   __syncthreads();
   const int s_exp = sh_int[0];
-  for (int idx = tid; idx < p * p; idx += kThreads) {
+  // complex G_X = B0 + i B1 embedded as [[B0, -B1], [B1, B0]] (symmetric:
+  // G_X is Hermitian, its diagonal imaginary parts taken as zero)
+  for (int idx = tid; a.embed_cx && idx < p * p; idx += kThreads) {
+    const int i = idx / p, j = idx - i * p;
+    const int bi = i >= pc, bj = j >= pc, ii = i - bi * pc, jj = j - bj * pc;
+    const double2 g = static_cast<const double2*>(a.G)[(int64_t)((a.start + ii) % m) * m + (a.start + jj) % m];
+    const double v = (bi == bj) ? g.x : ((ii == jj) ? 0.0 : (bi ? g.y : -g.y));
+    const dd gv = dd_from_double(v);
+    A[idx] = {ldexpf(gv.hi, -s_exp), ldexpf(gv.lo, -s_exp)};
+  }
+  for (int idx = tid; !a.embed_cx && idx < p * p; idx += kThreads) {
     const int i = idx / p, j = idx - i * p;
     const int si = (a.start + i) % m, sj = (a.start + j) % m, sj1 = (a.start + j + 1) % m;
     dd gx, gxy;
@@ -1179,6 +1194,44 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   }
   __syncthreads();
   if (tid == 0) w.clk[5] = clock64();
+  if (a.embed_cx) {
+    // hand the K = rw / 2 complex eigenpairs to the complex kernel: lambda_k
+    // (unscaled, FP64) at the start of its A~ array, x_k = u + i v from the
+    // pair's first Ritz vector [u; v] (unit norm) in its sorted-V array
+    double* cxb = a.ws + L.cx;
+    double* lam_h = cxb + 2 * 3 * (int64_t)pc * pc;   // A~ region
+    double* vec_h = cxb + 2 * 5 * (int64_t)pc * pc;   // sorted-V region: vector k at k pc
+    const int K = rw / 2;
+    // Missed-eigenvalue check: inverse iteration finds the eigenvectors
+    // nearest its shifts, and in a cluster below the FP32 multisection's
+    // resolution (eps32 |T|) those need not be the largest. A df64 Sturm
+    // count on T of the eigenvalues above the smallest kept Ritz value (less
+    // 1e-13 |T|) must not exceed rw; lam_h[K] = 1 accepts the handoff, 0
+    // sends the complex kernel to its Jacobi sweeps.
+    if (tid == 0) {
+      const dd x = dd_sub(lam[rw - 1], dd_make(1e-13f * tnorm));
+      const float pivmin = sh_f[3];
+      int below = 0;
+      dd q = dd_sub(d[0], x);
+      if (fabsf(q.hi) < pivmin) q = dd_make(-pivmin);
+      below += q.hi < 0.f;
+      for (int i = 1; i < p; ++i) {
+        q = dd_sub(dd_sub(d[i], x), dd_mul(dd_mul(e[i - 1], e[i - 1]), dd_recip(q)));
+        if (fabsf(q.hi) < pivmin) q = dd_make(-pivmin);
+        below += q.hi < 0.f;
+      }
+      lam_h[K] = (p - below <= rw) ? 1.0 : 0.0;
+    }
+    for (int k = tid; k < K; k += kThreads) lam_h[k] = ldexp(dd_to_double(lam[2 * k]), s_exp);
+    for (int idx = tid; idx < K * pc; idx += kThreads) {
+      const int k = idx / pc, i = idx - k * pc;
+      const dd* z = Z + (int64_t)(2 * k) * p;
+      vec_h[2 * idx] = dd_to_double(z[i]);
+      vec_h[2 * idx + 1] = dd_to_double(z[pc + i]);
+    }
+    if (tid == 0) w.clk[6] = w.clk[7] = w.clk[8] = clock64();
+    return;
+  }
 
   // ---- 5. rank, sigma, V (FP64 out), vsi = V Sigma^-1 (df64, scaled units)
   if (tid == 0) {
@@ -1470,7 +1523,9 @@ __global__ void __launch_bounds__(kCThreads, 1) modes_complex_kernel(ModesArgs a
   //         all disjoint pairs of a step at once)
   const int P2 = p + (p & 1);
   const int npairs = P2 / 2;
-  for (int sweep = 0; sweep < kJacobiMaxSweeps; ++sweep) {
+  // the handoff of the embedded solve, if it passed its missed-eigenvalue check
+  const bool pre = a.cx_pre && reinterpret_cast<const double*>(At)[min(R, p)] == 1.0;
+  for (int sweep = 0; !pre && sweep < kJacobiMaxSweeps; ++sweep) {
     double off = 0.0, tot = 0.0;
     for (int idx = tid; idx < p * p; idx += kCThreads) {
       const C64d v = Ac[idx];
@@ -1541,6 +1596,21 @@ __global__ void __launch_bounds__(kCThreads, 1) modes_complex_kernel(ModesArgs a
       }
       __syncthreads();
     }
+  }
+
+  // ---- 1'. (cx_pre, check passed) the eigenpairs handed over by the real
+  //          df64 solver of the embedding: lambda_k at the start of the A~
+  //          array, x_k in the sorted-V array; the other diagonal entries sort
+  //          last, below the rank threshold
+  if (pre) {
+    const int K = min(R, p);
+    const double* lam_h = reinterpret_cast<const double*>(At);
+    for (int idx = tid; idx < p * p; idx += kCThreads) {
+      const int i = idx / p, k = idx - i * p;
+      Vc[idx] = (k < K) ? Vo[(int64_t)k * p + i] : C64d{(i == k) ? 1.0 : 0.0, 0.0};
+    }
+    for (int i = tid; i < p; i += kCThreads) Ac[(int64_t)i * p + i].re = (i < K) ? ldexp(lam_h[i], -s_exp) : -1.0;
+    __syncthreads();
   }
 
   // ---- 2. eigenvalues (real diagonal) sorted descending, rank, sigma, V, vsi
@@ -1769,9 +1839,19 @@ __host__ __device__ ModesLayout modes_layout(int m) {
 
 int64_t modes_ws_doubles(int m) { return modes_layout(m).total; }
 
+bool modes_embed_ok(int c, int r) {
+  const int pc = c - 1, K = (r < pc) ? r : pc, p = 2 * pc;
+  const SmemPlan plan = smem_plan(p, 2 * K);
+  if (!plan.a_in_smem || !plan.rr_in_smem) return false;
+  if (plan.inv_in_smem) return true;
+  // otherwise LU + Ritz scratch and Z go to the workspace laid out for pc
+  const int64_t pp = (int64_t)pc * pc;
+  return (int64_t)plan.rr_dim * 6 * p <= 6 * pp + 64 && (int64_t)plan.rr_dim * p <= pp;
+}
+
 cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
   static size_t attr_bytes = 0;   // dynamic shared memory opted in so far
-  const SmemPlan plan = smem_plan(a.c - 1, a.r_req);
+  const SmemPlan plan = smem_plan(a.embed_cx ? 2 * (a.c - 1) : a.c - 1, a.r_req);
   const size_t bytes = (size_t)(plan.vec_units + plan.rr_units + plan.big_units + plan.inv_units) * 8;
   if (bytes > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(modes_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -172,6 +172,15 @@ struct ModesArgs {
   double* ws;           // workspace (modes_ws_doubles(m) doubles)
   int* status;          // device status word (sticky error bits)
   int* r_dev;           // kept rank (device int)
+  // Complex windows through the real df64 eigensolver: with embed_cx = 1 the
+  // real modes kernel reads G as complex128, runs its phases 0-4 on the real
+  // symmetric embedding [[Re G_X, -Im G_X], [Im G_X, Re G_X]] (2p x 2p, every
+  // eigenvalue of G_X twice) for r_req = 2K eigenpairs, and hands the K
+  // complex eigenpairs (lambda, x = u + i v from each pair's first vector
+  // [u; v]) to the complex kernel's workspace; cx_pre = 1 makes the complex
+  // kernel take them instead of running its Jacobi sweeps.
+  int32_t embed_cx = 0;
+  int32_t cx_pre = 0;
 };
 
 // Doubles of workspace needed by the modes kernel for window length m.
@@ -200,6 +209,9 @@ cudaError_t launch_modes_batch(const ModesBatch& b, cudaStream_t st);
 // The same outputs for complex windows (G complex128 Hermitian): FP64 Jacobi
 // for G_X, complex A~, W, M and amplitudes.
 cudaError_t launch_modes_complex(const ModesArgs& a, cudaStream_t st);
+// Whether a complex window of c snapshots and rank r can take the embedded
+// df64 path (its working set fits what that path may use).
+bool modes_embed_ok(int c, int r);
 
 struct PhiArgs {
   const uint8_t* ring;
