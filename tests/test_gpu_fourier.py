@@ -221,3 +221,42 @@ def test_dense_complex_phi_matches_oracle(cuda_device, n, m, r):
         assert S.sdmd_status(h) == S.SDMD_OK
     finally:
         S.sdmd_destroy(h)
+
+
+@pytest.mark.parametrize("n,m,r,noise", [(5000, 64, 5, 0.01), (4096, 64, 10, 0.01), (3000, 33, 10, 0.01),
+                                         (6000, 50, 8, 0.3)])
+def test_complex_eigensolver_paths_on_same_gram(cuda_device, n, m, r, noise):
+    # Complex windows of up to 72 snapshots take the real df64 eigensolver on
+    # the 2p x 2p real embedding of G_X; when its df64 Sturm count finds an
+    # eigenvalue above the smallest kept one that it did not return (the r
+    # requested include a noise floor below the FP32 multisection's
+    # resolution: the r = 10 cases with 6 planted modes and noise 0.01), the
+    # FP64 Jacobi runs instead. Either way: rank, sigma (1e-10 relative) and
+    # lambda (1e-9) against the oracle's LAPACK DMD of the device's own G.
+    rng = np.random.default_rng(n + m + r)
+    modes = rng.standard_normal((n, 6)) + 1j * rng.standard_normal((n, 6))
+    lamt = np.exp(1j * rng.uniform(0, 1, 6)) * rng.uniform(0.95, 1.0, 6)
+    X = np.stack([(modes * lamt ** t).sum(1) + noise * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+                  for t in range(m)]).astype(np.complex64)
+    h = S.sdmd_create(n, m, S.SDMD_C64)
+    try:
+        for t in range(m):
+            S.sdmd_push(h, torch.from_numpy(X[t].view(np.float32).reshape(n, 2)).to(cuda_device))
+        G = torch.empty(m, m, dtype=torch.complex128, device=cuda_device)
+        S.sdmd_gram(h, G)
+        lam = np.zeros(2 * r)
+        rout = np.zeros(1, dtype=np.int32)
+        S.sdmd_modes(h, r, None, lam, rout)
+        sig = np.zeros(r)
+        S.sdmd_svd(h, r, sig, None)
+        torch.cuda.synchronize()
+        assert S.sdmd_status(h) == S.SDMD_OK
+        Gn = G.cpu().numpy()
+        ref = oracle.dmd_from_gram(Gn[:-1, :-1], Gn[:-1, 1:], r)
+        rk = int(rout[0])
+        assert rk == ref.r
+        assert np.allclose(sig[:rk], ref.sigma, rtol=1e-10, atol=0)
+        err, _ = match_eigs((lam[0::2] + 1j * lam[1::2])[:rk], ref.lam)
+        assert err <= 1e-9, err
+    finally:
+        S.sdmd_destroy(h)
