@@ -389,6 +389,21 @@ __device__ int sturm32(const float* d, const float* e2, int p, float x, float pi
   return cnt;
 }
 
+// Number of eigenvalues of the df64 tridiagonal (d, e) below x (pivots kept
+// at least pivmin away from zero): the df64 counterpart of sturm32, for the
+// missed-eigenvalue check and the df64 multisection of phase 3'.
+__device__ int sturm_below_dd(const dd* d, const dd* e, int p, dd x, float pivmin) {
+  dd q = dd_sub(d[0], x);
+  if (fabsf(q.hi) < pivmin) q = dd_make(-pivmin);
+  int below = q.hi < 0.f;
+  for (int i = 1; i < p; ++i) {
+    q = dd_sub(dd_sub(d[i], x), dd_mul(dd_mul(e[i - 1], e[i - 1]), dd_recip(q)));
+    if (fabsf(q.hi) < pivmin) q = dd_make(-pivmin);
+    below += q.hi < 0.f;
+  }
+  return below;
+}
+
 // ---------------------------------------------------------------- phase 3 --
 // LU with partial pivoting of the df64 tridiagonal T - mu I. Row i of U has
 // (1/u0, u1, u2) on columns (i, i+1, i+2) (diagonal stored as reciprocal);
@@ -1131,6 +1146,7 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   }
   __syncthreads();
   const int rwe = (rw > 0) ? sh_int[2] : 0;
+  for (int i = tid; i < rwe; i += kThreads) pv[i] = lam[i];   // the FP32 values, for phase 3'
   if (tid == 0) w.clk[3] = clock64();
 
   // ---- 3. df64 inverse iteration + Gram-Schmidt + Rayleigh-Ritz, twice:
@@ -1138,7 +1154,52 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
   //         round-0 Ritz values (df64-accurate), which converges in one or two
   //         solves even for eigenvalues much closer than eps32 * |T|
   const float tiny = fmaxf(1e-13f * tnorm, FLT_MIN);
-  for (int round = 0; round < 2; ++round) {
+  for (int round = 0; round < 3; ++round) {
+    if (round == 2) {
+      // ---- 3'. missed-eigenvalue check: inverse iteration converges to the
+      //          eigenvectors nearest its shifts, and inside a cluster below
+      //          the FP32 multisection's resolution (eps32 |T|) those need not
+      //          be the largest. A df64 Sturm count of the eigenvalues above
+      //          the smallest kept Ritz value (less 1e-13 |T|) that exceeds rw
+      //          sends the wanted eigenvalues through a df64 multisection
+      //          (warp per eigenvalue, 33 points per round, bracketed by the
+      //          FP32 value or else by Gershgorin) and one more round runs
+      //          with those shifts.
+      if (tid == 0) {
+        const int below = sturm_below_dd(d, e, p, dd_sub(lam[rw - 1], dd_make(1e-13f * tnorm)), sh_f[3]);
+        sh_int[3] = (p - below > rw) ? 1 : 0;
+      }
+      __syncthreads();
+      // the embedding of a complex window leaves a failed check to the complex
+      // kernel's FP64 Jacobi: for modes that far below lambda_1 its FP64
+      // backward error keeps A~'s eigenvalues within 1e-9, df64 does not
+      if (!sh_int[3] || a.embed_cx) break;
+      for (int i = warp; i < rwe; i += kWarps) {
+        const int target = p - 1 - i;
+        const float W = 32.f * kEps32 * tnorm + sh_f[3];
+        dd lo = dd_sub(pv[i], dd_make(W)), hi = dd_add(pv[i], dd_make(W));
+        const int cb = (lane < 2) ? sturm_below_dd(d, e, p, lane ? hi : lo, sh_f[3]) : 0;
+        const int c_lo = __shfl_sync(0xffffffffu, cb, 0), c_hi = __shfl_sync(0xffffffffu, cb, 1);
+        if (!(c_lo <= target && c_hi >= target + 1)) {
+          lo = dd_make(sh_f[0]);
+          hi = dd_make(sh_f[1]);
+        }
+        for (int rnd = 0; rnd < 12; ++rnd) {
+          const dd wd = dd_sub(hi, lo);
+          if (wd.hi <= 1e-14f * tnorm) break;
+          const dd x = dd_add(lo, dd_mul_f(wd, (float)(lane + 1) / 33.f));
+          const int cnt = sturm_below_dd(d, e, p, x, sh_f[3]);
+          const unsigned above = __ballot_sync(0xffffffffu, cnt > target);
+          const int f = above ? __ffs(above) - 1 : 32;
+          const dd xf = {__shfl_sync(0xffffffffu, x.hi, f & 31), __shfl_sync(0xffffffffu, x.lo, f & 31)};
+          const dd xp = {__shfl_sync(0xffffffffu, x.hi, (f + 31) & 31), __shfl_sync(0xffffffffu, x.lo, (f + 31) & 31)};
+          if (f < 32) hi = xf;
+          if (f > 0) lo = xp;
+        }
+        if (lane == 0) lam[i] = dd_scale(dd_add(lo, hi), 0.5f);
+      }
+      __syncthreads();
+    }
     const float sep = (round == 0) ? 2.f * kEps32 * tnorm : 1e-12f * tnorm;
     // vector i on lane i / 8 of warp i % 8: the factorisations and solves are
     // serial recurrences, so they are spread over all warps' issue slots
@@ -1149,7 +1210,10 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
         if (fabsf(lam[q].hi - shift.hi) <= sep) shift = dd_sub(shift, dd_make(sep));
       tri_lu_dd(d, e, p, shift, tiny, u0, u0 + p, u0 + 2 * p, u0 + 3 * p, u0 + 4 * p);
     }
-    if (round == 0) {
+    // rounds 0 and 2 start from fixed pseudo-random vectors: round 1 refines
+    // round 0's, but round 2 follows a check that found an eigenvector round
+    // 1 missed, whose component in round 1's vectors is at rounding level
+    if (round != 1) {
       for (int idx = tid; idx < rwe * p; idx += kThreads) {
         const int i = idx / p, j = idx - i * p;
         Z[idx] = dd_make(1.f + 0.1f * (float)(((j + 1) * 7919 + (i + 1) * 104729) % 97) / 97.f);
@@ -1209,17 +1273,7 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
     // 1e-13 |T|) must not exceed rw; lam_h[K] = 1 accepts the handoff, 0
     // sends the complex kernel to its Jacobi sweeps.
     if (tid == 0) {
-      const dd x = dd_sub(lam[rw - 1], dd_make(1e-13f * tnorm));
-      const float pivmin = sh_f[3];
-      int below = 0;
-      dd q = dd_sub(d[0], x);
-      if (fabsf(q.hi) < pivmin) q = dd_make(-pivmin);
-      below += q.hi < 0.f;
-      for (int i = 1; i < p; ++i) {
-        q = dd_sub(dd_sub(d[i], x), dd_mul(dd_mul(e[i - 1], e[i - 1]), dd_recip(q)));
-        if (fabsf(q.hi) < pivmin) q = dd_make(-pivmin);
-        below += q.hi < 0.f;
-      }
+      const int below = sturm_below_dd(d, e, p, dd_sub(lam[rw - 1], dd_make(1e-13f * tnorm)), sh_f[3]);
       lam_h[K] = (p - below <= rw) ? 1.0 : 0.0;
     }
     for (int k = tid; k < K; k += kThreads) lam_h[k] = ldexp(dd_to_double(lam[2 * k]), s_exp);

@@ -128,6 +128,30 @@ def test_planted_fp32_noise_floor_cluster(cuda_device, seed_off, T):
         S.sdmd_destroy(h)
 
 
+@pytest.mark.parametrize("noise_var,seed_off", [(1e-8, 0), (1e-10, 2), (1e-9, 4)])
+def test_noise_floor_below_fp32_resolution(cuda_device, noise_var, seed_off):
+    # r = 10 with 5 planted modes reaches into a noise floor 1e-8 .. 1e-10 of
+    # lambda_1: above the rank threshold, below what the FP32 multisection
+    # resolves. The kept eigenvalues must still be the r largest of G_X: sigma^2
+    # within 1e-12 lambda_1 of the oracle's (the noise eigenvalues are about
+    # 1e-11 lambda_1 apart, and the df64 and LAPACK backward errors are
+    # relative to lambda_1, so sigma of a noise mode is not compared relatively).
+    ps = synth.PlantedStream(noise_var=noise_var, seed=synth.config_seed(1) + 20 + seed_off)
+    n, m, r = ps.n, 32, 10
+    h = S.sdmd_create(n, m, S.SDMD_F32)
+    so = oracle.StreamOracle(n, m, "f32")
+    try:
+        _stream(h, so, [ps.snapshot(t) for t in range(40)], cuda_device)
+        rk, lam, sig, V, _ = _modes(h, n, r, cuda_device, m)
+        G = _gram(h, m, cuda_device, False)
+        ref = oracle.dmd_from_gram(G[:-1, :-1], G[:-1, 1:], r)
+        assert rk == ref.r
+        l1 = ref.sigma[0] ** 2
+        assert np.max(np.abs(sig[:rk] ** 2 - ref.sigma ** 2)) <= 1e-12 * l1
+    finally:
+        S.sdmd_destroy(h)
+
+
 def test_ramp_up_window_not_full(cuda_device):
     ps = synth.PlantedStream(side=24, noise_var=1e-4, seed=77)
     n, m = ps.n, 32
