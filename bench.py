@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--scpu-seconds", type=float, default=3.0,
                     help="seconds of the streaming CPU Gram update (host cores)")
-    ap.add_argument("--case", choices=["bf16x3_catchup", "batched_rows", "fused_pass"], default=None,
+    ap.add_argument("--case", choices=["bf16x3_catchup", "f32_catchup", "batched_rows", "fused_pass"], default=None,
                     help="run one small fixed workload (for a profiler capture of its kernel) and exit")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served Poisson-arrival run (0 skips the serving measurement)")
@@ -1232,8 +1232,10 @@ def run_ours(args):
 def run_case(name):
     """Small fixed workloads for profiler captures of one kernel each:
     bf16x3_catchup: 128 random FP32 frames of n = 2^20 fill a window of 128,
-      then three sdmd_push_batch calls of k = 8 under SDMD_OPT_F32_BF16X3 = 1
-      (gram_f32_tc launches);
+      then three sdmd_push_batch calls of k = 32 under SDMD_OPT_F32_BF16X3 = 1
+      (gram_f32_tc launches: BF16x3 on the tensor cores, stacked B);
+    f32_catchup: the same window, three sdmd_push_batch calls of k = 8 under
+      the same option (gram_f32_simt launches: FP32 products on the CUDA cores);
     batched_rows: 24 streams of the serving mix (each window at most 200 MB)
       take 260 frames each through sdmd_push_many (gram_rows_batched launches);
     fused_pass: the HD video stream (n = 1920 x 1080 x 3 uint8, m = 100,
@@ -1245,8 +1247,8 @@ def run_case(name):
     from paper_1612_07875_gb300 import sdmd as S
     from paper_1612_07875_gb300 import synth
     dev = torch.device("cuda", 0)
-    if name == "bf16x3_catchup":
-        n, m, k = 1 << 20, 128, 8
+    if name in ("bf16x3_catchup", "f32_catchup"):
+        n, m, k = 1 << 20, 128, (32 if name == "bf16x3_catchup" else 8)
         g = torch.Generator(device=dev)
         g.manual_seed(5)
         frames = torch.randn(m + k, n, device=dev, generator=g)
