@@ -9,12 +9,33 @@
 #include <new>
 #include <string>
 #include <deque>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <vector>
 
 #include "sdmd.h"
 #include "sdmd_internal.cuh"
 
 using namespace sdmd;
+
+namespace sdmd {
+
+cudaError_t smem_optin(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> level;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& cur = level[std::make_pair(func, dev)];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
+}  // namespace sdmd
 
 // One in-flight DMD of the pipelined step (sdmd_step): its own workspace,
 // G snapshot and stream, and events ordering it against the push stream.

@@ -1904,33 +1904,24 @@ bool modes_embed_ok(int c, int r) {
 }
 
 cudaError_t launch_modes_small(const ModesArgs& a, cudaStream_t st) {
-  static size_t attr_bytes = 0;   // dynamic shared memory opted in so far
   const SmemPlan plan = smem_plan(a.embed_cx ? 2 * (a.c - 1) : a.c - 1, a.r_req);
   const size_t bytes = (size_t)(plan.vec_units + plan.rr_units + plan.big_units + plan.inv_units) * 8;
-  if (bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(modes_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e != cudaSuccess) return e;
-    attr_bytes = bytes;
-  }
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(modes_small_kernel), bytes);
+  if (e != cudaSuccess) return e;
   modes_small_kernel<<<1, kThreads, bytes, st>>>(a, modes_layout(a.ws_m));
   return cudaGetLastError();
 }
 
 cudaError_t launch_modes_batch(const ModesBatch& b, cudaStream_t st) {
   if (b.count < 1 || b.count > kMaxModesJobs) return cudaErrorInvalidValue;
-  static size_t attr_bytes = 0;
   size_t bytes = 0;
   for (int i = 0; i < b.count; ++i) {
     const SmemPlan plan = smem_plan(b.job[i].c - 1, b.job[i].r_req);
     const size_t jb = (size_t)(plan.vec_units + plan.rr_units + plan.big_units + plan.inv_units) * 8;
     if (jb > bytes) bytes = jb;
   }
-  if (bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(modes_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return e;
-    attr_bytes = bytes;
-  }
+  const cudaError_t e = smem_optin(reinterpret_cast<const void*>(modes_batch_kernel), bytes);
+  if (e != cudaSuccess) return e;
   modes_batch_kernel<<<b.count, kThreads, bytes, st>>>(b);
   return cudaGetLastError();
 }

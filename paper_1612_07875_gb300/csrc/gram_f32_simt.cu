@@ -169,15 +169,11 @@ __global__ void gram_f32_simt_finish_kernel(GramF32SimtArgs a, int ctas) {
 cudaError_t launch_gram_f32_simt(const GramF32SimtArgs& a, int num_sms, cudaStream_t st) {
   if (a.c < 1 || a.c > kSRows || a.k < 1 || a.k > kGramF32SimtMaxTargets || a.k > a.c || a.n < 1)
     return cudaErrorNotSupported;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_f32_simt_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_f32_simt_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_f32_simt_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSSmem);
+  {
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(gram_f32_simt_kernel<4>), kSSmem);
+    if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(gram_f32_simt_kernel<8>), kSSmem);
+    if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(gram_f32_simt_kernel<16>), kSSmem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int64_t nch = (a.n + kSPos - 1) / kSPos;
   int64_t ctas = (num_sms < kGramF32MaxCtas) ? num_sms : kGramF32MaxCtas;

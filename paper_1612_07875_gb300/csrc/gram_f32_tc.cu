@@ -495,15 +495,10 @@ int gram_f32_tc_ctas(int64_t n, int num_sms) {
 cudaError_t launch_gram_f32_tc(const GramF32Args& base, int c, int k, int num_sms, int* launches,
                                cudaStream_t st) {
   if (c < 1 || k < 1 || k > c) return cudaErrorNotSupported;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_f32_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         F32Layout<false>::kBytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_f32_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               F32Layout<true>::kBytes);
+  {
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(gram_f32_tc_kernel<false>), F32Layout<false>::kBytes);
+    if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(gram_f32_tc_kernel<true>), F32Layout<true>::kBytes);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const int ctas = gram_f32_tc_ctas(base.n, num_sms);
   int count = 0;

@@ -448,11 +448,9 @@ __global__ void gram_full_finish_kernel(GramFullArgs a, int ctas) {
 cudaError_t launch_gram_full_tc(const GramFullArgs& base, int* ctas_out, cudaStream_t st) {
   const int c = base.c, k = base.k;
   if (c < 1 || c > SDMD_MAX_M || k < 1 || k > c) return cudaErrorNotSupported;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_full_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(gram_full_tc_kernel), kSmemBytes);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

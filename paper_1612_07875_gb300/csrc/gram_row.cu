@@ -658,18 +658,13 @@ void gram_row_schedule_k(int64_t slot_bytes, int num_sms, int chunks_per_sm, int
 }
 
 cudaError_t launch_gram_row(int dtype, bool f64_ref, const GramRowArgs& a, cudaStream_t st) {
-  static bool attr = false;
   const size_t smem = sizeof(Smem);
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeU8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeC64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(gram_row_bulk_kernel<kModeF64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(gram_row_bulk_kernel<kModeU8>), smem);
+    if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(gram_row_bulk_kernel<kModeF32>), smem);
+    if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(gram_row_bulk_kernel<kModeC64>), smem);
+    if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(gram_row_bulk_kernel<kModeF64>), smem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -687,13 +682,10 @@ cudaError_t launch_gram_row(int dtype, bool f64_ref, const GramRowArgs& a, cudaS
 }
 
 cudaError_t batched_kernel_config(const BatchArgs& a, cudaKernelNodeParams* p) {
-  static bool attr = false;
   const size_t smem = sizeof(BatchSmem);
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(gram_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(gram_rows_batched_kernel), smem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -709,13 +701,10 @@ cudaError_t batched_kernel_config(const BatchArgs& a, cudaKernelNodeParams* p) {
 }
 
 cudaError_t launch_gram_rows_batched(const BatchArgs& a, cudaStream_t st) {
-  static bool attr = false;
   const size_t smem = sizeof(BatchSmem);
-  if (!attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(gram_rows_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(gram_rows_batched_kernel), smem);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -187,12 +187,9 @@ cudaError_t launch_t(const PhiArgs& a, cudaStream_t st, int sms) {
   constexpr int kPos = PhiTraits<T>::kPos;
   constexpr int kSlots = PhiTraits<T>::kSlots;
   const size_t smem = 2 * kSlots * kPos * sizeof(T) + (size_t)a.p * (kReal ? KT : 2 * KT) * sizeof(float);
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(phi_tile_kernel<T, KT, kReal>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(phi_tile_kernel<T, KT, kReal>), smem);
     if (e != cudaSuccess) return e;
-    attr = smem;
   }
   const int64_t ntiles = (a.n + kPos - 1) / kPos;
   const int ky = (a.r + KT - 1) / KT;

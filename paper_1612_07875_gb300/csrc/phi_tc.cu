@@ -551,12 +551,9 @@ __global__ void __launch_bounds__(kMaxThreads, 1) phi_tc_u8_kernel(PhiArgs a, in
 
 template <int kIpt, int kMd, int kB>
 cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int stages, size_t smem, int* ctas) {
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaError_t e =
-        cudaFuncSetAttribute(phi_tc_u8_kernel<kIpt, kMd, kB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(phi_tc_u8_kernel<kIpt, kMd, kB>), smem);
     if (e != cudaSuccess) return e;
-    attr = smem;
   }
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);

@@ -148,6 +148,11 @@ struct BatchPlan {
 int push_many_plan(sdmd_t const* hs, const void* const* xs, int count, cudaStream_t st, BatchPlan* plan);
 int push_many_finish(sdmd_t const* hs, int count, int copied, bool launched, cudaStream_t st);
 
+// Raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device. The attribute belongs to a device, so the level reached is
+// kept per (kernel, device); thread-safe.
+cudaError_t smem_optin(const void* func, size_t bytes);
+
 // Device bytes of a depth-1 dense handle (admission by footprint).
 int64_t handle_device_bytes(int64_t n, int32_t m, int32_t dtype, int num_sms);
 
