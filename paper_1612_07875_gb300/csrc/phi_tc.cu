@@ -565,6 +565,10 @@ cudaError_t launch_cfg(const PhiArgs& a, cudaStream_t st, int kpad, int n_a, int
   if (bx > ntiles) bx = ntiles;
   if (bx < 1) bx = 1;
   if (a.fuse && bx > kFusedMaxCtas) bx = kFusedMaxCtas;
+  // the fused pass runs beside the other frames' eigensolvers (one whole SM
+  // each, about 1.1 ms per 0.29 ms step: four at a time); leaving them their
+  // SMs measured 264 instead of 271 us per pass
+  if (a.fuse && bx > sms - kFusedReserveSms && sms - kFusedReserveSms >= 1) bx = sms - kFusedReserveSms;
   const int threads = 32 * (kConvWarp0 + kpad * kB / (4 * kIpt));
   phi_tc_u8_kernel<kIpt, kMd, kB><<<dim3((unsigned)bx, (unsigned)ky), threads, smem, st>>>(a, kpad, n_a, stages);
   if (ctas) *ctas = (int)bx;

@@ -248,6 +248,7 @@ struct PhiArgs {
 };
 // Per-CTA partial capacity of the fused Gram row (CTAs x window slots).
 constexpr int kFusedMaxCtas = 160;
+constexpr int kFusedReserveSms = 4;   // SMs the fused pass leaves to concurrent eigensolvers
 constexpr int kPhiSchedPasses = 16;                 // mode passes of 16 (r <= 256)
 constexpr int kPhiSchedWords = kPhiSchedPasses + 1;
 
