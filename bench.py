@@ -1234,8 +1234,9 @@ def run_case(name):
     bf16x3_catchup: 128 random FP32 frames of n = 2^20 fill a window of 128,
       then three sdmd_push_batch calls of k = 32 under SDMD_OPT_F32_BF16X3 = 1
       (gram_f32_tc launches: BF16x3 on the tensor cores, stacked B);
-    f32_catchup: the same window, three sdmd_push_batch calls of k = 8 under
-      the same option (gram_f32_simt launches: FP32 products on the CUDA cores);
+    f32_catchup: 256 random FP32 frames of n = 2^20 fill a window of 256, then
+      three sdmd_push_batch calls of k = 8 under the same option (gram_f32_simt
+      launches: FP32 products on the CUDA cores, two window rows per thread);
     batched_rows: 24 streams of the serving mix (each window at most 200 MB)
       take 260 frames each through sdmd_push_many (gram_rows_batched launches);
     fused_pass: the HD video stream (n = 1920 x 1080 x 3 uint8, m = 100,
@@ -1248,7 +1249,7 @@ def run_case(name):
     from paper_1612_07875_gb300 import synth
     dev = torch.device("cuda", 0)
     if name in ("bf16x3_catchup", "f32_catchup"):
-        n, m, k = 1 << 20, 128, (32 if name == "bf16x3_catchup" else 8)
+        n, m, k = (1 << 20, 128, 32) if name == "bf16x3_catchup" else (1 << 20, 256, 8)
         g = torch.Generator(device=dev)
         g.manual_seed(5)
         frames = torch.randn(m + k, n, device=dev, generator=g)

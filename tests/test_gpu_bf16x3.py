@@ -83,7 +83,9 @@ def test_rebuild_bf16x3_within_bound(cuda_device, n, m, data):
                                        ((1 << 19) + 5, 100, 37, 64), ((1 << 18) + 3, 256, 256, 65),
                                        ((1 << 18) + 3, 256, 10, 200), (3000, 128, 128, 128),
                                        # k <= 16: one CUDA-core pass with FP32 products
-                                       (70001, 256, 256, 16), ((1 << 18) + 3, 200, 150, 9), (100, 40, 3, 16)])
+                                       (70001, 256, 256, 16), ((1 << 18) + 3, 200, 150, 9), (100, 40, 3, 16),
+                                       # one row per thread up to c = 128, two above (and the k <= 4 instance)
+                                       (70001, 128, 128, 4), (70001, 129, 129, 7), ((1 << 18) + 3, 180, 177, 3)])
 def test_push_batch_bf16x3_within_bound(cuda_device, n, m, pre, k):
     X = _frames(n, pre + k, seed=3 * n + k)
     h = S.sdmd_create(n, m, S.SDMD_F32)
