@@ -99,8 +99,8 @@ SDMD_API int sdmd_create(int64_t n, int32_t m, int32_t dtype, sdmd_t *out);
  * sdmd_create_ex -- as sdmd_create, with `depth` DMD frames in flight for
  * sdmd_step (1 <= depth <= SDMD_MAX_DEPTH; 1 = no pipelining). A pipelined
  * handle keeps m + depth snapshots in its ring (so the X' of frames still
- * being decomposed is not overwritten), one workspace, G snapshot and CUDA
- * stream per frame in flight.
+ * being decomposed is not overwritten), one workspace and CUDA stream per
+ * frame in flight.
  */
 SDMD_API int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t *out);
 
@@ -292,11 +292,13 @@ SDMD_API int sdmd_modes(sdmd_t h, int32_t r, void *phi, void *lambda, int32_t *r
 /*
  * sdmd_step -- pipelined streaming DMD: push x (as sdmd_push), then compute
  * the exact DMD of the new window (as sdmd_modes) on an internal stream so
- * that it overlaps with the following pushes. The window's G is copied on
- * `stream` right after the push; the eigensolvers, Phi and the output copies
- * run on the internal stream of one of `depth` frame contexts. `stream` only
- * waits for a context when its workspace or the ring slots it reads are
- * about to be reused (depth pushes later).
+ * that it overlaps with the following pushes. The eigensolvers, Phi and the
+ * output copies run on the internal stream of one of `depth` frame contexts;
+ * the eigensolvers read the window's entries of G in place (later pushes
+ * write only their own slots' rows and columns). `stream` only waits for a
+ * context when its workspace, the ring slots it reads or their rows of G are
+ * about to be reused (depth pushes later); sdmd_rebuild waits for every
+ * context's eigensolver.
  * Results of this call (phi, lambda, r_out) are complete once `stream`
  * passes sdmd_sync, or the sdmd_step call `depth` calls later. phi must be
  * a distinct device buffer per frame in flight; lambda / r_out must be

@@ -37,15 +37,18 @@ cudaError_t smem_optin(const void* func, size_t bytes) {
 
 }  // namespace sdmd
 
-// One in-flight DMD of the pipelined step (sdmd_step): its own workspace,
-// G snapshot and stream, and events ordering it against the push stream.
+// One in-flight DMD of the pipelined step (sdmd_step): its own workspace and
+// stream, and events ordering it against the push stream. Its eigensolver
+// reads the frame's window of G in place: the pushes that follow write only
+// the rows and columns of their own slots, and a slot of the window is
+// rewritten only after the push stream has waited for the frame
+// (wait_ring_readers).
 struct PipeCtx {
   double* ws = nullptr;       // modes workspace (window m)
   int* r_dev = nullptr;
   unsigned* phi_sched = nullptr;  // Phi tile-scheduling words (zero between launches)
-  void* gsnap = nullptr;      // time-ordered c x c copy of G for this frame
   cudaStream_t st = nullptr;
-  cudaEvent_t ev_g = nullptr;     // G snapshot taken (push stream)
+  cudaEvent_t ev_g = nullptr;     // the frame's G row written (push stream)
   cudaEvent_t ev_done = nullptr;  // modes, Phi and output copies done (ctx stream, or the push
                                   // stream when Phi ran fused with a later Gram row)
   cudaEvent_t ev_modes = nullptr; // modes and output copies done (ctx stream)
@@ -314,7 +317,6 @@ void free_ctx(sdmd_s* h) {
     cudaFree(c.ws);
     cudaFree(c.r_dev);
     cudaFree(c.phi_sched);
-    cudaFree(c.gsnap);
     if (c.ev_g) cudaEventDestroy(c.ev_g);
     if (c.ev_done) cudaEventDestroy(c.ev_done);
     if (c.ev_modes) cudaEventDestroy(c.ev_modes);
@@ -355,11 +357,13 @@ inline int32_t oldest_slot(const sdmd_s* h) { return (int32_t)((h->count - resid
 int flush_pending(sdmd_s* h, cudaStream_t st);
 
 // Make `st` wait for every in-flight frame that still reads the ring slot
-// push number t (default: the next push) is about to overwrite.
+// push number t (default: the next push) is about to overwrite, or that
+// slot's row and column of G: a frame's Phi reads its pushes frame - p + 1 ..
+// frame, its eigensolver the G entries of pushes frame - p .. frame.
 int wait_ring_readers(sdmd_s* h, cudaStream_t st, int64_t t = -1) {
   if (t < 0) t = h->count;
   for (PipeCtx& c : h->ctx) {
-    if (c.busy && c.frame - h->m + 2 <= t - h->cap) {
+    if (c.busy && c.frame - c.p <= t - h->cap) {
       if (c.phi_pending) {                     // its Phi must run before the slot is reused
         const int rc = flush_pending(h, st);
         if (rc != SDMD_OK) return rc;
@@ -407,6 +411,14 @@ int flush_one(sdmd_s* h, cudaStream_t st) {
   if (k.fr1) CK(cudaEventRecord(k.fr1, st));
   k.fr1 = nullptr;
   k.phi_pending = false;
+  return SDMD_OK;
+}
+
+// Make `st` wait for every in-flight frame's eigensolver and output copies
+// (they read G in place), before G is rewritten inside resident windows.
+int wait_modes_readers(sdmd_s* h, cudaStream_t st) {
+  for (PipeCtx& c : h->ctx)
+    if (c.busy) CK(cudaStreamWaitEvent(st, c.ev_modes, 0));
   return SDMD_OK;
 }
 
@@ -494,7 +506,6 @@ int sdmd_create_ex(int64_t n, int32_t m, int32_t dtype, int32_t depth, sdmd_t* o
       if (e == cudaSuccess) e = cudaMalloc(&c.r_dev, sizeof(int));
       if (e == cudaSuccess) e = cudaMalloc(&c.phi_sched, kPhiSchedWords * sizeof(unsigned));
       if (e == cudaSuccess) e = cudaMemset(c.phi_sched, 0, kPhiSchedWords * sizeof(unsigned));
-      if (e == cudaSuccess) e = cudaMalloc(&c.gsnap, (size_t)m * m * h->gsz);
       if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c.st, cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_g, cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming);
@@ -969,7 +980,8 @@ int sdmd_rebuild(sdmd_t h, void* stream) {
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   {
-    const int rc = flush_pending(h, st);
+    int rc = flush_pending(h, st);
+    if (rc == SDMD_OK) rc = wait_modes_readers(h, st);
     if (rc != SDMD_OK) return rc;
   }
   const int c = resident(h);
@@ -1335,19 +1347,16 @@ int sdmd_step(sdmd_t h, const void* x, int32_t r, void* phi, void* lambda, int32
     CK(cudaStreamWaitEvent(st, k.ev_done, 0));
     k.busy = false;
   }
-  // snapshot the window's G (time order) on the push stream
-  gather_gram_kernel<<<(c * c + 255) / 256, 256, 0, st>>>(static_cast<const uint64_t*>(h->G), h->cap, c,
-                                                           oldest_slot(h), 1, static_cast<uint64_t*>(k.gsnap));
-  CK(cudaGetLastError());
+  // the eigensolver reads the window's G in place once this frame's row is in
   CK(cudaEventRecord(k.ev_g, st));
   CK(cudaStreamWaitEvent(k.st, k.ev_g, 0));
   ModesArgs a;
-  a.G = k.gsnap;
+  a.G = h->G;
   a.g_is_int = (h->dtype == SDMD_U8) ? 1 : 0;
-  a.m = c;
+  a.m = h->cap;
   a.ws_m = h->m;
   a.c = c;
-  a.start = 0;
+  a.start = oldest_slot(h);
   a.r_req = r;
   a.ws = k.ws;
   a.status = h->status;

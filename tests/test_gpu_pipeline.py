@@ -78,6 +78,47 @@ def test_pipelined_step_equals_serial(cuda_device, kind, depth, m, r):
         S.sdmd_destroy(hs)
 
 
+def test_rebuild_waits_for_frames_in_flight(cuda_device):
+    # the eigensolvers of frames in flight read the window's G in place; a
+    # rebuild rewrites every entry (BF16x3 on an FP32 window: within 1e-6 of
+    # the FP32 row passes, not equal to them), so it must wait for them: every
+    # frame stepped before the rebuild matches the serial handle bit for bit
+    ps = synth.PlantedStream(side=40, noise_var=1e-4, seed=9)
+    n, m, depth, r = ps.n, 24, 4, 5
+    T = m + 12
+    t_rb = T - 5
+    frames = [torch.from_numpy(ps.snapshot(t)).to(cuda_device) for t in range(T)]
+    hp = S.sdmd_create_ex(n, m, S.SDMD_F32, depth)
+    hs = S.sdmd_create(n, m, S.SDMD_F32)
+    lam_p = torch.zeros(T, 2 * r, dtype=torch.float64, device=cuda_device)
+    rk_p = torch.zeros(T, dtype=torch.int32, device=cuda_device)
+    phis = [torch.zeros(r, n, 2, dtype=torch.float32, device=cuda_device) for _ in range(depth)]
+    stream = torch.cuda.Stream(device=cuda_device)
+    try:
+        S.sdmd_set_option(hp, S.SDMD_OPT_F32_BF16X3, 1)   # single pushes stay FP32 row passes
+        with torch.cuda.stream(stream):
+            for t in range(T):
+                S.sdmd_step(hp, frames[t], r, phis[t % depth], lam_p[t], rk_p[t:t + 1], stream)
+                if t == t_rb:
+                    S.sdmd_rebuild(hp, stream)
+            S.sdmd_sync(hp, stream)
+        stream.synchronize()
+        assert S.sdmd_status(hp) == S.SDMD_OK
+        for t in range(T):
+            S.sdmd_push(hs, frames[t])
+            if t < 2 or t > t_rb:
+                continue
+            lam_s = torch.zeros(2 * r, dtype=torch.float64, device=cuda_device)
+            rk_s = torch.zeros(1, dtype=torch.int32, device=cuda_device)
+            S.sdmd_modes(hs, r, None, lam_s, rk_s)
+            torch.cuda.synchronize()
+            assert torch.equal(lam_s, lam_p[t]), t
+            assert torch.equal(rk_s, rk_p[t:t + 1]), t
+    finally:
+        S.sdmd_destroy(hp)
+        S.sdmd_destroy(hs)
+
+
 def _phi_reference_full(frames, t, m, M):
     """The oracle's modes X' M of the window ending at frame t, every row:
     X' = frames t - m + 2 .. t (exact uint8 values in FP64), M from the
