@@ -1054,21 +1054,38 @@ __device__ __forceinline__ void modes_small_body(const ModesArgs& a, const Modes
     const dd gv = dd_from_double(v);
     A[idx] = {ldexpf(gv.hi, -s_exp), ldexpf(gv.lo, -s_exp)};
   }
-  for (int idx = tid; !a.embed_cx && idx < p * p; idx += kThreads) {
-    const int i = idx / p, j = idx - i * p;
-    const int si = (a.start + i) % m, sj = (a.start + j) % m, sj1 = (a.start + j + 1) % m;
-    dd gx, gxy;
-    if (a.g_is_int) {
-      const long long* G = static_cast<const long long*>(a.G);
-      gx = dd_from_ll(G[(int64_t)si * m + sj]);
-      gxy = dd_from_ll(G[(int64_t)si * m + sj1]);
-    } else {
-      const double* G = static_cast<const double*>(a.G);
-      gx = dd_from_double(G[(int64_t)si * m + sj]);
-      gxy = dd_from_double(G[(int64_t)si * m + sj1]);
+  // G_X and G_XY entries, kGatherBatch per thread loaded before any is
+  // converted and stored (the stores could alias G for the compiler, so a
+  // plain loop waits a full memory latency per entry; beside a bandwidth-bound
+  // pass that latency is long)
+  constexpr int kGatherBatch = 8;
+  for (int base = tid; !a.embed_cx && base < p * p; base += kThreads * kGatherBatch) {
+    int64_t raw_x[kGatherBatch], raw_xy[kGatherBatch];   // the G words (int64 or the bits of an FP64)
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      const int idx = base + u * kThreads;
+      raw_x[u] = raw_xy[u] = 0;
+      if (idx < p * p) {
+        const int i = idx / p, j = idx - i * p;
+        int si = a.start + i, sj = a.start + j;
+        if (si >= m) si -= m;
+        if (sj >= m) sj -= m;
+        const int sj1 = (sj + 1 == m) ? 0 : sj + 1;
+        const long long* G = static_cast<const long long*>(a.G);
+        raw_x[u] = G[(int64_t)si * m + sj];
+        raw_xy[u] = G[(int64_t)si * m + sj1];
+      }
     }
-    A[idx] = {ldexpf(gx.hi, -s_exp), ldexpf(gx.lo, -s_exp)};
-    w.GXYd[idx] = {ldexpf(gxy.hi, -s_exp), ldexpf(gxy.lo, -s_exp)};
+#pragma unroll
+    for (int u = 0; u < kGatherBatch; ++u) {
+      const int idx = base + u * kThreads;
+      if (idx < p * p) {
+        const dd gx = a.g_is_int ? dd_from_ll(raw_x[u]) : dd_from_double(__longlong_as_double(raw_x[u]));
+        const dd gxy = a.g_is_int ? dd_from_ll(raw_xy[u]) : dd_from_double(__longlong_as_double(raw_xy[u]));
+        A[idx] = {ldexpf(gx.hi, -s_exp), ldexpf(gx.lo, -s_exp)};
+        w.GXYd[idx] = {ldexpf(gxy.hi, -s_exp), ldexpf(gxy.lo, -s_exp)};
+      }
+    }
   }
   __syncthreads();
   if (tid == 0) w.clk[1] = clock64();

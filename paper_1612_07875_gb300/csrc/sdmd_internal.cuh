@@ -172,7 +172,7 @@ struct ModesArgs {
   int32_t m;            // stride of G and modulus of its slot indices
   int32_t ws_m;         // window length the workspace `ws` was laid out for
   int32_t c;            // resident snapshots (>= 3)
-  int32_t start;        // physical slot of the oldest resident snapshot
+  int32_t start;        // physical slot of the oldest resident snapshot (0 <= start < m)
   int32_t r_req;        // requested modes (1 <= r_req <= c-1)
   double* ws;           // workspace (modes_ws_doubles(m) doubles)
   int* status;          // device status word (sticky error bits)
@@ -224,7 +224,7 @@ struct PhiArgs {
   int64_t n;
   int32_t dtype;
   int32_t m;
-  int32_t start;        // physical slot of the oldest resident snapshot
+  int32_t start;        // physical slot of the oldest resident snapshot (0 <= start < m)
   int32_t p;            // c-1 columns of X'
   int32_t r;            // requested modes (output columns)
   const float* Mf;      // p x 2r  (re, im) of V Sigma^-1 W, FP32
