@@ -318,8 +318,9 @@ SDMD_API int sdmd_step(sdmd_t h, const void *x, int32_t r, void *phi, void *lamb
  * schedule at the end. uint8 rows are exact under every schedule; float rows
  * change only in rounding (the reduction order follows the chunks).
  * chunk_bytes / us (host, may be NULL) receive the kept chunk size and its
- * time per row. Waits for the stream. Dense handles with at least one
- * snapshot (SDMD_ERR_NOT_READY otherwise).
+ * time per row. Waits for the stream, and first for the eigensolvers of
+ * sdmd_step frames still in flight (they read that row). Dense handles with
+ * at least one snapshot (SDMD_ERR_NOT_READY otherwise).
  */
 SDMD_API int sdmd_autotune(sdmd_t h, int64_t *chunk_bytes, double *us, void *stream);
 

@@ -1398,7 +1398,11 @@ int sdmd_autotune(sdmd_t h, int64_t* chunk_bytes, double* us, void* stream) {
   DeviceScope ds(h->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   {
-    const int rc = flush_pending(h, st);
+    // the timing passes rewrite the newest row and column of G (FP32 windows:
+    // in each schedule's summation order), which every in-flight frame's
+    // eigensolver reads in place
+    int rc = flush_pending(h, st);
+    if (rc == SDMD_OK) rc = wait_modes_readers(h, st);
     if (rc != SDMD_OK) return rc;
   }
   static const int kCands[] = {1, 2, 3, 4, 6};   // chunks per SM
