@@ -89,30 +89,43 @@ def test_streaming_equals_recomputed_bitwise(cuda_device, kind):
         S.sdmd_destroy(b)
 
 
-def test_host_pageable_pinned_and_device_inputs_agree(cuda_device):
+@pytest.mark.parametrize("kind", ["f32", "u8"])
+def test_host_pageable_pinned_and_device_inputs_agree(cuda_device, kind):
+    # device rows with 16-byte aligned addresses go through the library's copy
+    # kernel (n = 30011: the last 12 (f32) or 11 (u8) bytes by its tail path),
+    # a device view one element off and host sources through cudaMemcpyAsync:
+    # the same G bit for bit
     n, m = 30011, 4
-    gen = _gen("f32", n, seed=9)
+    gen = _gen(kind, n, seed=9)
     xs = [gen(t) for t in range(6)]
+    dt = S.SDMD_U8 if kind == "u8" else S.SDMD_F32
     Gs = []
-    for mode in ("device", "pageable", "pinned"):
-        h = S.sdmd_create(n, m, S.SDMD_F32)
-        keep = []      # pinned sources must outlive their asynchronous copies
+    for mode in ("device", "device_offset", "pageable", "pinned"):
+        h = S.sdmd_create(n, m, dt)
+        keep = []      # sources must outlive their asynchronous copies
         try:
             for x in xs:
+                xt = torch.from_numpy(x)
                 if mode == "device":
-                    S.sdmd_push(h, torch.from_numpy(x).to(cuda_device))
+                    S.sdmd_push(h, xt.to(cuda_device))
+                elif mode == "device_offset":
+                    buf = torch.empty(n + 1, dtype=xt.dtype, device=cuda_device)
+                    buf[1:].copy_(xt)
+                    keep.append(buf)
+                    S.sdmd_push(h, buf[1:])
                 elif mode == "pageable":
                     S.sdmd_push(h, x)
                 else:
-                    keep.append(torch.from_numpy(x).pin_memory())
+                    keep.append(xt.pin_memory())
                     S.sdmd_push(h, keep[-1])
             torch.cuda.synchronize()
-            out = np.zeros((m, m))
+            out = np.zeros((m, m), dtype=np.int64 if kind == "u8" else np.float64)
             S.sdmd_gram(h, out)           # pageable host output: call waits
             Gs.append(out)
         finally:
             S.sdmd_destroy(h)
-    assert np.array_equal(Gs[0], Gs[1]) and np.array_equal(Gs[0], Gs[2])
+    for G in Gs[1:]:
+        assert np.array_equal(Gs[0], G)
 
 
 def test_u8_extreme_values_exact_beyond_int32(cuda_device):
